@@ -1,0 +1,141 @@
+"""Seeded synthetic workloads shared by the CUDA path and the oracle.
+
+This module only builds inputs: parameter sets and boundary-data profiles of
+the consolidation problems used for parity tests and benchmarks.  It holds none
+of the method's arithmetic and imports neither the CUDA binding nor the oracle.
+
+A parameter set is a plain dict with the keys
+    nx, ny, lx, ly, lam, mu, alpha, c0, kappa, dt, r, levels, K, gamma,
+    tol, ne_max, ne_fixed, precision
+and ``sides`` is a list of four dicts (bottom, right, top, left) with
+``eta_type`` / ``p_type`` (PERIODIC, SYMMETRY, DIRICHLET, NEUMANN) and optional
+``eta_profile`` (shape (2, 2n+1): Dirichlet displacement or Neumann traction)
+and ``p_profile`` (shape (2n+1,): Dirichlet pressure).  Profile sample k sits
+at arc position k*h/2 along the side (even k: cell faces, odd k: centres).
+
+Problem statements: Terzaghi's consolidation problem of §4.2 (quasi-1D, top
+load, drained top, fixed bottom) and the step-load 2D extension of §4.3; the
+grid sizes, material values and step counts are those of the benchmark
+configurations (nodes n -> n-1 cells on the cell-centred lattice).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+PERIODIC, SYMMETRY, DIRICHLET, NEUMANN = 0, 1, 2, 3
+BOTTOM, RIGHT, TOP, LEFT = 0, 1, 2, 3
+FP64, FP32 = 0, 1
+
+
+def _params(n, *, lam, mu, alpha, c0, kappa, dt, levels, K=4, gamma=0.75, r=0.5,
+            tol=1e-10, ne_max=100, ne_fixed=0, precision=FP64, ny=None, lx=1.0):
+    ny = n if ny is None else ny
+    return dict(nx=n, ny=ny, lx=lx, ly=lx * ny / n, lam=lam, mu=mu, alpha=alpha, c0=c0,
+                kappa=kappa, dt=dt, r=r, levels=levels, K=K, gamma=gamma, tol=tol,
+                ne_max=ne_max, ne_fixed=ne_fixed, precision=precision)
+
+
+def top_load_sides(nx: int, load: np.ndarray, side_type=SYMMETRY):
+    """Bottom: fixed displacement, no flow.  Top: traction (0, -load(x)), p = 0.
+    Left/right: ``side_type`` for both fields (SYMMETRY = roller + no flux, or PERIODIC)."""
+    eta_top = np.zeros((2, 2 * nx + 1))
+    eta_top[1] = -np.asarray(load, dtype=np.float64)
+    return [
+        dict(eta_type=DIRICHLET, p_type=NEUMANN),
+        dict(eta_type=side_type, p_type=side_type),
+        dict(eta_type=NEUMANN, p_type=DIRICHLET, eta_profile=eta_top,
+             p_profile=np.zeros(2 * nx + 1)),
+        dict(eta_type=side_type, p_type=side_type),
+    ]
+
+
+def uniform_load(nx: int, sigma0: float = 1.0) -> np.ndarray:
+    return np.full(2 * nx + 1, sigma0)
+
+
+def step_load(nx: int, x_end: float = 0.5, sigma0: float = 1.0, lx: float = 1.0) -> np.ndarray:
+    """sigma0 for x < x_end, sigma0/2 exactly at x_end, 0 beyond (samples at k*h/2)."""
+    x = np.arange(2 * nx + 1) * (lx / nx) / 2.0
+    v = np.where(x < x_end, sigma0, 0.0)
+    v[np.isclose(x, x_end)] = 0.5 * sigma0
+    return v
+
+
+# ---------------------------------------------------------------------------
+# Benchmark / parity configurations.
+# ---------------------------------------------------------------------------
+
+def terzaghi_33(precision=FP64, side_type=SYMMETRY):
+    """Terzaghi consolidation, 33x33 nodes (32x32 cells), unit square,
+    lambda = mu = 1, alpha = 1, c0 = 0.1, kappa = 1, unit top load at t = 0+,
+    3 levels, residual tolerance 1e-10, 50 steps to T = 0.1."""
+    n = 32
+    p = _params(n, lam=1.0, mu=1.0, alpha=1.0, c0=0.1, kappa=1.0, dt=0.1 / 50, levels=3,
+                tol=1e-10, precision=precision)
+    return p, top_load_sides(n, uniform_load(n), side_type), 50
+
+
+def step_load_257(alpha=1.0, precision=FP64, n=256, ne_fixed=3, steps=200):
+    """2D Terzaghi extension, 257x257 nodes (256x256 cells): load 1 on the top
+    for x < 0.5, traction-free elsewhere; lambda = mu = 1, c0 = 0.01, kappa = 1,
+    6 levels, 200 steps to T = 0.1, fixed MG(3,4)."""
+    levels = int(np.log2(n)) - 2
+    p = _params(n, lam=1.0, mu=1.0, alpha=alpha, c0=0.01, kappa=1.0, dt=0.1 / 200,
+                levels=levels, ne_fixed=ne_fixed, precision=precision)
+    return p, top_load_sides(n, step_load(n)), steps
+
+
+def terzaghi_4097(precision=FP32, n=4096, ne_fixed=3, steps=100):
+    """Single large instance, 4097x4097 nodes (4096x4096 cells), same boundary
+    conditions as the 33x33 Terzaghi case; lambda = mu = 1, alpha = 1,
+    c0 = 0.1, kappa = 1e-2, 10 levels, 100 steps to T = 0.1, fixed MG(3,4)."""
+    levels = int(np.log2(n)) - 2
+    p = _params(n, lam=1.0, mu=1.0, alpha=1.0, c0=0.1, kappa=1e-2, dt=0.1 / 100,
+                levels=levels, ne_fixed=ne_fixed, precision=precision)
+    return p, top_load_sides(n, uniform_load(n)), steps
+
+
+def paper_terzaghi(n: int, alpha: float = 1.0, ne_fixed=3, K=4, side_type=PERIODIC):
+    """Terzaghi's problem with the parameters of §4.2: E = 1, nu = 0.8 (plane
+    stress), kappa = (25 + 9 alpha^2)/25, load varpi = alpha + (lam+2mu)/alpha so
+    that p0 = 1, c0 = 1, dt = dx^2/4, periodic sides, MG(ne_fixed, K)."""
+    lam, mu = 20.0 / 9.0, 5.0 / 18.0
+    kappa = (25.0 + 9.0 * alpha ** 2) / 25.0
+    varpi = alpha + (lam + 2 * mu) / alpha
+    h = 1.0 / n
+    p = _params(n, lam=lam, mu=mu, alpha=alpha, c0=1.0, kappa=kappa, dt=h * h / 4,
+                levels=int(np.log2(n)), K=K, ne_fixed=ne_fixed)
+    return p, top_load_sides(n, uniform_load(n, varpi), side_type), varpi
+
+
+def manufactured_params(n: int, alpha: float, r: float, ne_fixed=3, K=2):
+    """Periodic manufactured problem of §4.1: (0,1)^2, lambda = 11/45,
+    mu = 11/360, kappa = 1/10, c0 = 1, dt = dx^2, all sides periodic, MG(ne_fixed, K)."""
+    h = 1.0 / n
+    p = _params(n, lam=11.0 / 45.0, mu=11.0 / 360.0, alpha=alpha, c0=1.0, kappa=0.1,
+                dt=h * h, levels=int(np.log2(n)), K=K, r=r, ne_fixed=ne_fixed)
+    sides = [dict(eta_type=PERIODIC, p_type=PERIODIC) for _ in range(4)]
+    return p, sides
+
+
+def batched_instances(count: int = 64, seed: int = 2409):
+    """Seeded uneven instances: side uniform in {64,128,256,512} cells, lambda, mu
+    log-uniform [0.1, 10], alpha U[0.5, 1], c0 log-U[1e-3, 1], kappa log-U[1e-3, 1],
+    a partial top load on a seeded interval of length >= 1/8, fixed MG(3,4)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(count):
+        n = int(rng.choice([64, 128, 256, 512]))
+        lam = float(10 ** rng.uniform(-1, 1))
+        mu = float(10 ** rng.uniform(-1, 1))
+        alpha = float(rng.uniform(0.5, 1.0))
+        c0 = float(10 ** rng.uniform(-3, 0))
+        kappa = float(10 ** rng.uniform(-3, 0))
+        a = float(rng.uniform(0.0, 7.0 / 8.0))
+        b = float(rng.uniform(a + 1.0 / 8.0, 1.0))
+        x = np.arange(2 * n + 1) * (1.0 / n) / 2.0
+        load = np.where((x > a) & (x < b), 1.0, 0.0)
+        p = _params(n, lam=lam, mu=mu, alpha=alpha, c0=c0, kappa=kappa, dt=0.1 / 100,
+                    levels=int(np.log2(n)) - 2, ne_fixed=3, precision=FP32)
+        out.append((p, top_load_sides(n, load)))
+    return out
