@@ -1,0 +1,193 @@
+/*
+ * biot.h -- C ABI of a single-GPU (sm_103a) solver for Biot's consolidation
+ * model by the coupled lattice Boltzmann method of Lunowa & Wohlmuth,
+ * "A lattice Boltzmann method for Biot's consolidation model of linear
+ * poroelasticity" (arXiv 2409.11382).
+ *
+ * The problem (§2.1, eqs. elasticity, stress, flow, darcy) on the rectangle
+ * (0, lx) x (0, ly):
+ *     -div sigma + alpha grad p = f,   sigma = lambda div(eta) I + mu (grad eta + grad eta^T),
+ *     d/dt (c0 p + alpha div eta) + div u = s,   u = -kappa grad p,
+ * with p(0) = 0 and eta(0) = 0 (§3.6).  Each time step runs the pseudo-time
+ * MRT LBM for elasticity inside its multigrid V-cycle (Alg. 4 with Alg. 2)
+ * N_E times, then one SRT LBM step for the pressure (Alg. 3), coupled by the
+ * centered update of eq. source:implicit -- together Alg. 5.
+ *
+ * Conventions for every entry point:
+ *  - Return value: BIOT_OK (0) or a negative BIOT_ERR_* code; no exception or
+ *    abort crosses the ABI.  biot_last_error() describes the last failure of
+ *    the calling thread.
+ *  - All pointers passed in are HOST pointers unless the name ends in
+ *    "_device".  Inputs are copied before the call returns; the caller keeps
+ *    ownership of every buffer it passes.
+ *  - The handle owns all device memory it allocates; biot_destroy frees it.
+ *  - A handle may be used by one host thread at a time.
+ *  - Fields are stored y-major: value (x, y) of component c of an
+ *    nx-by-ny field lives at [c * nx * ny + y * nx + x]; cell (x, y) has its
+ *    centre at ((x + 1/2) h, (y + 1/2) h), h = lx / nx = ly / ny.
+ */
+#ifndef BIOT_GB300_H
+#define BIOT_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define BIOT_API __attribute__((visibility("default")))
+#else
+#define BIOT_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- return codes ---------------------------------------------------------- */
+#define BIOT_OK                 0
+#define BIOT_ERR_INVALID_ARG   -1  /* a parameter violates a documented constraint */
+#define BIOT_ERR_OOM           -2  /* device or host allocation failed */
+#define BIOT_ERR_DIVERGED      -3  /* a non-finite residual was met (e.g. unstable coupling) */
+#define BIOT_ERR_NOT_CONVERGED -4  /* a step reached ne_max V-cycles above tolerance (results kept) */
+#define BIOT_ERR_CUDA          -5  /* a CUDA call failed; see biot_last_error() */
+#define BIOT_ERR_TIMEOUT       -6  /* a bounded device-side wait gave up */
+#define BIOT_ERR_NO_DEVICE     -7  /* no CUDA device is visible */
+
+/* ---- storage precision of the populations --------------------------------- */
+#define BIOT_FP64 0  /* all populations and arithmetic in FP64 (parity path) */
+#define BIOT_FP32 1  /* FP32 populations and collisions; FP64 for residual norms,
+                        the coarsest multigrid level and the divergence / pressure
+                        accumulations of the coupling */
+
+/* ---- boundary condition types (§3.6) --------------------------------------- */
+#define BIOT_PERIODIC  0  /* wrap-around streaming; must be set on both opposite sides
+                             and for both fields */
+#define BIOT_SYMMETRY  1  /* mirror (specular) reflection: a roller wall for the
+                             displacement (normal displacement and shear stress vanish)
+                             and a no-flux wall for the pressure */
+#define BIOT_DIRICHLET 2  /* displacement: fullway bounce-back with a one-pseudo-step
+                             delay, eq. BC:elasticity;  pressure: halfway
+                             anti-bounce-back, eq. BC:pressure */
+#define BIOT_NEUMANN   3  /* displacement: traction via halfway anti-bounce-back,
+                             eq. BC:traction;  pressure: no-flow halfway bounce-back,
+                             eq. BC:noFlow */
+/* A population whose source lies beyond a corner follows the top/bottom rule,
+ * except that a DIRICHLET or NEUMANN left/right wall wins over a SYMMETRY
+ * top/bottom; two SYMMETRY walls reflect it twice. */
+
+/* ---- sides ------------------------------------------------------------------ */
+#define BIOT_BOTTOM 0  /* y = 0,  outward normal (0,-1) */
+#define BIOT_RIGHT  1  /* x = lx, outward normal (1,0)  */
+#define BIOT_TOP    2  /* y = ly, outward normal (0,1)  */
+#define BIOT_LEFT   3  /* x = 0,  outward normal (-1,0) */
+
+/* Parameters of one instance (all dimensional, §2.1).  Lattice quantities
+ * follow the scaling of §2.2 with L = h, T = dt, H = 1 (eps = h). */
+typedef struct biot_params {
+    int    nx, ny;     /* lattice cells of the finest grid (the paper's N_x, N_y);
+                          both divisible by 2^(mg_levels-1) */
+    double lx, ly;     /* domain size; lx/nx must equal ly/ny */
+    double lambda, mu; /* Lame coefficients; mu > 0, lambda + mu > 0 */
+    double alpha;      /* Biot-Willis coefficient, in [0, 1] */
+    double c0;         /* specific storage coefficient, > 0 */
+    double kappa;      /* permeability (viscosity-reduced), > 0 */
+    double dt;         /* physical time step, > 0 */
+    double r_coupling; /* ratio r of eq. source:implicit: 0 explicit, 0.5 centered, 1 implicit */
+    int    mg_levels;  /* multigrid levels L >= 1 (Alg. 4) */
+    int    K;          /* smoothing sweeps before and after the coarse correction, >= 1 */
+    double gamma;      /* under-relaxation of eq. MG:smoother, in (0, 1] (paper: 0.75) */
+    double tol;        /* stop the V-cycles of a step once the residual
+                          max|g - ELASTIC_STEP(g)| <= tol * max(1, max|g|) (ne_fixed <= 0) */
+    int    ne_max;     /* cap on V-cycles per step in tolerance mode */
+    int    ne_fixed;   /* > 0: exactly this many V-cycles per step, MG(ne_fixed, K) */
+    int    precision;  /* BIOT_FP64 or BIOT_FP32 */
+} biot_params;
+
+/* Boundary data of one side.  Profiles are sampled at the 2n+1 arc positions
+ * k*h/2, k = 0..2n, along the side (n = nx for bottom/top, ny for left/right;
+ * the arc runs in +x or +y), so that even k are cell faces and odd k cell
+ * centres; a bounce-back rule evaluated at x + c/2 (eqs. BC:pressure,
+ * BC:elasticity, BC:traction) reads the sample at its wall crossing. */
+typedef struct biot_side {
+    int eta_type;              /* BIOT_PERIODIC / SYMMETRY / DIRICHLET / NEUMANN */
+    int p_type;                /* BIOT_PERIODIC / SYMMETRY / DIRICHLET / NEUMANN */
+    const double *eta_profile; /* 2 x (2n+1), [component][k]: displacement eta_D (DIRICHLET)
+                                  or traction t = sigma n (NEUMANN); NULL = zero */
+    const double *p_profile;   /* 2n+1: pressure p_D (DIRICHLET); NULL = zero */
+} biot_side;
+
+typedef struct biot_stats {
+    int     last_ne;        /* V-cycles of the last elastic solve */
+    double  last_res;       /* residual measured in its last smoothing sweep */
+    long    total_cycles;   /* V-cycles since creation */
+    int     notconv_steps;  /* steps that hit ne_max */
+    int     diverged;       /* 1 once a non-finite residual was met */
+    long    nstep;          /* physical time steps taken */
+    double  t;              /* current time nstep*dt */
+    double  omega;          /* flow relaxation rate, eq. pressure:rate (lattice units) */
+    double  omega_s, omega_d; /* elastic relaxation rates, Tab. moments */
+    long    kernel_launches;  /* kernels launched since creation */
+    size_t  device_bytes;     /* device memory held */
+} biot_stats;
+
+typedef struct biot_ctx *biot_handle;
+
+/* Validate the parameters (constraints above; a PERIODIC side must face a
+ * PERIODIC side for both fields) and create an instance at t = 0 with zero body force
+ * and source.  Allocates all device memory of the multigrid hierarchy on the
+ * current CUDA device.  On failure *out is NULL. */
+BIOT_API int biot_create(const biot_params *p, const biot_side sides[4], biot_handle *out);
+
+/* Free all device and host memory of the instance.  NULL is accepted. */
+BIOT_API int biot_destroy(biot_handle h);
+
+/* Launch all further work of the instance on this CUDA stream (a
+ * cudaStream_t passed as void*); NULL selects the instance's own stream. */
+BIOT_API int biot_set_stream(biot_handle h, void *cuda_stream);
+
+/* Replace the solid body force f (2 x nx x ny, dimensional, NULL = zero) and
+ * the fluid source s (nx x ny, NULL = zero) of eqs. elasticity / flow.  They
+ * act from the next elastic solve on; before the first step they also enter
+ * the initial populations of eqs. ICs / ICs:moments. */
+BIOT_API int biot_set_sources(biot_handle h, const double *f_body, const double *s);
+
+/* Replace the boundary data of one side (same layout as biot_side; the types
+ * are fixed at creation).  NULL sets zero data. */
+BIOT_API int biot_set_side_profile(biot_handle h, int side, const double *eta_profile, const double *p_profile);
+
+/* Run n iterations of the time loop of Alg. 5 (elastic solve at t, flow step
+ * to t + dt), followed by the elastic solve at the new time, so that
+ * biot_read_u and biot_read_p refer to the same t.  Returns BIOT_OK,
+ * BIOT_ERR_NOT_CONVERGED (a step hit ne_max; the state is kept) or
+ * BIOT_ERR_DIVERGED (the state is no longer meaningful). */
+BIOT_API int biot_step(biot_handle h, int n);
+
+/* Step until t = round(T/dt)*dt (T not before the current time). */
+BIOT_API int biot_solve_to(biot_handle h, double T);
+
+/* Displacement eta (2 x nx x ny) of eq. displacement and its time. */
+BIOT_API int biot_read_u(biot_handle h, double *eta, double *t_out);
+
+/* Pressure p (nx x ny) of eq. pressure, p = p^ / c0, and its time. */
+BIOT_API int biot_read_p(biot_handle h, double *p, double *t_out);
+
+/* Stress (3 x nx x ny: sigma_11, sigma_12, sigma_22) of eqs. displacement /
+ * moments:bared. */
+BIOT_API int biot_read_stress(biot_handle h, double *sigma);
+
+BIOT_API int biot_stats_get(biot_handle h, biot_stats *out);
+
+/* Static description of an error code, and the last error of this thread. */
+BIOT_API const char *biot_error_string(int code);
+BIOT_API const char *biot_last_error(void);
+
+/* Kernel instrumentation: when enabled, every launch of the finest-level
+ * smoothing sweep is bracketed by CUDA events on the instance's stream.
+ * biot_sweep_timing_get synchronises the stream and returns the summed
+ * device time (ms) and the number of such launches since the last enable. */
+BIOT_API int biot_sweep_timing(biot_handle h, int enable);
+BIOT_API int biot_sweep_timing_get(biot_handle h, double *ms_total, long *launches);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BIOT_GB300_H */

@@ -1,0 +1,228 @@
+"""Thin Python binding of the C ABI declared in ``include/biot.h``.
+
+Argument marshalling only: every step of the solver runs in the sm_103a
+kernels of ``libbiot_gb300.so``.  There is no CPU fallback -- loading fails
+with an error if the shared library has not been built, and creating an
+instance fails if no CUDA device is visible.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libbiot_gb300.so")
+
+OK, ERR_INVALID_ARG, ERR_OOM, ERR_DIVERGED, ERR_NOT_CONVERGED, ERR_CUDA, ERR_TIMEOUT, ERR_NO_DEVICE = (
+    0, -1, -2, -3, -4, -5, -6, -7)
+FP64, FP32 = 0, 1
+PERIODIC, SYMMETRY, DIRICHLET, NEUMANN = 0, 1, 2, 3
+BOTTOM, RIGHT, TOP, LEFT = 0, 1, 2, 3
+
+# Every function the header declares (checked by the tests against include/biot.h).
+API_FUNCTIONS = (
+    "biot_create", "biot_destroy", "biot_set_stream", "biot_set_sources", "biot_set_side_profile",
+    "biot_step", "biot_solve_to", "biot_read_u", "biot_read_p", "biot_read_stress",
+    "biot_stats_get", "biot_error_string", "biot_last_error", "biot_sweep_timing",
+    "biot_sweep_timing_get",
+)
+
+
+class BiotError(RuntimeError):
+    def __init__(self, code: int, where: str, detail: str):
+        super().__init__(f"{where} failed with code {code}: {detail}")
+        self.code = code
+
+
+class biot_params(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("lx", C.c_double), ("ly", C.c_double),
+                ("lambda_", C.c_double), ("mu", C.c_double), ("alpha", C.c_double),
+                ("c0", C.c_double), ("kappa", C.c_double), ("dt", C.c_double),
+                ("r_coupling", C.c_double), ("mg_levels", C.c_int), ("K", C.c_int),
+                ("gamma", C.c_double), ("tol", C.c_double), ("ne_max", C.c_int),
+                ("ne_fixed", C.c_int), ("precision", C.c_int)]
+
+
+class biot_side(C.Structure):
+    _fields_ = [("eta_type", C.c_int), ("p_type", C.c_int),
+                ("eta_profile", C.POINTER(C.c_double)), ("p_profile", C.POINTER(C.c_double))]
+
+
+class biot_stats(C.Structure):
+    _fields_ = [("last_ne", C.c_int), ("last_res", C.c_double), ("total_cycles", C.c_long),
+                ("notconv_steps", C.c_int), ("diverged", C.c_int), ("nstep", C.c_long),
+                ("t", C.c_double), ("omega", C.c_double), ("omega_s", C.c_double),
+                ("omega_d", C.c_double), ("kernel_launches", C.c_long),
+                ("device_bytes", C.c_size_t)]
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load ``libbiot_gb300.so``; raises if it is missing (no fallback path exists)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(
+            f"{path} is missing: build the CUDA library first "
+            "(python -c 'import __graft_entry__ as g; g.build()')")
+    lib = C.CDLL(path)
+    P = C.POINTER(C.c_double)
+    H = C.c_void_p
+    lib.biot_create.argtypes = [C.POINTER(biot_params), C.POINTER(biot_side), C.POINTER(H)]
+    lib.biot_destroy.argtypes = [H]
+    lib.biot_set_stream.argtypes = [H, C.c_void_p]
+    lib.biot_set_sources.argtypes = [H, P, P]
+    lib.biot_set_side_profile.argtypes = [H, C.c_int, P, P]
+    lib.biot_step.argtypes = [H, C.c_int]
+    lib.biot_solve_to.argtypes = [H, C.c_double]
+    lib.biot_read_u.argtypes = [H, P, P]
+    lib.biot_read_p.argtypes = [H, P, P]
+    lib.biot_read_stress.argtypes = [H, P]
+    lib.biot_stats_get.argtypes = [H, C.POINTER(biot_stats)]
+    lib.biot_error_string.argtypes = [C.c_int]
+    lib.biot_error_string.restype = C.c_char_p
+    lib.biot_last_error.argtypes = []
+    lib.biot_last_error.restype = C.c_char_p
+    lib.biot_sweep_timing.argtypes = [H, C.c_int]
+    lib.biot_sweep_timing_get.argtypes = [H, P, C.POINTER(C.c_long)]
+    for name in API_FUNCTIONS:
+        if name not in ("biot_error_string", "biot_last_error"):
+            getattr(lib, name).restype = C.c_int
+    _lib = lib
+    return lib
+
+
+def _dptr(a: Optional[np.ndarray]):
+    if a is None:
+        return C.POINTER(C.c_double)()
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _f64(a) -> Optional[np.ndarray]:
+    if a is None:
+        return None
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+class Solver:
+    """One instance of the coupled problem on the current CUDA device.
+
+    ``params`` uses the keys of ``biot_params`` (``lam`` for lambda); ``sides``
+    is a list of four dicts (bottom, right, top, left) with ``eta_type``,
+    ``p_type`` and optional ``eta_profile`` / ``p_profile`` arrays.
+    Methods map one-to-one onto the C entry points.
+    """
+
+    def __init__(self, params: dict, sides: Sequence[dict], stream: Optional[int] = None):
+        self._lib = load_library()
+        p = biot_params()
+        p.nx, p.ny = int(params["nx"]), int(params["ny"])
+        p.lx, p.ly = float(params["lx"]), float(params["ly"])
+        p.lambda_, p.mu = float(params["lam"]), float(params["mu"])
+        p.alpha, p.c0, p.kappa = float(params["alpha"]), float(params["c0"]), float(params["kappa"])
+        p.dt, p.r_coupling = float(params["dt"]), float(params.get("r", 0.5))
+        p.mg_levels, p.K = int(params["levels"]), int(params["K"])
+        p.gamma, p.tol = float(params["gamma"]), float(params["tol"])
+        p.ne_max, p.ne_fixed = int(params["ne_max"]), int(params["ne_fixed"])
+        p.precision = int(params.get("precision", FP64))
+        self.nx, self.ny = p.nx, p.ny
+        arr = (biot_side * 4)()
+        keep = []
+        for i, s in enumerate(sides):
+            arr[i].eta_type = int(s["eta_type"])
+            arr[i].p_type = int(s["p_type"])
+            for key in ("eta_profile", "p_profile"):
+                v = _f64(s.get(key))
+                if v is not None:
+                    keep.append(v)
+                setattr(arr[i], key, _dptr(v))
+        h = C.c_void_p()
+        self._check(self._lib.biot_create(C.byref(p), arr, C.byref(h)), "biot_create")
+        self._h = h
+        if stream is not None:
+            self.set_stream(stream)
+
+    # -- helpers --------------------------------------------------------------------
+    def _check(self, code: int, where: str, allow=(OK,)):
+        if code not in allow:
+            detail = self._lib.biot_last_error().decode(errors="replace")
+            raise BiotError(code, where, detail)
+        return code
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.biot_destroy(self._h)
+            self._h = None
+
+    destroy = close
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- API --------------------------------------------------------------------------
+    def set_stream(self, stream: Optional[int]):
+        self._check(self._lib.biot_set_stream(self._h, C.c_void_p(stream or 0)), "biot_set_stream")
+
+    def set_sources(self, f_body=None, s=None):
+        fb, sr = _f64(f_body), _f64(s)
+        self._check(self._lib.biot_set_sources(self._h, _dptr(fb), _dptr(sr)), "biot_set_sources")
+
+    def set_side_profile(self, side: int, eta_profile=None, p_profile=None):
+        e, p = _f64(eta_profile), _f64(p_profile)
+        self._check(self._lib.biot_set_side_profile(self._h, side, _dptr(e), _dptr(p)),
+                    "biot_set_side_profile")
+
+    def step(self, n: int = 1, allow_not_converged: bool = True) -> int:
+        allow = (OK, ERR_NOT_CONVERGED) if allow_not_converged else (OK,)
+        return self._check(self._lib.biot_step(self._h, int(n)), "biot_step", allow)
+
+    def solve_to(self, T: float, allow_not_converged: bool = True) -> int:
+        allow = (OK, ERR_NOT_CONVERGED) if allow_not_converged else (OK,)
+        return self._check(self._lib.biot_solve_to(self._h, float(T)), "biot_solve_to", allow)
+
+    def read_u(self, out: Optional[np.ndarray] = None):
+        out = np.empty((2, self.ny, self.nx)) if out is None else out
+        t = C.c_double()
+        self._check(self._lib.biot_read_u(self._h, _dptr(out), C.byref(t)), "biot_read_u")
+        return out, t.value
+
+    def read_p(self, out: Optional[np.ndarray] = None):
+        out = np.empty((self.ny, self.nx)) if out is None else out
+        t = C.c_double()
+        self._check(self._lib.biot_read_p(self._h, _dptr(out), C.byref(t)), "biot_read_p")
+        return out, t.value
+
+    def read_stress(self, out: Optional[np.ndarray] = None):
+        out = np.empty((3, self.ny, self.nx)) if out is None else out
+        self._check(self._lib.biot_read_stress(self._h, _dptr(out)), "biot_read_stress")
+        return out
+
+    def stats(self) -> dict:
+        s = biot_stats()
+        self._check(self._lib.biot_stats_get(self._h, C.byref(s)), "biot_stats_get")
+        return {name: getattr(s, name) for name, _ in biot_stats._fields_}
+
+    def sweep_timing(self, enable: bool):
+        self._check(self._lib.biot_sweep_timing(self._h, int(enable)), "biot_sweep_timing")
+
+    def sweep_timing_get(self):
+        ms = C.c_double()
+        n = C.c_long()
+        self._check(self._lib.biot_sweep_timing_get(self._h, C.byref(ms), C.byref(n)),
+                    "biot_sweep_timing_get")
+        return ms.value, n.value

@@ -1,0 +1,107 @@
+// biot_args.h -- argument blocks passed by value from the host runtime to the
+// sm_103a kernels, and the launcher declarations.  Plain structs of pointers
+// and scalars; no torch types anywhere.
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+namespace biot {
+
+enum { SIDE_BOTTOM = 0, SIDE_RIGHT = 1, SIDE_TOP = 2, SIDE_LEFT = 3 };
+enum { BC_PERIODIC = 0, BC_SYMMETRY = 1, BC_DIRICHLET = 2, BC_NEUMANN = 3 };
+enum { SWEEP_SMOOTH = 0, SWEEP_RESTRICT = 1 };
+
+// One elastic sweep on one multigrid level: either the under-relaxed smoother
+// of eq. MG:smoother, g <- (1-gamma) g + gamma ELASTIC_STEP(g - r, F~ + F_*(g)),
+// or the residual + restriction of Alg. 4 (r_c = R(g - ELASTIC_STEP(...))).
+// T is the population type of this level, TC that of the next coarser level.
+template <typename T, typename TC>
+struct SweepArgs {
+    int nx, ny;                  // cells of this level
+    const T *g;                  // iterate, 8 planes of nx*ny (ignored when zero_init)
+    T *gout;                     // smoothed iterate (SMOOTH) or nullptr (RESTRICT)
+    const T *r;                  // residual right-hand side (coarse levels) or nullptr
+    const T *Ft;                 // explicit force F~, 2 planes (finest level) or nullptr
+    const TC *gc;                // coarse correction added on load (prolongation) or nullptr
+    TC *rc;                      // restricted residual (RESTRICT) or nullptr
+    T *H[4];                     // fullway bounce-back history per Dirichlet side: 3 per wall cell
+    const double *prof[4];       // boundary data per side, 2 x (2n+1) (finest level) or nullptr
+    int bc[4];                   // displacement boundary type per side
+    int hist_valid;              // 0: first ELASTIC_STEP after a reset (use current populations)
+    int zero_init;               // 1: the iterate is identically zero (first sweep of a coarse solve)
+    int mode;                    // SWEEP_SMOOTH or SWEEP_RESTRICT
+    double gamma;                // under-relaxation
+    double om_s, om_d;           // relaxation rates of Tab. moments
+    double lm;                   // lambda^ + mu^
+    double coef_fstar;           // alpha^2 r / 2 (self-dependence force)
+    double c0h;                  // c0 * h (lattice traction per unit traction)
+    unsigned long long *resmax;  // [2] ordered bits of max|g - g**| and max|g|, or nullptr
+};
+
+// Explicit force F~ of a time step (finest level).
+template <typename T>
+struct ForceArgs {
+    int nx, ny;
+    const T *f;          // flow populations, 9 planes
+    const double *D1, *D2;  // lattice divergence at t - dt and t - 2 dt
+    const double *src;   // fluid source s (dimensional) or nullptr
+    const double *fbody; // body force f (2 planes, dimensional) or nullptr
+    T *Ft;               // output, 2 planes
+    int perx, pery;      // periodic in x / y
+    double dt, a_over_h, r, omega, alpha_h, c0h2;
+};
+
+// Divergence, effective source and pressure of the flow step (Alg. 3 setup):
+// Dt = D(g), s' of eq. source:implicit, p^ = sum f + s'/2.
+template <typename T>
+struct FlowMomentsArgs {
+    int nx, ny;
+    const T *g;          // finest-level elastic populations (final iterate)
+    const T *f;          // flow populations
+    const double *D1, *D2, *src;
+    double *P, *S;       // outputs: p^ and s' per cell
+    double *Dnew;        // output D(t) (may alias D2: read before written per cell)
+    double dt, a_over_h, r, lm;
+};
+
+// Collide + stream + boundary rules of the flow populations.
+template <typename T>
+struct FlowStreamArgs {
+    int nx, ny;
+    const T *f;
+    T *fout;
+    const double *P, *S;
+    const double *pprof[4];  // Dirichlet pressure data per side, 2n+1, or nullptr
+    int bc[4];               // pressure boundary type per side
+    double omega, c0;
+};
+
+// Physical fields of the current state.
+template <typename T>
+struct ReadoutArgs {
+    int nx, ny;
+    const T *g, *f, *Ft;
+    const double *D1, *D2, *src;
+    double *eta, *p, *sigma;  // outputs (any may be nullptr)
+    int perx, pery;
+    double dt, a_over_h, r, lm, mu_hat, coef_fstar, c0, c0h;
+};
+
+// Initial populations of eqs. ICs / ICs:moments.
+template <typename T>
+struct InitArgs {
+    int nx, ny;
+    T *f, *g;
+    const double *src, *fbody;
+    double dt, c0h2;
+};
+
+template <typename T, typename TC> cudaError_t launch_sweep(const SweepArgs<T, TC> &a, cudaStream_t s);
+template <typename T> cudaError_t launch_force(const ForceArgs<T> &a, cudaStream_t s);
+template <typename T> cudaError_t launch_flow_moments(const FlowMomentsArgs<T> &a, cudaStream_t s);
+template <typename T> cudaError_t launch_flow_stream(const FlowStreamArgs<T> &a, cudaStream_t s);
+template <typename T> cudaError_t launch_readout(const ReadoutArgs<T> &a, cudaStream_t s);
+template <typename T> cudaError_t launch_init(const InitArgs<T> &a, cudaStream_t s);
+
+}  // namespace biot

@@ -1,0 +1,101 @@
+"""CPU checks of the C-ABI library: it builds, loads, exports every function that
+include/biot.h declares, and validates arguments before touching a device.
+No compute call is made here."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "biot.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    return sorted(set(re.findall(r"^BIOT_API\s+[\w\s\*]+?\b(biot_\w+)\s*\(", text, flags=re.M)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2409_11382_gb300 import build as B
+    from paper_2409_11382_gb300 import biot
+    B.build()
+    return biot.load_library()
+
+
+def test_header_declares_the_documented_api():
+    names = declared_functions()
+    for must in ("biot_create", "biot_step", "biot_solve_to", "biot_read_u", "biot_read_p", "biot_destroy"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_binding_covers_the_header():
+    from paper_2409_11382_gb300 import biot
+    assert sorted(biot.API_FUNCTIONS) == declared_functions()
+
+
+def test_struct_layout_matches_header():
+    """ctypes mirrors of the structs have the C sizes (x86-64 / aarch64 LP64)."""
+    from paper_2409_11382_gb300 import biot
+    assert C.sizeof(biot.biot_params) == 4 * 2 + 8 * 2 + 8 * 7 + 4 * 2 + 8 * 2 + 4 * 3 + 4  # + tail padding
+    assert C.sizeof(biot.biot_side) == 24
+
+
+def _params(**kw):
+    from paper_2409_11382_gb300 import workloads as W
+    p, sides, _ = W.terzaghi_33()
+    p.update(kw)
+    return p, sides
+
+
+@pytest.mark.parametrize("bad", [
+    dict(nx=30),            # not divisible by 2^(levels-1)
+    dict(ly=2.0),           # non-square cells
+    dict(alpha=1.5),
+    dict(c0=0.0),
+    dict(gamma=0.0),
+    dict(K=0),
+    dict(r=1.5),
+    dict(levels=0),
+    dict(mu=-1.0),
+    dict(precision=7),
+])
+def test_invalid_parameters_are_rejected_before_device_use(lib, bad):
+    from paper_2409_11382_gb300 import biot
+    p, sides = _params(**bad)
+    with pytest.raises(biot.BiotError) as e:
+        biot.Solver(p, sides)
+    assert e.value.code == biot.ERR_INVALID_ARG
+
+
+def test_unpaired_periodic_side_is_rejected(lib):
+    from paper_2409_11382_gb300 import biot
+    p, sides = _params()
+    sides = [dict(s) for s in sides]
+    sides[1] = dict(eta_type=biot.PERIODIC, p_type=biot.PERIODIC)  # right periodic, left mirror
+    with pytest.raises(biot.BiotError) as e:
+        biot.Solver(p, sides)
+    assert e.value.code == biot.ERR_INVALID_ARG
+
+
+def test_missing_device_is_reported(lib):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a device is present")
+    from paper_2409_11382_gb300 import biot
+    p, sides = _params()
+    with pytest.raises(biot.BiotError) as e:
+        biot.Solver(p, sides)
+    assert e.value.code in (biot.ERR_NO_DEVICE, biot.ERR_CUDA)
+
+
+def test_error_strings(lib):
+    from paper_2409_11382_gb300 import biot
+    for code in (biot.OK, biot.ERR_INVALID_ARG, biot.ERR_DIVERGED, biot.ERR_NO_DEVICE):
+        assert lib.biot_error_string(code)
