@@ -54,9 +54,12 @@ extern "C" {
 
 /* ---- storage precision of the populations --------------------------------- */
 #define BIOT_FP64 0  /* all populations and arithmetic in FP64 (parity path) */
-#define BIOT_FP32 1  /* FP32 populations and collisions; FP64 for residual norms,
-                        the coarsest multigrid level and the divergence / pressure
-                        accumulations of the coupling */
+#define BIOT_FP32 1  /* FP32 elastic state and collisions, the displacement moments of
+                        the finest level kept as double-float (two FP32 planes); FP64
+                        for residual norms, the coarsest multigrid level and the
+                        divergence / pressure accumulations of the coupling */
+/* In both precisions the elastic state is stored as the MRT moments of the
+ * populations (an exact change of basis, eqs. moments / moments:stress). */
 
 /* ---- boundary condition types (§3.6) --------------------------------------- */
 #define BIOT_PERIODIC  0  /* wrap-around streaming; must be set on both opposite sides

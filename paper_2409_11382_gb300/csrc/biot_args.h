@@ -15,12 +15,14 @@ enum { SWEEP_SMOOTH = 0, SWEEP_RESTRICT = 1 };
 // One elastic sweep on one multigrid level: either the under-relaxed smoother
 // of eq. MG:smoother, g <- (1-gamma) g + gamma ELASTIC_STEP(g - r, F~ + F_*(g)),
 // or the residual + restriction of Alg. 4 (r_c = R(g - ELASTIC_STEP(...))).
-// T is the population type of this level, TC that of the next coarser level.
+// T is the storage type of this level, TC that of the next coarser level.
 template <typename T, typename TC>
 struct SweepArgs {
     int nx, ny;                  // cells of this level
-    const T *g;                  // iterate, 8 planes of nx*ny (ignored when zero_init)
+    const T *g;                  // iterate: 8 moment planes of nx*ny (ignored when zero_init)
     T *gout;                     // smoothed iterate (SMOOTH) or nullptr (RESTRICT)
+    const T *glo;                // low parts of m_10, m_01 (double-float, finest FP32 level) or nullptr
+    T *glo_out;                  // their update (SMOOTH) or nullptr
     const T *r;                  // residual right-hand side (coarse levels) or nullptr
     const T *Ft;                 // explicit force F~, 2 planes (finest level) or nullptr
     const TC *gc;                // coarse correction added on load (prolongation) or nullptr
@@ -57,7 +59,7 @@ struct ForceArgs {
 template <typename T>
 struct FlowMomentsArgs {
     int nx, ny;
-    const T *g;          // finest-level elastic populations (final iterate)
+    const T *g;          // finest-level elastic state (final iterate)
     const T *f;          // flow populations
     const double *D1, *D2, *src;
     double *P, *S;       // outputs: p^ and s' per cell
@@ -82,6 +84,7 @@ template <typename T>
 struct ReadoutArgs {
     int nx, ny;
     const T *g, *f, *Ft;
+    const T *glo;             // low parts of the first moments (double-float) or nullptr
     const double *D1, *D2, *src;
     double *eta, *p, *sigma;  // outputs (any may be nullptr)
     int perx, pery;
@@ -93,11 +96,12 @@ template <typename T>
 struct InitArgs {
     int nx, ny;
     T *f, *g;
+    T *glo;  // low parts of the first moments (double-float) or nullptr
     const double *src, *fbody;
     double dt, c0h2;
 };
 
-template <typename T, typename TC> cudaError_t launch_sweep(const SweepArgs<T, TC> &a, cudaStream_t s);
+template <typename T, typename TC> cudaError_t launch_sweep_mom(const SweepArgs<T, TC> &a, cudaStream_t s);
 template <typename T> cudaError_t launch_force(const ForceArgs<T> &a, cudaStream_t s);
 template <typename T> cudaError_t launch_flow_moments(const FlowMomentsArgs<T> &a, cudaStream_t s);
 template <typename T> cudaError_t launch_flow_stream(const FlowStreamArgs<T> &a, cudaStream_t s);

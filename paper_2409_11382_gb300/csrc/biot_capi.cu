@@ -43,6 +43,7 @@ struct Level {
     size_t np = 0;
     bool fp64 = true;
     void *g[2] = {nullptr, nullptr};
+    void *glo[2] = {nullptr, nullptr};  // low parts of m_10, m_01 (finest FP32 level)
     int cur = 0;
     void *r = nullptr;
     void *H[4] = {nullptr, nullptr, nullptr, nullptr};
@@ -57,7 +58,7 @@ struct biot_ctx {
     double *eta_prof[4]{}, *p_prof[4]{};  // device copies of the boundary data (finest level)
     double h = 0, lam = 0, mu = 0, kap = 0, omega = 0, om_s = 0, om_d = 0, lm = 0;
     int L = 0;
-    bool fp32 = false;
+    bool fp32 = false;  // FP32 state (finest and middle levels)
     Level lv[MAX_LEVELS];
     void *f[2]{};
     int fcur = 0;
@@ -181,6 +182,8 @@ int sweep_typed(biot_ctx *h, int l, int mode, bool zero_init, bool prolong, bool
     a.ny = Lv.ny;
     a.g = static_cast<const T *>(Lv.g[Lv.cur]);
     a.gout = (mode == SWEEP_SMOOTH) ? static_cast<T *>(Lv.g[1 - Lv.cur]) : nullptr;
+    a.glo = static_cast<const T *>(Lv.glo[Lv.cur]);
+    a.glo_out = (mode == SWEEP_SMOOTH) ? static_cast<T *>(Lv.glo[1 - Lv.cur]) : nullptr;
     a.r = fine ? nullptr : static_cast<const T *>(Lv.r);
     a.Ft = fine ? static_cast<const T *>(h->Ft) : nullptr;
     a.gc = prolong ? static_cast<const TC *>(h->lv[l - 1].g[h->lv[l - 1].cur]) : nullptr;
@@ -210,7 +213,7 @@ int sweep_typed(biot_ctx *h, int l, int mode, bool zero_init, bool prolong, bool
         }
         CUDA_TRY(cudaEventRecord(h->ev[h->ev_used], h->stream));
     }
-    CUDA_TRY((launch_sweep<T, TC>(a, h->stream)));
+    CUDA_TRY((launch_sweep_mom<T, TC>(a, h->stream)));
     if (timed) {
         CUDA_TRY(cudaEventRecord(h->ev[h->ev_used + 1], h->stream));
         h->ev_used += 2;
@@ -381,6 +384,7 @@ int init_typed(biot_ctx *h)
     a.ny = h->P.ny;
     a.f = static_cast<T *>(h->f[h->fcur]);
     a.g = static_cast<T *>(Lf.g[Lf.cur]);
+    a.glo = static_cast<T *>(Lf.glo[Lf.cur]);
     a.src = h->has_src ? h->src : nullptr;
     a.fbody = h->has_fbody ? h->fbody : nullptr;
     a.dt = h->P.dt;
@@ -411,6 +415,7 @@ int readout_typed(biot_ctx *h, double *eta, double *p, double *sigma)
     a.nx = h->P.nx;
     a.ny = h->P.ny;
     a.g = static_cast<const T *>(Lf.g[Lf.cur]);
+    a.glo = static_cast<const T *>(Lf.glo[Lf.cur]);
     a.f = static_cast<const T *>(h->f[h->fcur]);
     a.Ft = static_cast<const T *>(h->Ft);
     a.D1 = h->D1;
@@ -543,6 +548,10 @@ int biot_create(const biot_params *p, const biot_side sides[4], biot_handle *out
         const size_t esz = Lv.fp64 ? sizeof(double) : sizeof(float);
         TRY_RC(dev_alloc(h, &Lv.g[0], 8 * Lv.np * esz));
         TRY_RC(dev_alloc(h, &Lv.g[1], 8 * Lv.np * esz));
+        if (!Lv.fp64 && l == h->L - 1) {  // double-float displacement moments
+            TRY_RC(dev_alloc(h, &Lv.glo[0], 2 * Lv.np * esz));
+            TRY_RC(dev_alloc(h, &Lv.glo[1], 2 * Lv.np * esz));
+        }
         if (l < h->L - 1) TRY_RC(dev_alloc(h, &Lv.r, 8 * Lv.np * esz));
         for (int s = 0; s < 4; s++) {
             if (h->bc_eta[s] != BIOT_DIRICHLET) continue;

@@ -1,0 +1,20 @@
+// instantiate.h -- explicit specialisations of the launchers for one
+// precision; included once by each kernels_*.cu translation unit.
+#pragma once
+#include "field_kernels.cuh"
+#include "sweep_mom.cuh"
+
+#define BIOT_SWEEP_MOM(T, TC)                                                                          \
+    template <> cudaError_t biot::launch_sweep_mom<T, TC>(const biot::SweepArgs<T, TC> &a, cudaStream_t s) \
+    { return biot::launch_sweep_mom_impl<T, TC>(a, s); }
+#define BIOT_FIELDS(T)                                                                                 \
+    template <> cudaError_t biot::launch_force<T>(const biot::ForceArgs<T> &a, cudaStream_t s)           \
+    { return biot::launch_force_impl<T>(a, s); }                                                       \
+    template <> cudaError_t biot::launch_flow_stream<T>(const biot::FlowStreamArgs<T> &a, cudaStream_t s) \
+    { return biot::launch_flow_stream_impl<T>(a, s); }                                                 \
+    template <> cudaError_t biot::launch_flow_moments<T>(const biot::FlowMomentsArgs<T> &a, cudaStream_t s) \
+    { return biot::launch_flow_moments_impl<T>(a, s); }                                                \
+    template <> cudaError_t biot::launch_readout<T>(const biot::ReadoutArgs<T> &a, cudaStream_t s)       \
+    { return biot::launch_readout_impl<T>(a, s); }                                                     \
+    template <> cudaError_t biot::launch_init<T>(const biot::InitArgs<T> &a, cudaStream_t s)             \
+    { return biot::launch_init_impl<T>(a, s); }

@@ -1,7 +1,7 @@
-// FP32 instantiation of the kernels: FP32 populations and collisions; the
+// FP32 instantiation of the kernels: moment storage, FP32 collisions; the
 // coarsest multigrid level stays FP64 (float -> double level pair).
-#include "biot_kernels.cuh"
+#include "instantiate.h"
 
-BIOT_INSTANTIATE_LEVEL(float, float)
-BIOT_INSTANTIATE_LEVEL(float, double)
-BIOT_INSTANTIATE_FIELD(float)
+BIOT_SWEEP_MOM(float, float)
+BIOT_SWEEP_MOM(float, double)
+BIOT_FIELDS(float)
