@@ -41,17 +41,26 @@ struct SweepArgs {
     unsigned long long *resmax;  // [2] ordered bits of max|g - g**| and max|g|, or nullptr
 };
 
+// Explicit part of the effective source (eq. source:implicit) per cell.
+template <typename T>
+struct SexpArgs {
+    int nx, ny;
+    const double *D1, *D2;  // lattice divergence at t - dt and t - 2 dt
+    const double *src;      // fluid source s (dimensional) or nullptr
+    double *SE;             // output: dt s - (alpha/h)[(1-r)(D1 - D2) - r D1]
+    double dt, a_over_h, r;
+};
+
 // Explicit force F~ of a time step (finest level).
 template <typename T>
 struct ForceArgs {
     int nx, ny;
-    const T *f;          // flow populations, 9 planes
-    const double *D1, *D2;  // lattice divergence at t - dt and t - 2 dt
-    const double *src;   // fluid source s (dimensional) or nullptr
-    const double *fbody; // body force f (2 planes, dimensional) or nullptr
-    T *Ft;               // output, 2 planes
-    int perx, pery;      // periodic in x / y
-    double dt, a_over_h, r, omega, alpha_h, c0h2;
+    const T *f;           // flow populations, 9 planes
+    const double *SE;     // explicit source (SexpArgs output)
+    const double *fbody;  // body force f (2 planes, dimensional) or nullptr
+    T *Ft;                // output, 2 planes
+    int perx, pery;       // periodic in x / y
+    double omega, alpha_h, c0h2;
 };
 
 // Divergence, effective source and pressure of the flow step (Alg. 3 setup):
@@ -62,7 +71,7 @@ struct FlowMomentsArgs {
     const T *g;          // finest-level elastic state (final iterate)
     const T *f;          // flow populations
     const double *D1, *D2, *src;
-    double *P, *S;       // outputs: p^ and s' per cell
+    T *P, *S;            // outputs: p^ and s' per cell (population precision)
     double *Dnew;        // output D(t) (may alias D2: read before written per cell)
     double dt, a_over_h, r, lm;
 };
@@ -73,7 +82,7 @@ struct FlowStreamArgs {
     int nx, ny;
     const T *f;
     T *fout;
-    const double *P, *S;
+    const T *P, *S;
     const double *pprof[4];  // Dirichlet pressure data per side, 2n+1, or nullptr
     int bc[4];               // pressure boundary type per side
     double omega, c0;
@@ -102,6 +111,7 @@ struct InitArgs {
 };
 
 template <typename T, typename TC> cudaError_t launch_sweep_mom(const SweepArgs<T, TC> &a, cudaStream_t s);
+template <typename T> cudaError_t launch_sexp(const SexpArgs<T> &a, cudaStream_t s);
 template <typename T> cudaError_t launch_force(const ForceArgs<T> &a, cudaStream_t s);
 template <typename T> cudaError_t launch_flow_moments(const FlowMomentsArgs<T> &a, cudaStream_t s);
 template <typename T> cudaError_t launch_flow_stream(const FlowStreamArgs<T> &a, cudaStream_t s);

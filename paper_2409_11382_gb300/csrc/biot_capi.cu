@@ -62,7 +62,8 @@ struct biot_ctx {
     Level lv[MAX_LEVELS];
     void *f[2]{};
     int fcur = 0;
-    double *D1 = nullptr, *D2 = nullptr, *Pp = nullptr, *Ss = nullptr;
+    double *D1 = nullptr, *D2 = nullptr, *SE = nullptr;
+    void *Pp = nullptr, *Ss = nullptr;  // p^ and s' of the flow step (population type)
     void *Ft = nullptr;
     double *src = nullptr, *fbody = nullptr;
     bool has_src = false, has_fbody = false;
@@ -80,6 +81,11 @@ struct biot_ctx {
     int diverged = 0;
     long launches = 0;
     size_t bytes = 0;
+    // CUDA graphs of one time step (flow step + elastic solve) in fixed-cycle
+    // mode, one per parity of the flow ping-pong buffer
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    long graph_launches[2] = {0, 0};
+    bool use_graphs = true;
     // instrumentation of the finest-level smoothing sweep
     bool timing = false;
     std::vector<cudaEvent_t> ev;
@@ -255,25 +261,31 @@ int vcycle(biot_ctx *h, int l, bool zero_start)
 template <typename T>
 int force_typed(biot_ctx *h)
 {
+    SexpArgs<T> e{};
+    e.nx = h->P.nx;
+    e.ny = h->P.ny;
+    e.D1 = h->D1;
+    e.D2 = h->D2;
+    e.src = h->has_src ? h->src : nullptr;
+    e.SE = h->SE;
+    e.dt = h->P.dt;
+    e.a_over_h = h->P.alpha / h->h;
+    e.r = h->P.r_coupling;
+    CUDA_TRY(launch_sexp<T>(e, h->stream));
     ForceArgs<T> a{};
     a.nx = h->P.nx;
     a.ny = h->P.ny;
     a.f = static_cast<const T *>(h->f[h->fcur]);
-    a.D1 = h->D1;
-    a.D2 = h->D2;
-    a.src = h->has_src ? h->src : nullptr;
+    a.SE = h->SE;
     a.fbody = h->has_fbody ? h->fbody : nullptr;
     a.Ft = static_cast<T *>(h->Ft);
     a.perx = h->bc_eta[BIOT_LEFT] == BIOT_PERIODIC;
     a.pery = h->bc_eta[BIOT_BOTTOM] == BIOT_PERIODIC;
-    a.dt = h->P.dt;
-    a.a_over_h = h->P.alpha / h->h;
-    a.r = h->P.r_coupling;
     a.omega = h->omega;
     a.alpha_h = h->P.alpha * h->h;
     a.c0h2 = h->P.c0 * h->h * h->h;
     CUDA_TRY(launch_force<T>(a, h->stream));
-    h->launches++;
+    h->launches += 2;
     return BIOT_OK;
 }
 
@@ -344,8 +356,8 @@ int flow_typed(biot_ctx *h)
     m.D1 = h->D1;
     m.D2 = h->D2;
     m.src = h->has_src ? h->src : nullptr;
-    m.P = h->Pp;
-    m.S = h->Ss;
+    m.P = static_cast<T *>(h->Pp);
+    m.S = static_cast<T *>(h->Ss);
     m.Dnew = h->D2;  // D(t) overwrites D(t - 2 dt) cell by cell after it was read
     m.dt = h->P.dt;
     m.a_over_h = h->P.alpha / h->h;
@@ -360,8 +372,8 @@ int flow_typed(biot_ctx *h)
     s.ny = h->P.ny;
     s.f = static_cast<const T *>(h->f[h->fcur]);
     s.fout = static_cast<T *>(h->f[1 - h->fcur]);
-    s.P = h->Pp;
-    s.S = h->Ss;
+    s.P = static_cast<const T *>(h->Pp);
+    s.S = static_cast<const T *>(h->Ss);
     for (int i = 0; i < 4; i++) {
         s.pprof[i] = h->p_prof[i];
         s.bc[i] = h->bc_p[i];
@@ -464,10 +476,73 @@ int readout(biot_ctx *h, double *eta_host, double *p_host, double *sigma_host)
     return BIOT_OK;
 }
 
+void drop_graphs(biot_ctx *h)
+{
+    for (int i = 0; i < 2; i++) {
+        if (h->graph[i]) cudaGraphExecDestroy(h->graph[i]);
+        h->graph[i] = nullptr;
+    }
+}
+
+// One iteration of the time loop of Alg. 5 from a solved state: flow step to
+// t + dt, then the elastic solve at t + dt.
+int advance(biot_ctx *h)
+{
+    int rc = h->fp32 ? flow_typed<float>(h) : flow_typed<double>(h);
+    if (rc) return rc;
+    h->solved = false;
+    rc = elastic_solve(h);
+    return rc;
+}
+
+// advance() through a captured CUDA graph (fixed number of V-cycles: the
+// launch sequence and every buffer parity repeat from step to step except the
+// flow ping-pong, hence one graph per parity).
+int advance_graph(biot_ctx *h)
+{
+    const int par = h->fcur;
+    if (!h->graph[par]) {
+        const long l0 = h->launches, c0 = h->total_cycles;
+        CUDA_TRY(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+        int rc = advance(h);
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamEndCapture(h->stream, &g);
+        if (rc) {
+            if (g) cudaGraphDestroy(g);
+            return rc;
+        }
+        if (e != cudaSuccess) return fail(BIOT_ERR_CUDA, std::string("cudaStreamEndCapture: ") + cudaGetErrorString(e));
+        e = cudaGraphInstantiate(&h->graph[par], g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            h->graph[par] = nullptr;
+            return fail(BIOT_ERR_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+        }
+        h->graph_launches[par] = h->launches - l0;
+        h->launches = l0;
+        h->total_cycles = c0;
+        // capture recorded the state transitions; replay them from the start state
+        h->fcur ^= 1;
+        std::swap(h->D1, h->D2);
+        h->nstep -= 1;
+    }
+    CUDA_TRY(cudaGraphLaunch(h->graph[par], h->stream));
+    h->launches += h->graph_launches[par];
+    h->fcur ^= 1;
+    std::swap(h->D1, h->D2);
+    h->nstep += 1;
+    h->total_cycles += h->P.ne_fixed;
+    h->last_ne = h->P.ne_fixed;
+    h->solved = true;
+    h->pending_res = true;
+    return BIOT_OK;
+}
+
 void release(biot_ctx *h)
 {
     if (!h) return;
     if (h->stream) cudaStreamSynchronize(h->stream);
+    drop_graphs(h);
     for (void *p : h->allocs) cudaFree(p);
     h->allocs.clear();
     if (h->resmax_host) cudaFreeHost(h->resmax_host);
@@ -564,8 +639,9 @@ int biot_create(const biot_params *p, const biot_side sides[4], biot_handle *out
     TRY_RC(dev_alloc(h, &h->Ft, 2 * np * tsz));
     TRY_RC(dev_alloc(h, (void **)&h->D1, np * sizeof(double)));
     TRY_RC(dev_alloc(h, (void **)&h->D2, np * sizeof(double)));
-    TRY_RC(dev_alloc(h, (void **)&h->Pp, np * sizeof(double)));
-    TRY_RC(dev_alloc(h, (void **)&h->Ss, np * sizeof(double)));
+    TRY_RC(dev_alloc(h, (void **)&h->SE, np * sizeof(double)));
+    TRY_RC(dev_alloc(h, &h->Pp, np * tsz));
+    TRY_RC(dev_alloc(h, &h->Ss, np * tsz));
     TRY_RC(dev_alloc(h, (void **)&h->resmax, 2 * sizeof(unsigned long long)));
     if (cudaMallocHost((void **)&h->resmax_host, 2 * sizeof(unsigned long long)) != cudaSuccess) {
         cudaGetLastError();
@@ -609,6 +685,7 @@ int biot_set_sources(biot_handle h, const double *f_body, const double *s)
     }
     h->has_src = s != nullptr;
     CUDA_TRY(cudaStreamSynchronize(h->stream));
+    drop_graphs(h);
     h->solved = false;
     return BIOT_OK;
 }
@@ -618,6 +695,7 @@ int biot_set_side_profile(biot_handle h, int side, const double *eta_profile, co
     if (!h || side < 0 || side > 3) return fail(BIOT_ERR_INVALID_ARG, "bad handle or side");
     int rc = set_profiles(h, side, eta_profile, p_profile);
     if (rc) return rc;
+    drop_graphs(h);
     h->solved = false;
     return BIOT_OK;
 }
@@ -628,19 +706,17 @@ int biot_step(biot_handle h, int n)
     if (h->diverged) return fail(BIOT_ERR_DIVERGED, "instance has diverged");
     int rc, status = BIOT_OK;
     if ((rc = ensure_initialized(h))) return rc;
-    for (int i = 0; i < n; i++) {
-        if (!h->solved) {
-            rc = elastic_solve(h);
-            if (rc == BIOT_ERR_NOT_CONVERGED) status = rc;
-            else if (rc) return rc;
-        }
-        if ((rc = finish_pending(h))) return rc;
-        rc = h->fp32 ? flow_typed<float>(h) : flow_typed<double>(h);
-        if (rc) return rc;
-        h->solved = false;
-    }
     if (!h->solved) {
         rc = elastic_solve(h);
+        if (rc == BIOT_ERR_NOT_CONVERGED) status = rc;
+        else if (rc) return rc;
+    }
+    // with a fixed number of V-cycles nothing is read back until the end: a
+    // diverged state stays non-finite, so the last residual reveals it
+    const bool graphs = h->P.ne_fixed > 0 && h->use_graphs && !h->timing;
+    for (int i = 0; i < n; i++) {
+        if (h->P.ne_fixed <= 0 && (rc = finish_pending(h))) return rc;
+        rc = graphs ? advance_graph(h) : advance(h);
         if (rc == BIOT_ERR_NOT_CONVERGED) status = rc;
         else if (rc) return rc;
     }

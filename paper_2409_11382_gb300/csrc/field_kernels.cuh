@@ -7,20 +7,31 @@
 namespace biot {
 
 // ---------------------------------------------------------------------------
-// Explicit force of a time step:
-//   F~ = c0 h^2 f - alpha h [ -3 omega sum_i f_i c_i + 1/2 grad^c s'_exp ]
-// with s'_exp = dt s - (alpha/h)[(1-r)(D1 - D2) - r D1] (eqs. pressure:gradient,
-// source:implicit; the iterate-dependent part is added in the sweep).
+// Explicit part of eq. source:implicit in lattice units (FP64):
+//   s'_exp = dt s - (alpha/h)[(1-r)(D1 - D2) - r D1]
+// (the iterate-dependent part -(alpha r/h) D(g) is added in the sweep).
 // ---------------------------------------------------------------------------
 template <typename T>
-__device__ __forceinline__ double sexp_at(const ForceArgs<T> &a, int x, int y)
+__global__ void __launch_bounds__(256) k_sexp(const SexpArgs<T> a)
+{
+    const size_t NP = (size_t)a.nx * a.ny;
+    const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= NP) return;
+    const double d1 = a.D1[idx], d2 = a.D2[idx];
+    const double s = a.src ? a.dt * a.src[idx] : 0.0;
+    a.SE[idx] = s - a.a_over_h * ((1.0 - a.r) * (d1 - d2) - a.r * d1);
+}
+
+// Explicit force of a time step:
+//   F~ = c0 h^2 f - alpha h [ -3 omega sum_i f_i c_i + 1/2 grad^c s'_exp ]
+// (eqs. pressure:gradient and pressure:gradient:alternative).  The stencil
+// differences of s'_exp are taken in FP64, the rest in the population type.
+template <typename T>
+__device__ __forceinline__ double se_at(const ForceArgs<T> &a, int x, int y)
 {
     if (a.perx) x = wrapi(x, a.nx); else x = clampi(x, a.nx);
     if (a.pery) y = wrapi(y, a.ny); else y = clampi(y, a.ny);
-    const size_t idx = (size_t)y * a.nx + x;
-    const double d1 = a.D1[idx], d2 = a.D2[idx];
-    const double s = a.src ? a.dt * a.src[idx] : 0.0;
-    return s - a.a_over_h * ((1.0 - a.r) * (d1 - d2) - a.r * d1);
+    return a.SE[(size_t)y * a.nx + x];
 }
 
 template <typename T>
@@ -30,28 +41,26 @@ __global__ void __launch_bounds__(256) k_force(const ForceArgs<T> a)
     const int y = blockIdx.y * 8 + (threadIdx.x >> 5);
     if (x >= a.nx || y >= a.ny) return;
     const size_t NP = (size_t)a.nx * a.ny, idx = (size_t)y * a.nx + x;
-    double jx = 0.0, jy = 0.0;
+    T f[9];
 #pragma unroll
-    for (int i = 1; i < 9; i++) {
-        const double fi = (double)a.f[i * NP + idx];
-        if (ex9(i)) jx += ex9(i) * fi;
-        if (ey9(i)) jy += ey9(i) * fi;
-    }
-    const double sE = sexp_at(a, x + 1, y), sW = sexp_at(a, x - 1, y);
-    const double sN = sexp_at(a, x, y + 1), sS = sexp_at(a, x, y - 1);
-    const double sNE = sexp_at(a, x + 1, y + 1), sNW = sexp_at(a, x - 1, y + 1);
-    const double sSE = sexp_at(a, x + 1, y - 1), sSW = sexp_at(a, x - 1, y - 1);
-    const double gsx = (sE - sW) / 3.0 + ((sNE + sSE) - (sNW + sSW)) / 12.0;
-    const double gsy = (sN - sS) / 3.0 + ((sNE + sNW) - (sSE + sSW)) / 12.0;
-    const double gpx = -3.0 * a.omega * jx + 0.5 * gsx;
-    const double gpy = -3.0 * a.omega * jy + 0.5 * gsy;
-    double fx = -a.alpha_h * gpx, fy = -a.alpha_h * gpy;
+    for (int i = 1; i < 9; i++) f[i] = a.f[i * NP + idx];
+    const T jx = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
+    const T jy = (f[2] - f[4]) + (f[5] + f[6]) - (f[7] + f[8]);
+    const double sE = se_at(a, x + 1, y), sW = se_at(a, x - 1, y);
+    const double sN = se_at(a, x, y + 1), sS = se_at(a, x, y - 1);
+    const double sNE = se_at(a, x + 1, y + 1), sNW = se_at(a, x - 1, y + 1);
+    const double sSE = se_at(a, x + 1, y - 1), sSW = se_at(a, x - 1, y - 1);
+    const T gx_ = T(sE - sW) * T(1.0 / 3.0) + (T(sNE - sNW) + T(sSE - sSW)) * T(1.0 / 12.0);
+    const T gy_ = T(sN - sS) * T(1.0 / 3.0) + (T(sNE - sSE) + T(sNW - sSW)) * T(1.0 / 12.0);
+    const T gpx = T(-3.0 * a.omega) * jx + T(0.5) * gx_;
+    const T gpy = T(-3.0 * a.omega) * jy + T(0.5) * gy_;
+    T fx = T(-a.alpha_h) * gpx, fy = T(-a.alpha_h) * gpy;
     if (a.fbody) {
-        fx += a.c0h2 * a.fbody[idx];
-        fy += a.c0h2 * a.fbody[NP + idx];
+        fx += T(a.c0h2 * a.fbody[idx]);
+        fy += T(a.c0h2 * a.fbody[NP + idx]);
     }
-    a.Ft[idx] = (T)fx;
-    a.Ft[NP + idx] = (T)fy;
+    a.Ft[idx] = fx;
+    a.Ft[NP + idx] = fy;
 }
 
 // ---------------------------------------------------------------------------
@@ -68,11 +77,11 @@ __global__ void __launch_bounds__(256) k_flow_moments(const FlowMomentsArgs<T> a
     const double d1 = a.D1[idx], d2 = a.D2[idx];
     const double s0 = a.src ? a.dt * a.src[idx] : 0.0;
     const double sp = s0 - a.a_over_h * ((1.0 - a.r) * (d1 - d2) + a.r * (dt_ - d1));
-    double sum = 0.0;
+    T sum = T(0);
 #pragma unroll
-    for (int i = 0; i < 9; i++) sum += (double)a.f[i * NP + idx];
-    a.P[idx] = sum + 0.5 * sp;
-    a.S[idx] = sp;
+    for (int i = 0; i < 9; i++) sum += a.f[i * NP + idx];
+    a.P[idx] = T((double)sum + 0.5 * sp);
+    a.S[idx] = T(sp);
     a.Dnew[idx] = dt_;
 }
 
@@ -85,7 +94,7 @@ __device__ __forceinline__ T flow_post(const FlowStreamArgs<T> &a, size_t NP, si
     const T om = T(a.omega);
     const T fi = a.f[(size_t)i * NP + idx];
     const T wi = T(w9(i));
-    return fi - om * (fi - wi * T(a.P[idx])) + (T(1) - T(0.5) * om) * wi * T(a.S[idx]);
+    return fi - om * (fi - wi * a.P[idx]) + (T(1) - T(0.5) * om) * wi * a.S[idx];
 }
 
 template <typename T>
@@ -228,6 +237,14 @@ __global__ void __launch_bounds__(256) k_init(const InitArgs<T> a)
 // ---------------------------------------------------------------------------
 // Launchers.
 // ---------------------------------------------------------------------------
+template <typename T>
+cudaError_t launch_sexp_impl(const SexpArgs<T> &a, cudaStream_t s)
+{
+    const size_t n = (size_t)a.nx * a.ny;
+    k_sexp<T><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t launch_force_impl(const ForceArgs<T> &a, cudaStream_t s)
 {

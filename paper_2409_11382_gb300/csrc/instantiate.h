@@ -8,6 +8,8 @@
     template <> cudaError_t biot::launch_sweep_mom<T, TC>(const biot::SweepArgs<T, TC> &a, cudaStream_t s) \
     { return biot::launch_sweep_mom_impl<T, TC>(a, s); }
 #define BIOT_FIELDS(T)                                                                                 \
+    template <> cudaError_t biot::launch_sexp<T>(const biot::SexpArgs<T> &a, cudaStream_t s)             \
+    { return biot::launch_sexp_impl<T>(a, s); }                                                        \
     template <> cudaError_t biot::launch_force<T>(const biot::ForceArgs<T> &a, cudaStream_t s)           \
     { return biot::launch_force_impl<T>(a, s); }                                                       \
     template <> cudaError_t biot::launch_flow_stream<T>(const biot::FlowStreamArgs<T> &a, cudaStream_t s) \
