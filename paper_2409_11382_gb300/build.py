@@ -22,7 +22,7 @@ LIB = os.path.join(HERE, "libbiot_gb300.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
-          f"-I{INCLUDE}", f"-I{CSRC}", "--expt-relaxed-constexpr"]
+          f"-I{INCLUDE}", f"-I{CSRC}", "--expt-relaxed-constexpr", "-Xcompiler", "-ffp-contract=off"]
 
 # translation unit -> extra flags
 UNITS = {

@@ -39,6 +39,12 @@ struct SweepArgs {
     double coef_fstar;           // alpha^2 r / 2 (self-dependence force)
     double c0h;                  // c0 * h (lattice traction per unit traction)
     unsigned long long *resmax;  // [2] ordered bits of max|g - g**| and max|g|, or nullptr
+    // the same coefficients, evaluated once on the host in the storage type:
+    T k_fs;   // coef_fstar * dD/dm_s = -(alpha^2 r / 2) * 3 / (2 (3 lm + 1))
+    T k_ws;   // 1 - om_s
+    T k_wd;   // 1 - om_d
+    T k_22;   // -1 / (12 lm + 4)   (eq. moments:collision:22)
+    T k_gam;  // gamma
 };
 
 // Explicit part of the effective source (eq. source:implicit) per cell.
@@ -61,6 +67,7 @@ struct ForceArgs {
     T *Ft;                // output, 2 planes
     int perx, pery;       // periodic in x / y
     double omega, alpha_h, c0h2;
+    T k_m3w, k_mah;       // -3 omega and -alpha h in the storage type (host-evaluated)
 };
 
 // Divergence, effective source and pressure of the flow step (Alg. 3 setup):
@@ -73,7 +80,10 @@ struct FlowMomentsArgs {
     const double *D1, *D2, *src;
     T *P, *S;            // outputs: p^ and s' per cell (population precision)
     double *Dnew;        // output D(t) (may alias D2: read before written per cell)
+    double *SEnext;      // output: explicit source of the next step (SexpArgs formula with
+                         // D1 -> D(t), D2 -> D(t - dt)), or nullptr
     double dt, a_over_h, r, lm;
+    double kD;           // dD/dm_s = -3 / (2 (3 lm + 1)) (host-evaluated)
 };
 
 // Collide + stream + boundary rules of the flow populations.
@@ -86,6 +96,7 @@ struct FlowStreamArgs {
     const double *pprof[4];  // Dirichlet pressure data per side, 2n+1, or nullptr
     int bc[4];               // pressure boundary type per side
     double omega, c0;
+    T k_om, k_src;           // omega and 1 - omega/2 in the storage type (host-evaluated)
 };
 
 // Physical fields of the current state.
@@ -98,6 +109,7 @@ struct ReadoutArgs {
     double *eta, *p, *sigma;  // outputs (any may be nullptr)
     int perx, pery;
     double dt, a_over_h, r, lm, mu_hat, coef_fstar, c0, c0h;
+    double kD;  // dD/dm_s = -3 / (2 (3 lm + 1)) (host-evaluated)
 };
 
 // Initial populations of eqs. ICs / ICs:moments.

@@ -4,7 +4,8 @@
 // populations, coupling history) and drives Alg. 5: per time step the explicit
 // force, N_E V-cycles of Alg. 4 built from fused elastic sweeps, then the
 // flow step of Alg. 3.  Every arithmetic step runs in the sm_103a kernels of
-// biot_kernels.cuh; this file only sequences launches and copies.
+// sweep_mom.cuh and field_kernels.cuh; this file only sequences launches and
+// copies, and evaluates the per-instance coefficients once on the host.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -73,6 +74,7 @@ struct biot_ctx {
     cudaStream_t stream = nullptr, own_stream = nullptr;
     long nstep = 0;
     bool solved = false, initialized = false, pending_res = false;
+    bool se_stale = true;  // SE must be recomputed from D1, D2 (else the last flow step wrote it)
     // statistics
     int last_ne = 0;
     double last_res = 0;
@@ -209,6 +211,11 @@ int sweep_typed(biot_ctx *h, int l, int mode, bool zero_init, bool prolong, bool
     a.coef_fstar = 0.5 * h->P.alpha * h->P.alpha * h->P.r_coupling;
     a.c0h = h->P.c0 * h->h;
     a.resmax = want_res ? h->resmax : nullptr;
+    a.k_fs = T(a.coef_fstar * (-1.5 / (3.0 * a.lm + 1.0)));
+    a.k_ws = T(1.0 - a.om_s);
+    a.k_wd = T(1.0 - a.om_d);
+    a.k_22 = T(-1.0 / (12.0 * a.lm + 4.0));
+    a.k_gam = T(a.gamma);
 
     const bool timed = h->timing && fine && mode == SWEEP_SMOOTH;
     if (timed) {
@@ -271,7 +278,11 @@ int force_typed(biot_ctx *h)
     e.dt = h->P.dt;
     e.a_over_h = h->P.alpha / h->h;
     e.r = h->P.r_coupling;
-    CUDA_TRY(launch_sexp<T>(e, h->stream));
+    if (h->se_stale) {
+        CUDA_TRY(launch_sexp<T>(e, h->stream));
+        h->launches++;
+        h->se_stale = false;
+    }
     ForceArgs<T> a{};
     a.nx = h->P.nx;
     a.ny = h->P.ny;
@@ -284,8 +295,10 @@ int force_typed(biot_ctx *h)
     a.omega = h->omega;
     a.alpha_h = h->P.alpha * h->h;
     a.c0h2 = h->P.c0 * h->h * h->h;
+    a.k_m3w = T(-3.0 * a.omega);
+    a.k_mah = T(-a.alpha_h);
     CUDA_TRY(launch_force<T>(a, h->stream));
-    h->launches += 2;
+    h->launches++;
     return BIOT_OK;
 }
 
@@ -363,7 +376,10 @@ int flow_typed(biot_ctx *h)
     m.a_over_h = h->P.alpha / h->h;
     m.r = h->P.r_coupling;
     m.lm = h->lm;
+    m.kD = -1.5 / (3.0 * h->lm + 1.0);
+    m.SEnext = h->SE;  // the explicit source of the next elastic solve
     CUDA_TRY(launch_flow_moments<T>(m, h->stream));
+    h->se_stale = false;
     h->launches++;
     std::swap(h->D1, h->D2);  // D1 <- D(t), D2 <- D(t - dt)
 
@@ -380,6 +396,8 @@ int flow_typed(biot_ctx *h)
     }
     s.omega = h->omega;
     s.c0 = h->P.c0;
+    s.k_om = T(h->omega);
+    s.k_src = T(1.0 - 0.5 * h->omega);
     CUDA_TRY(launch_flow_stream<T>(s, h->stream));
     h->launches++;
     h->fcur ^= 1;
@@ -446,6 +464,7 @@ int readout_typed(biot_ctx *h, double *eta, double *p, double *sigma)
     a.coef_fstar = 0.5 * h->P.alpha * h->P.alpha * h->P.r_coupling;
     a.c0 = h->P.c0;
     a.c0h = h->P.c0 * h->h;
+    a.kD = -1.5 / (3.0 * h->lm + 1.0);
     CUDA_TRY(launch_readout<T>(a, h->stream));
     h->launches++;
     return BIOT_OK;
@@ -684,6 +703,7 @@ int biot_set_sources(biot_handle h, const double *f_body, const double *s)
         CUDA_TRY(cudaMemcpyAsync(h->src, s, np * sizeof(double), cudaMemcpyHostToDevice, h->stream));
     }
     h->has_src = s != nullptr;
+    h->se_stale = true;
     CUDA_TRY(cudaStreamSynchronize(h->stream));
     drop_graphs(h);
     h->solved = false;

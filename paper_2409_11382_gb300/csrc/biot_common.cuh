@@ -114,19 +114,20 @@ __device__ __forceinline__ void pairs_to_moments(const T (&S)[4], const T (&A)[4
     m[6] = A[2] + A[3];
     m[7] = S[2] + S[3];
 }
-// max |g_k| over the populations of a moment vector (NaN -> +inf).
+// max |g_k| over the populations of a moment vector (NaN -> +inf), in the
+// storage type (a maximum is exact in any precision).
 template <typename T>
-__device__ __forceinline__ double pop_absmax(const T (&m)[8])
+__device__ __forceinline__ T pop_absmax(const T (&m)[8])
 {
     T S[4], A[4];
     moments_to_pairs(m, S, A);
-    double r = 0.0;
+    T r = T(0);
 #pragma unroll
     for (int p = 0; p < 4; p++) {
-        const double u = fabs((double)(T(0.5) * (S[p] + A[p])));
-        const double v = fabs((double)(T(0.5) * (S[p] - A[p])));
-        r = fmax(r, (u == u) ? u : (double)INFINITY);
-        r = fmax(r, (v == v) ? v : (double)INFINITY);
+        const T u = fabs(T(0.5) * (S[p] + A[p]));
+        const T v = fabs(T(0.5) * (S[p] - A[p]));
+        r = fmax(r, (u == u) ? u : T(INFINITY));
+        r = fmax(r, (v == v) ? v : T(INFINITY));
     }
     return r;
 }

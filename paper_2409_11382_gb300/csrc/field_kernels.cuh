@@ -52,9 +52,9 @@ __global__ void __launch_bounds__(256) k_force(const ForceArgs<T> a)
     const double sSE = se_at(a, x + 1, y - 1), sSW = se_at(a, x - 1, y - 1);
     const T gx_ = T(sE - sW) * T(1.0 / 3.0) + (T(sNE - sNW) + T(sSE - sSW)) * T(1.0 / 12.0);
     const T gy_ = T(sN - sS) * T(1.0 / 3.0) + (T(sNE - sSE) + T(sNW - sSW)) * T(1.0 / 12.0);
-    const T gpx = T(-3.0 * a.omega) * jx + T(0.5) * gx_;
-    const T gpy = T(-3.0 * a.omega) * jy + T(0.5) * gy_;
-    T fx = T(-a.alpha_h) * gpx, fy = T(-a.alpha_h) * gpy;
+    const T gpx = a.k_m3w * jx + T(0.5) * gx_;
+    const T gpy = a.k_m3w * jy + T(0.5) * gy_;
+    T fx = a.k_mah * gpx, fy = a.k_mah * gpy;
     if (a.fbody) {
         fx += T(a.c0h2 * a.fbody[idx]);
         fy += T(a.c0h2 * a.fbody[NP + idx]);
@@ -73,7 +73,7 @@ __global__ void __launch_bounds__(256) k_flow_moments(const FlowMomentsArgs<T> a
     const size_t NP = (size_t)a.nx * a.ny;
     const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= NP) return;
-    const double dt_ = -1.5 / (3.0 * a.lm + 1.0) * (double)a.g[3 * NP + idx];
+    const double dt_ = a.kD * (double)a.g[3 * NP + idx];
     const double d1 = a.D1[idx], d2 = a.D2[idx];
     const double s0 = a.src ? a.dt * a.src[idx] : 0.0;
     const double sp = s0 - a.a_over_h * ((1.0 - a.r) * (d1 - d2) + a.r * (dt_ - d1));
@@ -83,6 +83,8 @@ __global__ void __launch_bounds__(256) k_flow_moments(const FlowMomentsArgs<T> a
     a.P[idx] = T((double)sum + 0.5 * sp);
     a.S[idx] = T(sp);
     a.Dnew[idx] = dt_;
+    // explicit source of the next time step, from D(t) and D(t - dt) (k_sexp's formula)
+    if (a.SEnext) a.SEnext[idx] = s0 - a.a_over_h * ((1.0 - a.r) * (dt_ - d1) - a.r * dt_);
 }
 
 // Flow step, part 2: BGK collision with source (eqs. pressure:equilibrium,
@@ -91,10 +93,10 @@ __global__ void __launch_bounds__(256) k_flow_moments(const FlowMomentsArgs<T> a
 template <typename T>
 __device__ __forceinline__ T flow_post(const FlowStreamArgs<T> &a, size_t NP, size_t idx, int i)
 {
-    const T om = T(a.omega);
+    const T om = a.k_om;
     const T fi = a.f[(size_t)i * NP + idx];
     const T wi = T(w9(i));
-    return fi - om * (fi - wi * a.P[idx]) + (T(1) - T(0.5) * om) * wi * a.S[idx];
+    return fi - om * (fi - wi * a.P[idx]) + a.k_src * wi * a.S[idx];
 }
 
 template <typename T>
@@ -161,7 +163,7 @@ __device__ __forceinline__ double div_at(const ReadoutArgs<T> &a, int x, int y)
     if (a.perx) x = wrapi(x, a.nx); else x = clampi(x, a.nx);
     if (a.pery) y = wrapi(y, a.ny); else y = clampi(y, a.ny);
     const size_t NP = (size_t)a.nx * a.ny;
-    return -1.5 / (3.0 * a.lm + 1.0) * (double)a.g[3 * NP + (size_t)y * a.nx + x];
+    return a.kD * (double)a.g[3 * NP + (size_t)y * a.nx + x];
 }
 
 template <typename T>
@@ -200,7 +202,7 @@ __global__ void __launch_bounds__(256) k_readout(const ReadoutArgs<T> a)
         a.sigma[2 * NP + idx] = sc * (mbs - mbd);
     }
     if (a.p) {
-        const double dt_ = -1.5 / (3.0 * a.lm + 1.0) * ms;
+        const double dt_ = a.kD * ms;
         const double d1 = a.D1[idx], d2 = a.D2[idx];
         const double s0 = a.src ? a.dt * a.src[idx] : 0.0;
         const double sp = s0 - a.a_over_h * ((1.0 - a.r) * (d1 - d2) + a.r * (dt_ - d1));

@@ -141,7 +141,7 @@ __device__ __forceinline__ void collide_cell(const SweepArgs<T, TC> &a, const Ri
     T m0 = rg.R(s, 0, c), m1 = rg.R(s, 1, c), m2 = rg.R(s, 2, c), m3 = rg.R(s, 3, c), m4 = rg.R(s, 4, c);
     const T dE = rg.R(s, 3, c + 1), dW = rg.R(s, 3, c - 1), dN = rg.R(sp, 3, c), dS = rg.R(sm, 3, c);
     const T dNE = rg.R(sp, 3, c + 1), dNW = rg.R(sp, 3, c - 1), dSE = rg.R(sm, 3, c + 1), dSW = rg.R(sm, 3, c - 1);
-    const T cf = T(a.coef_fstar * (-1.5 / (3.0 * a.lm + 1.0)));  // alpha^2 r/2 * dD/dm_s
+    const T cf = a.k_fs;  // alpha^2 r/2 * dD/dm_s
     T Fx = cf * ((dE - dW) * T(1.0 / 3.0) + ((dNE + dSE) - (dNW + dSW)) * T(1.0 / 12.0));
     T Fy = cf * ((dN - dS) * T(1.0 / 3.0) + ((dNE + dNW) - (dSE + dSW)) * T(1.0 / 12.0));
     if (KIND == KIND_FINE) {
@@ -154,8 +154,8 @@ __device__ __forceinline__ void collide_cell(const SweepArgs<T, TC> &a, const Ri
         m3 -= rg.R(s, L::XV + 3, c);
         m4 -= rg.R(s, L::XV + 4, c);
     }
-    const T one_m_ws = T(1.0 - a.om_s), one_m_wd = T(1.0 - a.om_d);
-    const T c22 = T(-1.0 / (12.0 * a.lm + 4.0));
+    const T one_m_ws = a.k_ws, one_m_wd = a.k_wd;
+    const T c22 = a.k_22;
     const T ms = one_m_ws * m3, md = one_m_wd * m4, m11 = one_m_wd * m2, m22 = c22 * m3;
     rg.P(s, 0, c) = T(0.5) * (ms + md) - m22;
     rg.P(s, 1, c) = T(0.5) * (ms - md) - m22;
@@ -393,11 +393,11 @@ __global__ void __launch_bounds__(NT) k_sweep_mom(const SweepArgs<T, TC> a, int 
     collide_row(y0);
     __syncthreads();
 
-    double rmax = 0.0, gmax = 0.0;
+    T rmax = T(0), gmax = T(0);
     T acc[8];
 #pragma unroll
     for (int k = 0; k < 8; k++) acc[k] = T(0);
-    const T gam = T(a.gamma);
+    const T gam = a.k_gam;
 
     for (int y = y0; y < y1; y++) {
         store_row(y + 2);  // (A) prefetched row y+2 -> raw ring
@@ -471,8 +471,8 @@ __global__ void __launch_bounds__(NT) k_sweep_mom(const SweepArgs<T, TC> a, int 
         }
         const int warp = t >> 5, lane = t & 31;
         if (lane == 0) {
-            red[0][warp] = rmax;
-            red[1][warp] = gmax;
+            red[0][warp] = (double)rmax;
+            red[1][warp] = (double)gmax;
         }
         __syncthreads();
         if (t == 0) {
