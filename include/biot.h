@@ -190,6 +190,32 @@ BIOT_API const char *biot_last_error(void);
 BIOT_API int biot_sweep_timing(biot_handle h, int enable);
 BIOT_API int biot_sweep_timing_get(biot_handle h, double *ms_total, long *launches);
 
+/* ---- read-out without device allocation ------------------------------------
+ * The paper has no counterpart; this is a library convenience.
+ *
+ * biot_read_u stages the displacement in a device buffer that the instance
+ * allocates with cudaMalloc on its first read.  Some callers cannot allocate at
+ * that point: a process whose device memory is already handed out to another
+ * allocator (a framework's caching pool, or other instances filling the GPU),
+ * or a latency-critical loop that must not take the allocator's implicit
+ * device-wide synchronisation.  biot_read_u_noalloc returns the same values as
+ * biot_read_u but stages them in a fixed array that is part of the library
+ * image (BIOT_NOALLOC_MAX_CELLS * 2 doubles = 4 MiB of device memory, held by
+ * every GPU that loads the library until the process exits); it calls no
+ * cudaMalloc, cudaFree or other allocating routine.
+ *  - Grids with more than BIOT_NOALLOC_MAX_CELLS cells (nx * ny) are rejected
+ *    with BIOT_ERR_INVALID_ARG before any device work.
+ *  - The first call on a device looks up the array's device address with that
+ *    device current; make that first call before any stream capture.
+ *  - Every call shares the one array (per device).  The read-out kernel
+ *    overwrites every value it copies back, so nothing needs clearing, but calls
+ *    from different host threads whose GPU work overlaps (e.g. two instances on
+ *    two streams) race on it: serialise them.
+ *  - Like biot_read_u it may first run the pending elastic solve of the instance
+ *    and returns after the values are in *eta (2 x nx x ny, host memory). */
+#define BIOT_NOALLOC_MAX_CELLS 262144
+BIOT_API int biot_read_u_noalloc(biot_handle h, double *eta, double *t_out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -27,8 +27,9 @@ API_FUNCTIONS = (
     "biot_create", "biot_destroy", "biot_set_stream", "biot_set_sources", "biot_set_side_profile",
     "biot_step", "biot_solve_to", "biot_read_u", "biot_read_p", "biot_read_stress",
     "biot_stats_get", "biot_error_string", "biot_last_error", "biot_sweep_timing",
-    "biot_sweep_timing_get",
+    "biot_sweep_timing_get", "biot_read_u_noalloc",
 )
+NOALLOC_MAX_CELLS = 262144  # BIOT_NOALLOC_MAX_CELLS of include/biot.h
 
 
 class BiotError(RuntimeError):
@@ -91,6 +92,7 @@ def load_library(path: str = LIB_PATH):
     lib.biot_last_error.restype = C.c_char_p
     lib.biot_sweep_timing.argtypes = [H, C.c_int]
     lib.biot_sweep_timing_get.argtypes = [H, P, C.POINTER(C.c_long)]
+    lib.biot_read_u_noalloc.argtypes = [H, P, P]
     for name in API_FUNCTIONS:
         if name not in ("biot_error_string", "biot_last_error"):
             getattr(lib, name).restype = C.c_int
@@ -199,6 +201,14 @@ class Solver:
         out = np.empty((2, self.ny, self.nx)) if out is None else out
         t = C.c_double()
         self._check(self._lib.biot_read_u(self._h, _dptr(out), C.byref(t)), "biot_read_u")
+        return out, t.value
+
+    def read_u_noalloc(self, out: Optional[np.ndarray] = None):
+        """biot_read_u_noalloc: the displacement staged through the library's
+        static device array instead of an allocated buffer."""
+        out = np.empty((2, self.ny, self.nx)) if out is None else out
+        t = C.c_double()
+        self._check(self._lib.biot_read_u_noalloc(self._h, _dptr(out), C.byref(t)), "biot_read_u_noalloc")
         return out, t.value
 
     def read_p(self, out: Optional[np.ndarray] = None):

@@ -11,6 +11,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -818,3 +819,63 @@ int biot_sweep_timing_get(biot_handle h, double *ms_total, long *launches)
 }
 
 }  // extern "C"
+
+// ============================================================================
+// Read-out through a static device array (no allocation; see biot.h).
+// ============================================================================
+namespace {
+
+constexpr int NOALLOC_MAX_DEVICES = 64;
+// Staging array of biot_read_u_noalloc: the 2 displacement planes of at most
+// BIOT_NOALLOC_MAX_CELLS cells.  In host code this name is only a stand-in for
+// the device symbol; kernels get the address looked up by noalloc_scratch().
+static __device__ __align__(256) double g_noalloc_eta[2 * (size_t)BIOT_NOALLOC_MAX_CELLS];
+
+std::mutex g_noalloc_mu;
+double *g_noalloc_addr[NOALLOC_MAX_DEVICES] = {};
+
+// Device address of the staging array on the current device, looked up once
+// per device with that device current.
+int noalloc_scratch(double **out)
+{
+    int dev = -1;
+    CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return fail(BIOT_ERR_INVALID_ARG, "device ordinal out of range for the static read-out array");
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_eta);
+        if (e != cudaSuccess || !p)
+            return fail(BIOT_ERR_CUDA, std::string("cudaGetSymbolAddress(static read-out array): ") + cudaGetErrorString(e));
+        g_noalloc_addr[dev] = static_cast<double *>(p);
+    }
+    *out = g_noalloc_addr[dev];
+    return BIOT_OK;
+}
+
+}  // namespace
+
+extern "C" int biot_read_u_noalloc(biot_handle h, double *eta, double *t_out)
+{
+    if (!h || !eta) return fail(BIOT_ERR_INVALID_ARG, "null argument");
+    const size_t np = (size_t)h->P.nx * h->P.ny;
+    if (np > (size_t)BIOT_NOALLOC_MAX_CELLS)
+        return fail(BIOT_ERR_INVALID_ARG, "biot_read_u_noalloc: the grid has " + std::to_string(np) +
+                                              " cells, more than the static read-out array holds (" +
+                                              std::to_string(BIOT_NOALLOC_MAX_CELLS) + "); use biot_read_u");
+    double *scratch = nullptr;
+    int rc = noalloc_scratch(&scratch);
+    if (rc) return rc;
+    if ((rc = ensure_initialized(h))) return rc;
+    if (!h->solved) {  // as biot_read_u: a step that hit ne_max still reads out
+        rc = elastic_solve(h);
+        if (rc && rc != BIOT_ERR_NOT_CONVERGED) return rc;
+    }
+    if ((rc = finish_pending(h))) return rc;
+    rc = h->fp32 ? readout_typed<float>(h, scratch, nullptr, nullptr) : readout_typed<double>(h, scratch, nullptr, nullptr);
+    if (rc) return rc;
+    CUDA_TRY(cudaMemcpyAsync(eta, scratch, 2 * np * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(cudaStreamSynchronize(h->stream));
+    if (t_out) *t_out = h->P.dt * (double)h->nstep;
+    return BIOT_OK;
+}
