@@ -115,10 +115,11 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def oracle_sample_step():
+def oracle_sample_step(keep=None):
     """The oracle (single-threaded FP64 C) on one physical step of the same workload,
     restricted to a 512-cell-wide strip: the problem does not depend on x, so every
-    cell does the same work as in the full grid.  Returns (seconds, cells)."""
+    cell does the same work as in the full grid.  Returns (seconds, cells); with a
+    dict ``keep``, also stores the oracle's eta and p after the step there."""
     from oracle import oracle as O
     from paper_2409_11382_gb300 import workloads as W
     params, _, _ = W.terzaghi_4097(precision=W.FP64)
@@ -128,12 +129,31 @@ def oracle_sample_step():
     t0 = time.perf_counter()
     o.step(1)  # one Biot step: flow step + elastic solve
     dt = time.perf_counter() - t0
+    if keep is not None:
+        keep["eta"], keep["p"] = o.read_u()[0], o.read_p()[0]
     o.close()
     return dt, 512 * params["ny"]
 
 
-def cpu_baseline_entry():
-    secs, cells = oracle_sample_step()
+def accuracy_vs_oracle(oracle_fields, n):
+    """L-infinity and L2 relative errors of eta and p of the GPU path after one step
+    of the benchmark problem against the oracle's strip (x-independent problem)."""
+    from paper_2409_11382_gb300 import biot, workloads as W
+    params, sides, _ = W.terzaghi_4097(n=n)
+    with biot.Solver(params, sides) as s:
+        s.step(1)
+        eta, _ = s.read_u()
+        p, _ = s.read_p()
+    out = {}
+    for name, g, o in (("eta", eta[:, :, :512], oracle_fields["eta"]), ("p", p[:, :512], oracle_fields["p"])):
+        out[f"{name}_linf_rel"] = float(np.abs(g - o).max() / np.abs(o).max())
+        out[f"{name}_l2_rel"] = float(np.linalg.norm(g - o) / np.linalg.norm(o))
+    out["how"] = "after 1 step, first 512 columns vs the FP64 oracle on a 512-column strip"
+    return out
+
+
+def cpu_baseline_entry(keep=None):
+    secs, cells = oracle_sample_step(keep)
     return {"value": cells / secs / 1e6, "unit": "MLUPS", "cores": 1, "kind": "oracle",
             "sample": f"1 physical step of the same problem on a 512x4096-cell strip "
                       f"(x-independent solution, same per-cell work), {secs:.1f} s, FP64, 1 thread"}
@@ -168,8 +188,27 @@ def run_reference(args):
     return 0
 
 
+def _init_dist(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+
+def _barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def _finish_dist(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
 def run_ours(args):
     import torch
+    from paper_2409_11382_gb300 import dist as D
     rank, world, local = dist_info()
     from paper_2409_11382_gb300 import biot, workloads as W
     from paper_2409_11382_gb300 import build as B
@@ -218,10 +257,7 @@ def run_ours(args):
     sweep_ms, sweep_n = solver.sweep_timing_get()
     solver.sweep_timing(False)
 
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = D.max_over_ranks(ms, device="cuda")  # slowest rank (no-op on one GPU)
 
     # ---- end to end through the public API with host buffers ------------------------
     e2e_steps = max(1, min(args.steps, 5))
@@ -253,6 +289,11 @@ def run_ours(args):
 
     value = world * cells * args.steps / (ms / 1e3) / 1e6
     peak, peak_kind = measured_peaks()
+    cpu_base, accuracy = None, None
+    if not args.no_cpu_baseline and args.n == 4096:
+        fields = {}
+        cpu_base = cpu_baseline_entry(fields)
+        accuracy = accuracy_vs_oracle(fields, args.n)
     # finest-level smoothing sweep, FP32: 8 moments + 2 low parts in and out, F~ in;
     # the prolongated correction (8 coarse moments per 4 cells) once per 2K sweeps
     bytes_per_cell = (10 + 10 + 2) * 4.0 + 8.0 / (2 * params["K"])
@@ -274,7 +315,8 @@ def run_ours(args):
                      "peak_kind": f"{peak_kind} copy bandwidth (burst)",
                      "bytes_per_cell": bytes_per_cell, "launches": sweep_n, "avg_launch_ms": avg_sweep_ms,
                      "traffic": None if traffic_pc is None else traffic_pc * cells},
-        "cpu_baseline": cpu_baseline_entry() if (rank == 0 and not args.no_cpu_baseline) else None,
+        "cpu_baseline": cpu_base,
+        "accuracy": accuracy,
         "e2e": {"value": cells * e2e_steps / e2e_s / 1e6, "unit": "MLUPS", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "steps": e2e_steps, "finite": finite},
         "gpu_launches": launches,
@@ -288,6 +330,159 @@ def run_ours(args):
     return 0
 
 
+def _percentile(v, q):
+    return float(np.percentile(np.asarray(v, dtype=np.float64), q)) if len(v) else None
+
+
+def run_batched(args):
+    """64 seeded uneven instances (sides 64..512 cells, random materials and partial
+    top loads), FP32, MG(3,4); one CUDA graph per physical step of all instances."""
+    import torch
+    from paper_2409_11382_gb300 import biot, build as B, dist as D, workloads as W
+    rank, world, local = dist_info()
+    torch.cuda.set_device(local)
+    _init_dist(world)
+    if rank == 0:
+        B.build()
+    _barrier(world)
+    # weak scaling: every rank advances its own 64 seeded instances
+    probs = W.batched_instances(count=args.instances, seed=2409 + 7919 * rank)
+    cells = sum(p["nx"] * p["ny"] for p, _ in probs)
+    b = biot.Batch(probs)
+    b.step(args.warmup)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local) if rank == 0 else None
+    if clocks:
+        clocks.start()
+    _barrier(world)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    t0 = time.perf_counter()
+    b.step(args.steps)  # one graph launch per step, one read-back at the end
+    ev1.record()
+    torch.cuda.synchronize()
+    _barrier(world)
+    secs = D.max_over_ranks(max(time.perf_counter() - t0, ev0.elapsed_time(ev1) / 1e3), device="cuda")
+    clock_info = clocks.stop() if clocks else None
+    st = b.stats()
+    # end to end: each step, H2D of every instance's top-load profile and D2H of eta and p
+    e2e_steps = max(1, min(args.steps, 3))
+    h2d = d2h = 0
+    t1 = time.perf_counter()
+    for _ in range(e2e_steps):
+        for i, (p, sides) in enumerate(probs):
+            b[i].set_side_profile(W.TOP, sides[W.TOP]["eta_profile"], sides[W.TOP]["p_profile"])
+        b.step(1)
+        for i in range(len(b)):
+            eta, _ = b[i].read_u()
+            pr, _ = b[i].read_p()
+            d2h += eta.nbytes + pr.nbytes
+    e2e = time.perf_counter() - t1
+    for p, sides in probs:
+        h2d += sides[W.TOP]["eta_profile"].nbytes + sides[W.TOP]["p_profile"].nbytes
+    b.close()
+    value = world * cells * args.steps / secs / 1e6
+    line = {"metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "batched_64_instances_64-512_fp32", "instances": len(probs),
+                       "cells_total": cells, "ne_fixed": 3, "K": 4,
+                       "l2": "state of all instances larger than L2; no flush needed",
+                       "parallelism": f"replicas{world}"},
+            "e2e": {"value": cells * e2e_steps / e2e / 1e6, "unit": "MLUPS",
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h // e2e_steps},
+            "gpu_launches": st["launches_per_step"] * args.steps,
+            "batch": st, "clocks": clock_info}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    _finish_dist(world)
+    return 0
+
+
+def run_served(args):
+    """Seeded Poisson stream of solve requests (sides 64..1024 cells, the 4097^2
+    case's materials, 100 steps to T = 0.1, FP32) through the continuous-batching
+    server; then the same requests one at a time through the plain FP64 path (and
+    the plain FP32 path) with the same arrival times (first come, first served)."""
+    import torch
+    from paper_2409_11382_gb300 import biot, build as B, workloads as W
+    rank, world, local = dist_info()
+    torch.cuda.set_device(local)
+    _init_dist(world)
+    if rank == 0:
+        B.build()
+    _barrier(world)
+    reqs = W.served_requests(count=args.requests, seed=11382 + 7919 * rank,
+                             mean_service_s=args.mean_service)
+    cells_steps = sum(p["nx"] * p["ny"] * round(T / p["dt"]) for _, p, _, T in reqs)
+    budget = int(args.budget_gb * (1 << 30))
+    # warm-up: kernels, graphs and the allocator on one small request of each size
+    for n in sorted({p["nx"] for _, p, _, _ in reqs}):
+        _, p, s, T = next(r for r in reqs if r[1]["nx"] == n)
+        with biot.Solver(p, s) as sol:
+            sol.step(2)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local) if rank == 0 else None
+    if clocks:
+        clocks.start()
+    with biot.Server(budget, max_resident=args.max_resident) as srv:
+        ids = []
+        t0 = time.perf_counter()
+        for arrival, p, s, T in reqs:
+            delay = arrival - (time.perf_counter() - t0)
+            if delay > 0:
+                time.sleep(delay)
+            ids.append(srv.submit(p, s, T))
+        for rid in ids:
+            srv.wait(rid, timeout=3600)
+        makespan = time.perf_counter() - t0
+        infos = [srv.poll(rid) for rid in ids]
+        st = srv.stats()
+        checks = [srv.fetch(rid) for rid in ids[:2]]
+    clock_info = clocks.stop() if clocks else None
+    lat = [i["t_done"] - i["t_submit"] for i in infos]
+
+    def one_at_a_time(precision):
+        finish, lats, busy = 0.0, [], 0.0
+        for arrival, p, s, T in reqs:
+            t1 = time.perf_counter()
+            with biot.Solver(dict(p, precision=precision), s) as sol:
+                sol.solve_to(T)
+                sol.read_u()
+                sol.read_p()
+            svc = time.perf_counter() - t1
+            busy += svc
+            finish = max(arrival, finish) + svc
+            lats.append(finish - arrival)
+        return {"p50_s": _percentile(lats, 50), "p99_s": _percentile(lats, 99),
+                "throughput_mlups": cells_steps / busy / 1e6, "busy_s": busy}
+
+    plain64 = one_at_a_time(W.FP64)
+    plain32 = one_at_a_time(W.FP32)
+    # the first two served results against their plain FP32 solo runs (same kernels)
+    same = True
+    for (arrival, p, s, T), (eta, pr, t) in zip(reqs[:2], checks):
+        with biot.Solver(p, s) as sol:
+            sol.solve_to(T)
+            same = same and np.array_equal(eta, sol.read_u()[0]) and np.array_equal(pr, sol.read_p()[0])
+    value = world * cells_steps / makespan / 1e6
+    line = {"metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world,
+            "steps": args.requests, "warmup": 1, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "served_poisson_64-1024_fp32", "requests": len(reqs),
+                       "mean_in_flight_target": 8, "budget_gb": args.budget_gb,
+                       "max_resident": args.max_resident, "parallelism": f"replicas{world}"},
+            "latency": {"p50_s": _percentile(lat, 50), "p99_s": _percentile(lat, 99),
+                        "makespan_s": makespan},
+            "plain_fp64_one_at_a_time": plain64, "plain_fp32_one_at_a_time": plain32,
+            "served_equals_solo": same, "server": st, "clocks": clock_info}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    _finish_dist(world)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -296,11 +491,21 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--n", type=int, default=4096, help="cells per side (4096 = the benchmark workload)")
+    ap.add_argument("--workload", choices=["single", "batched", "served"], default="single")
+    ap.add_argument("--instances", type=int, default=64, help="batched: number of instances")
+    ap.add_argument("--requests", type=int, default=48, help="served: number of requests")
+    ap.add_argument("--mean-service", type=float, default=0.05, help="served: assumed mean service time (s)")
+    ap.add_argument("--budget-gb", type=float, default=16.0, help="served: device-memory budget")
+    ap.add_argument("--max-resident", type=int, default=16, help="served: resident-instance limit")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batched":
+        return run_batched(args)
+    if args.workload == "served":
+        return run_served(args)
     return run_ours(args)
 
 

@@ -154,7 +154,9 @@ BIOT_API int biot_set_stream(biot_handle h, void *cuda_stream);
 BIOT_API int biot_set_sources(biot_handle h, const double *f_body, const double *s);
 
 /* Replace the boundary data of one side (same layout as biot_side; the types
- * are fixed at creation).  NULL sets zero data. */
+ * are fixed at creation).  NULL sets zero data.  The data act from the next
+ * elastic solve on (the next biot_step); the current state keeps the data it
+ * was solved with. */
 BIOT_API int biot_set_side_profile(biot_handle h, int side, const double *eta_profile, const double *p_profile);
 
 /* Run n iterations of the time loop of Alg. 5 (elastic solve at t, flow step
@@ -189,6 +191,87 @@ BIOT_API const char *biot_last_error(void);
  * device time (ms) and the number of such launches since the last enable. */
 BIOT_API int biot_sweep_timing(biot_handle h, int enable);
 BIOT_API int biot_sweep_timing_get(biot_handle h, double *ms_total, long *launches);
+
+/* ---- batched execution ----------------------------------------------------------
+ * Many independent instances (different grids, materials, boundary data) advanced
+ * together.  Each physical step of every instance is Alg. 5 exactly as in
+ * biot_step -- same kernels, same arithmetic, bitwise the same result as the
+ * instance stepped alone -- but the multigrid sweeps of all instances are
+ * regrouped: the V-cycles are aligned by depth below the finest level and each
+ * phase is one work-list launch per storage kind whose CTAs process strips of
+ * sweeps of different instances and levels; the whole step is one CUDA graph.
+ * Instances need a fixed number of V-cycles (ne_fixed > 0) and equal K and
+ * ne_fixed.  The batch owns its instances: read them with biot_read_u / _p /
+ * _stress / biot_stats_get through biot_batch_instance, do not destroy them or
+ * move them to another stream, and do not step them with biot_step. */
+typedef struct biot_batch_s *biot_batch;
+
+/* Create `count` instances (params[i], sides[4*i .. 4*i+3]); all device memory is
+ * allocated here.  On failure *out is NULL and the message names the instance. */
+BIOT_API int biot_batch_create(int count, const biot_params *params, const biot_side *sides, biot_batch *out);
+BIOT_API int biot_batch_destroy(biot_batch b);
+BIOT_API int biot_batch_size(biot_batch b, int *count);
+/* Handle of instance i (owned by the batch). */
+BIOT_API int biot_batch_instance(biot_batch b, int i, biot_handle *out);
+/* n physical steps of every instance (plus the trailing elastic solve, as biot_step). */
+BIOT_API int biot_batch_step(biot_batch b, int n);
+/* Kernel launches since creation, per captured step, and strip work items per step. */
+BIOT_API int biot_batch_stats_get(biot_batch b, long *kernel_launches, long *launches_per_step,
+                                  long *work_items_per_step);
+
+/* ---- serving: continuous batching of solve requests ---------------------------
+ * A scheduler thread admits submitted solves in arrival order while the
+ * device-memory budget (biot_estimate_bytes per request) and the resident-slot
+ * limit allow, keeps each admitted instance resident on its own CUDA stream, and
+ * in each tick launches the next time steps of every resident instance before it
+ * waits for any, so that their kernels overlap on the GPU.  A finished instance
+ * is read out (eta and p at the end time, as biot_read_u / biot_read_p) into host
+ * memory and freed at once, which admits the next request.  Every request runs
+ * the same kernels as biot_create + biot_solve_to, so its result does not depend
+ * on what else is resident.  Times are seconds since biot_server_create. */
+typedef struct biot_server_s *biot_server;
+
+#define BIOT_REQ_QUEUED  0
+#define BIOT_REQ_RUNNING 1
+#define BIOT_REQ_DONE    2
+#define BIOT_REQ_FAILED  3
+
+typedef struct biot_request_info {
+    int    state;         /* BIOT_REQ_* */
+    int    status;        /* BIOT_OK or the error code of a failed request */
+    double t_submit, t_start, t_done;
+    int    nx, ny;
+    long   steps;         /* physical steps to the end time */
+    size_t device_bytes;  /* admission estimate */
+} biot_request_info;
+
+typedef struct biot_server_stats {
+    int    queued, peak_resident;
+    size_t used_bytes, peak_bytes;
+    long   ticks, graph_launches;
+} biot_server_stats;
+
+/* Device bytes an instance with these parameters holds (allocation plus the
+ * read-out buffer); validates the parameters. */
+BIOT_API int biot_estimate_bytes(const biot_params *p, const biot_side sides[4], size_t *bytes);
+/* Start a server on the current device with a device-memory budget and at most
+ * max_resident instances resident at once. */
+BIOT_API int biot_server_create(size_t mem_budget_bytes, int max_resident, biot_server *out);
+/* Queue a solve to time T (copies all inputs); BIOT_ERR_OOM if it alone exceeds
+ * the budget. */
+BIOT_API int biot_server_submit(biot_server s, const biot_params *p, const biot_side sides[4], double T, uint64_t *id);
+BIOT_API int biot_server_poll(biot_server s, uint64_t id, biot_request_info *info);
+/* Block until the request is done (BIOT_OK), failed (its error code) or the
+ * timeout expires (BIOT_ERR_TIMEOUT). */
+BIOT_API int biot_server_wait(biot_server s, uint64_t id, double timeout_s);
+/* Copy the result of a finished request: eta 2 x nx x ny, p nx x ny (either may
+ * be NULL) and its time. */
+BIOT_API int biot_server_fetch(biot_server s, uint64_t id, double *eta, double *p, double *t_out);
+/* Forget a finished request (its result buffers are freed). */
+BIOT_API int biot_server_release(biot_server s, uint64_t id);
+BIOT_API int biot_server_stats_get(biot_server s, biot_server_stats *out);
+/* Stop the scheduler; requests still queued or resident are dropped. */
+BIOT_API int biot_server_destroy(biot_server s);
 
 /* ---- read-out without device allocation ------------------------------------
  * The paper has no counterpart; this is a library convenience.

@@ -28,7 +28,13 @@ API_FUNCTIONS = (
     "biot_step", "biot_solve_to", "biot_read_u", "biot_read_p", "biot_read_stress",
     "biot_stats_get", "biot_error_string", "biot_last_error", "biot_sweep_timing",
     "biot_sweep_timing_get", "biot_read_u_noalloc",
+    "biot_batch_create", "biot_batch_destroy", "biot_batch_size", "biot_batch_instance",
+    "biot_batch_step", "biot_batch_stats_get",
+    "biot_estimate_bytes", "biot_server_create", "biot_server_submit", "biot_server_poll",
+    "biot_server_wait", "biot_server_fetch", "biot_server_release", "biot_server_stats_get",
+    "biot_server_destroy",
 )
+REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_FAILED = 0, 1, 2, 3
 NOALLOC_MAX_CELLS = 262144  # BIOT_NOALLOC_MAX_CELLS of include/biot.h
 
 
@@ -50,6 +56,17 @@ class biot_params(C.Structure):
 class biot_side(C.Structure):
     _fields_ = [("eta_type", C.c_int), ("p_type", C.c_int),
                 ("eta_profile", C.POINTER(C.c_double)), ("p_profile", C.POINTER(C.c_double))]
+
+
+class biot_request_info(C.Structure):
+    _fields_ = [("state", C.c_int), ("status", C.c_int), ("t_submit", C.c_double),
+                ("t_start", C.c_double), ("t_done", C.c_double), ("nx", C.c_int), ("ny", C.c_int),
+                ("steps", C.c_long), ("device_bytes", C.c_size_t)]
+
+
+class biot_server_stats(C.Structure):
+    _fields_ = [("queued", C.c_int), ("peak_resident", C.c_int), ("used_bytes", C.c_size_t),
+                ("peak_bytes", C.c_size_t), ("ticks", C.c_long), ("graph_launches", C.c_long)]
 
 
 class biot_stats(C.Structure):
@@ -93,6 +110,22 @@ def load_library(path: str = LIB_PATH):
     lib.biot_sweep_timing.argtypes = [H, C.c_int]
     lib.biot_sweep_timing_get.argtypes = [H, P, C.POINTER(C.c_long)]
     lib.biot_read_u_noalloc.argtypes = [H, P, P]
+    lib.biot_batch_create.argtypes = [C.c_int, C.POINTER(biot_params), C.POINTER(biot_side), C.POINTER(H)]
+    lib.biot_batch_destroy.argtypes = [H]
+    lib.biot_batch_size.argtypes = [H, C.POINTER(C.c_int)]
+    lib.biot_batch_instance.argtypes = [H, C.c_int, C.POINTER(H)]
+    lib.biot_batch_step.argtypes = [H, C.c_int]
+    lib.biot_batch_stats_get.argtypes = [H, C.POINTER(C.c_long), C.POINTER(C.c_long), C.POINTER(C.c_long)]
+    lib.biot_estimate_bytes.argtypes = [C.POINTER(biot_params), C.POINTER(biot_side), C.POINTER(C.c_size_t)]
+    lib.biot_server_create.argtypes = [C.c_size_t, C.c_int, C.POINTER(H)]
+    lib.biot_server_submit.argtypes = [H, C.POINTER(biot_params), C.POINTER(biot_side), C.c_double,
+                                       C.POINTER(C.c_uint64)]
+    lib.biot_server_poll.argtypes = [H, C.c_uint64, C.POINTER(biot_request_info)]
+    lib.biot_server_wait.argtypes = [H, C.c_uint64, C.c_double]
+    lib.biot_server_fetch.argtypes = [H, C.c_uint64, P, P, P]
+    lib.biot_server_release.argtypes = [H, C.c_uint64]
+    lib.biot_server_stats_get.argtypes = [H, C.POINTER(biot_server_stats)]
+    lib.biot_server_destroy.argtypes = [H]
     for name in API_FUNCTIONS:
         if name not in ("biot_error_string", "biot_last_error"):
             getattr(lib, name).restype = C.c_int
@@ -112,6 +145,33 @@ def _f64(a) -> Optional[np.ndarray]:
     return np.ascontiguousarray(a, dtype=np.float64)
 
 
+def _fill_params(p: "biot_params", params: dict) -> "biot_params":
+    p.nx, p.ny = int(params["nx"]), int(params["ny"])
+    p.lx, p.ly = float(params["lx"]), float(params["ly"])
+    p.lambda_, p.mu = float(params["lam"]), float(params["mu"])
+    p.alpha, p.c0, p.kappa = float(params["alpha"]), float(params["c0"]), float(params["kappa"])
+    p.dt, p.r_coupling = float(params["dt"]), float(params.get("r", 0.5))
+    p.mg_levels, p.K = int(params["levels"]), int(params["K"])
+    p.gamma, p.tol = float(params["gamma"]), float(params["tol"])
+    p.ne_max, p.ne_fixed = int(params["ne_max"]), int(params["ne_fixed"])
+    p.precision = int(params.get("precision", FP64))
+    return p
+
+
+def _fill_sides(arr, base: int, sides: Sequence[dict]) -> list:
+    """Fill arr[base .. base+3] from four side dicts; returns the arrays to keep alive."""
+    keep = []
+    for i, s in enumerate(sides):
+        arr[base + i].eta_type = int(s["eta_type"])
+        arr[base + i].p_type = int(s["p_type"])
+        for key in ("eta_profile", "p_profile"):
+            v = _f64(s.get(key))
+            if v is not None:
+                keep.append(v)
+            setattr(arr[base + i], key, _dptr(v))
+    return keep
+
+
 class Solver:
     """One instance of the coupled problem on the current CUDA device.
 
@@ -121,31 +181,20 @@ class Solver:
     Methods map one-to-one onto the C entry points.
     """
 
-    def __init__(self, params: dict, sides: Sequence[dict], stream: Optional[int] = None):
+    def __init__(self, params: dict, sides: Sequence[dict], stream: Optional[int] = None,
+                 _handle: Optional[C.c_void_p] = None, _owner=None):
         self._lib = load_library()
-        p = biot_params()
-        p.nx, p.ny = int(params["nx"]), int(params["ny"])
-        p.lx, p.ly = float(params["lx"]), float(params["ly"])
-        p.lambda_, p.mu = float(params["lam"]), float(params["mu"])
-        p.alpha, p.c0, p.kappa = float(params["alpha"]), float(params["c0"]), float(params["kappa"])
-        p.dt, p.r_coupling = float(params["dt"]), float(params.get("r", 0.5))
-        p.mg_levels, p.K = int(params["levels"]), int(params["K"])
-        p.gamma, p.tol = float(params["gamma"]), float(params["tol"])
-        p.ne_max, p.ne_fixed = int(params["ne_max"]), int(params["ne_fixed"])
-        p.precision = int(params.get("precision", FP64))
-        self.nx, self.ny = p.nx, p.ny
+        self._owner = _owner  # a Batch that owns this instance (not destroyed here)
+        self.nx, self.ny = int(params["nx"]), int(params["ny"])
+        if _handle is not None:
+            self._h = _handle
+            return
+        p = _fill_params(biot_params(), params)
         arr = (biot_side * 4)()
-        keep = []
-        for i, s in enumerate(sides):
-            arr[i].eta_type = int(s["eta_type"])
-            arr[i].p_type = int(s["p_type"])
-            for key in ("eta_profile", "p_profile"):
-                v = _f64(s.get(key))
-                if v is not None:
-                    keep.append(v)
-                setattr(arr[i], key, _dptr(v))
+        keep = _fill_sides(arr, 0, sides)
         h = C.c_void_p()
         self._check(self._lib.biot_create(C.byref(p), arr, C.byref(h)), "biot_create")
+        del keep
         self._h = h
         if stream is not None:
             self.set_stream(stream)
@@ -158,6 +207,9 @@ class Solver:
         return code
 
     def close(self):
+        if getattr(self, "_owner", None) is not None:
+            self._h = None
+            return
         if getattr(self, "_h", None):
             self._lib.biot_destroy(self._h)
             self._h = None
@@ -236,3 +288,149 @@ class Solver:
         self._check(self._lib.biot_sweep_timing_get(self._h, C.byref(ms), C.byref(n)),
                     "biot_sweep_timing_get")
         return ms.value, n.value
+
+
+class Batch:
+    """Many instances advanced together (biot_batch_*).  ``problems`` is a list of
+    (params, sides) pairs; ``batch[i]`` is a Solver view of instance i (owned by
+    the batch) for read-out."""
+
+    def __init__(self, problems: Sequence):
+        self._lib = load_library()
+        n = len(problems)
+        ps = (biot_params * n)()
+        arr = (biot_side * (4 * n))()
+        keep = []
+        for i, (params, sides) in enumerate(problems):
+            _fill_params(ps[i], params)
+            keep += _fill_sides(arr, 4 * i, sides)
+        h = C.c_void_p()
+        code = self._lib.biot_batch_create(n, ps, arr, C.byref(h))
+        if code != OK:
+            raise BiotError(code, "biot_batch_create", self._lib.biot_last_error().decode(errors="replace"))
+        self._h = h
+        self._views = []
+        for i, (params, _) in enumerate(problems):
+            ih = C.c_void_p()
+            self._lib.biot_batch_instance(self._h, i, C.byref(ih))
+            self._views.append(Solver(params, None, _handle=ih, _owner=self))
+
+    def __len__(self):
+        return len(self._views)
+
+    def __getitem__(self, i) -> Solver:
+        return self._views[i]
+
+    def step(self, n: int = 1) -> int:
+        code = self._lib.biot_batch_step(self._h, int(n))
+        if code not in (OK, ERR_NOT_CONVERGED):
+            raise BiotError(code, "biot_batch_step", self._lib.biot_last_error().decode(errors="replace"))
+        return code
+
+    def stats(self) -> dict:
+        a, b, c = C.c_long(), C.c_long(), C.c_long()
+        self._lib.biot_batch_stats_get(self._h, C.byref(a), C.byref(b), C.byref(c))
+        return dict(kernel_launches=a.value, launches_per_step=b.value, work_items_per_step=c.value)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            for v in self._views:
+                v._h = None
+            self._lib.biot_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def estimate_bytes(params: dict, sides: Sequence[dict]) -> int:
+    lib = load_library()
+    p = _fill_params(biot_params(), params)
+    arr = (biot_side * 4)()
+    keep = _fill_sides(arr, 0, sides)
+    n = C.c_size_t()
+    code = lib.biot_estimate_bytes(C.byref(p), arr, C.byref(n))
+    del keep
+    if code != OK:
+        raise BiotError(code, "biot_estimate_bytes", lib.biot_last_error().decode(errors="replace"))
+    return n.value
+
+
+class Server:
+    """Continuous-batching request loop (biot_server_*) on the current device."""
+
+    def __init__(self, mem_budget_bytes: int, max_resident: int):
+        self._lib = load_library()
+        h = C.c_void_p()
+        self._check(self._lib.biot_server_create(C.c_size_t(int(mem_budget_bytes)), int(max_resident), C.byref(h)),
+                    "biot_server_create")
+        self._h = h
+        self._shape = {}
+
+    def _check(self, code: int, where: str, allow=(OK,)):
+        if code not in allow:
+            raise BiotError(code, where, self._lib.biot_last_error().decode(errors="replace"))
+        return code
+
+    def submit(self, params: dict, sides: Sequence[dict], T: float) -> int:
+        p = _fill_params(biot_params(), params)
+        arr = (biot_side * 4)()
+        keep = _fill_sides(arr, 0, sides)
+        rid = C.c_uint64()
+        self._check(self._lib.biot_server_submit(self._h, C.byref(p), arr, float(T), C.byref(rid)),
+                    "biot_server_submit")
+        del keep
+        self._shape[rid.value] = (int(params["ny"]), int(params["nx"]))
+        return rid.value
+
+    def poll(self, rid: int) -> dict:
+        info = biot_request_info()
+        self._check(self._lib.biot_server_poll(self._h, C.c_uint64(rid), C.byref(info)), "biot_server_poll")
+        return {name: getattr(info, name) for name, _ in biot_request_info._fields_}
+
+    def wait(self, rid: int, timeout: float = 600.0) -> int:
+        return self._check(self._lib.biot_server_wait(self._h, C.c_uint64(rid), float(timeout)), "biot_server_wait")
+
+    def fetch(self, rid: int):
+        ny, nx = self._shape[rid]
+        eta = np.empty((2, ny, nx))
+        p = np.empty((ny, nx))
+        t = C.c_double()
+        self._check(self._lib.biot_server_fetch(self._h, C.c_uint64(rid), _dptr(eta), _dptr(p), C.byref(t)),
+                    "biot_server_fetch")
+        return eta, p, t.value
+
+    def release(self, rid: int):
+        self._check(self._lib.biot_server_release(self._h, C.c_uint64(rid)), "biot_server_release")
+        self._shape.pop(rid, None)
+
+    def stats(self) -> dict:
+        st = biot_server_stats()
+        self._check(self._lib.biot_server_stats_get(self._h, C.byref(st)), "biot_server_stats_get")
+        return {name: getattr(st, name) for name, _ in biot_server_stats._fields_}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.biot_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

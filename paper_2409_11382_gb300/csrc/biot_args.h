@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 #include <stddef.h>
 #include <stdint.h>
+#include <stdlib.h>
 
 namespace biot {
 
@@ -46,6 +47,15 @@ struct SweepArgs {
     T k_22;   // -1 / (12 lm + 4)   (eq. moments:collision:22)
     T k_gam;  // gamma
 };
+
+// One CTA's work item of a batched sweep launch: strip (bx, by) of TY rows of
+// the sweep jobs[job].
+struct SweepItem {
+    int job, bx, by, ty;
+};
+
+// Storage kind of a sweep launch (bit flags).
+enum { SWEEP_V_COARSE = 1, SWEEP_V_LO = 2, SWEEP_V_RESTRICT = 4 };
 
 // Explicit part of the effective source (eq. source:implicit) per cell.
 template <typename T>
@@ -123,6 +133,45 @@ struct InitArgs {
 };
 
 template <typename T, typename TC> cudaError_t launch_sweep_mom(const SweepArgs<T, TC> &a, cudaStream_t s);
+// Batched sweep: one launch of n work items of storage kind `variant`
+// (SWEEP_V_* flags); jobs and items are device arrays.
+template <typename T, typename TC>
+cudaError_t launch_sweep_batch(int variant, const SweepArgs<T, TC> *jobs, const SweepItem *items, int n, cudaStream_t s);
+// Resident CTAs of a sweep launch of this kind on the current device, and the
+// strip geometry of the sweep kernels (columns per strip).
+template <typename T, typename TC> int sweep_slots(int variant);
+constexpr int SWEEP_STRIP_COLS = 124;
+
+// Largest strip height of a sweep launch (rows); the environment variable
+// BIOT_SWEEP_MAX_ROWS overrides it.
+inline int sweep_rows_cap()
+{
+    static int cap = 0;
+    if (!cap) {
+        const char *e = getenv("BIOT_SWEEP_MAX_ROWS");
+        const int v = e ? atoi(e) : 0;
+        cap = v >= 2 ? v : 32;
+    }
+    return cap;
+}
+
+// Rows per strip of a sweep over nx x ny cells given `slots` resident CTAs:
+// the grid fills whole waves of slots, with the first wave count whose strips
+// are at most sweep_rows_cap() rows tall.  Even (restriction pairs rows), >= 2.
+inline int sweep_strip_rows(int nx, int ny, int slots)
+{
+    const int strips_x = (nx + SWEEP_STRIP_COLS - 1) / SWEEP_STRIP_COLS;
+    const int cap = sweep_rows_cap();
+    if (slots < 1) slots = 1;
+    for (int waves = 1;; waves++) {
+        long nsy = ((long)waves * slots) / strips_x;
+        if (nsy < 1) nsy = 1;
+        long ty = (ny + nsy - 1) / nsy;
+        ty += ty & 1;
+        if (ty < 2) ty = 2;
+        if (ty <= cap || waves >= 64) return (int)ty;
+    }
+}
 template <typename T> cudaError_t launch_sexp(const SexpArgs<T> &a, cudaStream_t s);
 template <typename T> cudaError_t launch_force(const ForceArgs<T> &a, cudaStream_t s);
 template <typename T> cudaError_t launch_flow_moments(const FlowMomentsArgs<T> &a, cudaStream_t s);

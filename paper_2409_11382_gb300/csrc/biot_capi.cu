@@ -11,7 +11,13 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <map>
 #include <mutex>
+#include <thread>
 #include <new>
 #include <string>
 #include <vector>
@@ -20,6 +26,22 @@
 #include "biot_args.h"
 
 using namespace biot;
+
+namespace biot {
+// A sweep prepared for a batched launch: its storage kind and arguments.
+struct SweepJob {
+    int tkind;    // 0: double/double, 1: float/double, 2: float/float
+    int variant;  // SWEEP_V_* flags
+    int level;
+    SweepArgs<double, double> dd;
+    SweepArgs<float, double> fd;
+    SweepArgs<float, float> ff;
+};
+template <typename T, typename TC> SweepArgs<T, TC> &job_args(SweepJob &j);
+template <> SweepArgs<double, double> &job_args<double, double>(SweepJob &j) { return j.dd; }
+template <> SweepArgs<float, double> &job_args<float, double>(SweepJob &j) { return j.fd; }
+template <> SweepArgs<float, float> &job_args<float, float>(SweepJob &j) { return j.ff; }
+}  // namespace biot
 
 namespace {
 
@@ -89,11 +111,16 @@ struct biot_ctx {
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     long graph_launches[2] = {0, 0};
     bool use_graphs = true;
+    long epoch = 0;  // bumped whenever captured launch arguments become stale
     // instrumentation of the finest-level smoothing sweep
     bool timing = false;
     std::vector<cudaEvent_t> ev;
     size_t ev_used = 0;
     std::vector<void *> allocs;
+    // measure the residual in the V-cycle being issued (set by elastic_solve)
+    bool measure_cycle = true;
+    // record mode (batched execution): sweeps are appended here instead of launched
+    std::vector<biot::SweepJob> *rec = nullptr;
 };
 
 namespace {
@@ -218,6 +245,17 @@ int sweep_typed(biot_ctx *h, int l, int mode, bool zero_init, bool prolong, bool
     a.k_22 = T(-1.0 / (12.0 * a.lm + 4.0));
     a.k_gam = T(a.gamma);
 
+    if (h->rec) {
+        SweepJob j{};
+        j.tkind = sizeof(T) == 8 ? 0 : (sizeof(TC) == 8 ? 1 : 2);
+        j.variant = (fine ? 0 : SWEEP_V_COARSE) | (fine && a.glo ? SWEEP_V_LO : 0) | (mode == SWEEP_RESTRICT ? SWEEP_V_RESTRICT : 0);
+        j.level = l;
+        job_args<T, TC>(j) = a;
+        h->rec->push_back(j);
+        Lv.hist_valid = 1;
+        if (mode == SWEEP_SMOOTH) Lv.cur ^= 1;
+        return BIOT_OK;
+    }
     const bool timed = h->timing && fine && mode == SWEEP_SMOOTH;
     if (timed) {
         while (h->ev.size() < h->ev_used + 2) {
@@ -262,7 +300,7 @@ int vcycle(biot_ctx *h, int l, bool zero_start)
         if ((rc = vcycle(h, l - 1, true))) return rc;
     }
     for (int k = 0; k < K; k++)
-        if ((rc = sweep(h, l, SWEEP_SMOOTH, false, l > 0 && k == 0, fine && k == K - 1))) return rc;
+        if ((rc = sweep(h, l, SWEEP_SMOOTH, false, l > 0 && k == 0, fine && k == K - 1 && h->measure_cycle))) return rc;
     return BIOT_OK;
 }
 
@@ -330,13 +368,16 @@ int elastic_solve(biot_ctx *h)
     int ne = 0, status = BIOT_OK;
     for (;;) {
         const bool measure = !fixed || (ne + 1 == h->P.ne_fixed);
+        h->measure_cycle = measure;
         if (measure) CUDA_TRY(cudaMemsetAsync(h->resmax, 0, 2 * sizeof(unsigned long long), h->stream));
         if ((rc = vcycle(h, h->L - 1, false))) return rc;
         ne++;
         h->total_cycles++;
         if (fixed) {
             if (ne >= h->P.ne_fixed) {
-                CUDA_TRY(cudaMemcpyAsync(h->resmax_host, h->resmax, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, h->stream));
+                // (a batched step issues this copy after its merged sweeps)
+                if (!h->rec)
+                    CUDA_TRY(cudaMemcpyAsync(h->resmax_host, h->resmax, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, h->stream));
                 h->pending_res = true;
                 break;
             }
@@ -498,6 +539,7 @@ int readout(biot_ctx *h, double *eta_host, double *p_host, double *sigma_host)
 
 void drop_graphs(biot_ctx *h)
 {
+    h->epoch++;
     for (int i = 0; i < 2; i++) {
         if (h->graph[i]) cudaGraphExecDestroy(h->graph[i]);
         h->graph[i] = nullptr;
@@ -714,10 +756,12 @@ int biot_set_sources(biot_handle h, const double *f_body, const double *s)
 int biot_set_side_profile(biot_handle h, int side, const double *eta_profile, const double *p_profile)
 {
     if (!h || side < 0 || side > 3) return fail(BIOT_ERR_INVALID_ARG, "bad handle or side");
+    const double *e0 = h->eta_prof[side], *p0 = h->p_prof[side];
     int rc = set_profiles(h, side, eta_profile, p_profile);
     if (rc) return rc;
-    drop_graphs(h);
-    h->solved = false;
+    // captured launches read the profile buffers when they run; only a newly
+    // allocated buffer makes them stale
+    if (h->eta_prof[side] != e0 || h->p_prof[side] != p0) drop_graphs(h);
     return BIOT_OK;
 }
 
@@ -879,3 +923,748 @@ extern "C" int biot_read_u_noalloc(biot_handle h, double *eta, double *t_out)
     if (t_out) *t_out = h->P.dt * (double)h->nstep;
     return BIOT_OK;
 }
+
+// ============================================================================
+// Batched execution of many instances (one CUDA graph per time step).
+//
+// Every instance keeps its own state and runs exactly the launch sequence of
+// biot_step; only the sweeps are regrouped.  The V-cycles of all instances are
+// aligned by depth below the finest level: the down-legs start together, the
+// up-legs end together, and an instance with fewer levels does its coarsest
+// sweeps while deeper instances are still going down.  Each phase of that
+// schedule is one work-list launch per storage kind, whose CTAs take strips of
+// sweeps of different instances and levels.
+// ============================================================================
+namespace {
+
+// One sweep of the static schedule of an instance.
+struct PlanOp {
+    int level, mode, key;
+};
+
+// Mirror of vcycle(): the sweeps of one V-cycle from level l down, with their
+// phase keys (Dmax: coarsest depth over the batch).
+void plan_vcycle(const biot_ctx *h, int l, int K, int Dmax, std::vector<PlanOp> &out)
+{
+    const int D = h->L - 1, d = h->L - 1 - l;
+    const int up = Dmax * (K + 1) + 2 * K + Dmax * K;
+    for (int k = 0; k < K; k++) out.push_back({l, SWEEP_SMOOTH, l == 0 ? D * (K + 1) + k : d * (K + 1) + k});
+    if (l > 0) {
+        out.push_back({l, SWEEP_RESTRICT, d * (K + 1) + K});
+        plan_vcycle(h, l - 1, K, Dmax, out);
+    }
+    for (int k = 0; k < K; k++)
+        out.push_back({l, SWEEP_SMOOTH, l == 0 ? D * (K + 1) + K + k : up - (d + 1) * K + k});
+}
+
+int level_tkind(const biot_ctx *h, int l)
+{
+    const bool t64 = h->lv[l].fp64;
+    const bool c64 = (l > 0) ? h->lv[l - 1].fp64 : t64;
+    return t64 ? 0 : (c64 ? 1 : 2);
+}
+
+int level_variant(const biot_ctx *h, int l, int mode)
+{
+    const bool fine = l == h->L - 1;
+    return (fine ? 0 : SWEEP_V_COARSE) | (fine && !h->lv[l].fp64 ? SWEEP_V_LO : 0) |
+           (mode == SWEEP_RESTRICT ? SWEEP_V_RESTRICT : 0);
+}
+
+int tkind_slots(int tkind, int variant)
+{
+    return tkind == 0 ? sweep_slots<double, double>(variant)
+         : tkind == 1 ? sweep_slots<float, double>(variant) : sweep_slots<float, float>(variant);
+}
+
+// One launch of the batched schedule.
+struct BatchLaunch {
+    int tkind, variant;
+    size_t job_off, item_off;  // offsets into the job table of tkind and the item table
+    int njobs, nitems;
+};
+
+// A job of the schedule: which instance's which recorded sweep fills it.
+struct BatchSlot {
+    int inst, op;  // op: index into the instance's recorded sweeps of one step
+};
+
+}  // namespace
+
+struct biot_batch_s {
+    std::vector<biot_ctx *> inst;
+    cudaStream_t stream = nullptr;
+    int K = 0, ne = 0, Dmax = 0;
+    std::vector<BatchLaunch> launches;            // in issue order
+    std::vector<BatchSlot> slots[3];              // per tkind, parallel to the job tables
+    std::vector<SweepItem> items;
+    std::vector<size_t> nops;                     // recorded sweeps per instance and step
+    void *jobs_dev[2][3] = {};                    // per graph parity, per tkind
+    SweepItem *items_dev = nullptr;
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    std::vector<long> epoch[2];                   // instance epochs the graphs were captured at
+    long launches_per_step = 0, kernel_launches = 0, nstep = 0;
+    std::vector<void *> allocs;
+};
+
+namespace {
+
+size_t tkind_size(int tk)
+{
+    return tk == 0 ? sizeof(SweepArgs<double, double>) : tk == 1 ? sizeof(SweepArgs<float, double>) : sizeof(SweepArgs<float, float>);
+}
+
+int batch_alloc(biot_batch_s *b, void **p, size_t bytes)
+{
+    *p = nullptr;
+    if (!bytes) return BIOT_OK;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        cudaGetLastError();
+        return fail(e == cudaErrorMemoryAllocation ? BIOT_ERR_OOM : BIOT_ERR_CUDA, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    }
+    b->allocs.push_back(*p);
+    return BIOT_OK;
+}
+
+// Static schedule of one time step: phases by key, launches per storage kind,
+// strip work items sized so that each launch fills the GPU.
+int batch_plan(biot_batch_s *b)
+{
+    const int n = (int)b->inst.size();
+    std::vector<std::vector<PlanOp>> ops(n);
+    int maxkey = 0;
+    const int up = b->Dmax * (b->K + 1) + 2 * b->K + b->Dmax * b->K;
+    b->nops.assign(n, 0);
+    for (int i = 0; i < n; i++) {
+        std::vector<PlanOp> cyc;
+        plan_vcycle(b->inst[i], b->inst[i]->L - 1, b->K, b->Dmax, cyc);
+        for (int c = 0; c < b->ne; c++)
+            for (const PlanOp &o : cyc) ops[i].push_back({o.level, o.mode, c * up + o.key});
+        b->nops[i] = ops[i].size();
+        for (const PlanOp &o : ops[i]) maxkey = o.key > maxkey ? o.key : maxkey;
+    }
+    // bucket the ops by key, then by (tkind, variant)
+    std::vector<std::vector<BatchSlot>> bykey(maxkey + 1);
+    for (int i = 0; i < n; i++)
+        for (size_t j = 0; j < ops[i].size(); j++) bykey[ops[i][j].key].push_back({i, (int)j});
+    b->launches.clear();
+    b->items.clear();
+    for (int t = 0; t < 3; t++) b->slots[t].clear();
+    for (int key = 0; key <= maxkey; key++) {
+        for (int tk = 0; tk < 3; tk++) {
+            for (int v = 0; v < 8; v++) {
+                std::vector<BatchSlot> grp;
+                double cells = 0;
+                for (const BatchSlot &s : bykey[key]) {
+                    const biot_ctx *h = b->inst[s.inst];
+                    const PlanOp &o = ops[s.inst][s.op];
+                    if (level_tkind(h, o.level) != tk || level_variant(h, o.level, o.mode) != v) continue;
+                    grp.push_back(s);
+                    cells += (double)h->lv[o.level].np;
+                }
+                if (grp.empty()) continue;
+                const int slots = tkind_slots(tk, v);
+                if (!slots) return fail(BIOT_ERR_CUDA, "occupancy query of the batched sweep kernel failed");
+                BatchLaunch L{tk, v, b->slots[tk].size(), b->items.size(), (int)grp.size(), 0};
+                for (size_t g = 0; g < grp.size(); g++) {
+                    const biot_ctx *h = b->inst[grp[g].inst];
+                    const Level &Lv = h->lv[ops[grp[g].inst][grp[g].op].level];
+                    const int share = (int)(slots * (double)Lv.np / cells) + 1;
+                    const int ty = sweep_strip_rows(Lv.nx, Lv.ny, share);
+                    const int sx = (Lv.nx + SWEEP_STRIP_COLS - 1) / SWEEP_STRIP_COLS, sy = (Lv.ny + ty - 1) / ty;
+                    for (int by = 0; by < sy; by++)
+                        for (int bx = 0; bx < sx; bx++) b->items.push_back({(int)g, bx, by, ty});
+                    b->slots[tk].push_back(grp[g]);
+                }
+                L.nitems = (int)(b->items.size() - L.item_off);
+                b->launches.push_back(L);
+            }
+        }
+    }
+    int rc;
+    for (int par = 0; par < 2; par++)
+        for (int tk = 0; tk < 3; tk++)
+            if ((rc = batch_alloc(b, &b->jobs_dev[par][tk], b->slots[tk].size() * tkind_size(tk)))) return rc;
+    if ((rc = batch_alloc(b, (void **)&b->items_dev, b->items.size() * sizeof(SweepItem)))) return rc;
+    CUDA_TRY(cudaMemcpy(b->items_dev, b->items.data(), b->items.size() * sizeof(SweepItem), cudaMemcpyHostToDevice));
+    return BIOT_OK;
+}
+
+template <typename T, typename TC>
+cudaError_t batch_launch_typed(biot_batch_s *b, int par, const BatchLaunch &L)
+{
+    const SweepArgs<T, TC> *jobs = static_cast<const SweepArgs<T, TC> *>(b->jobs_dev[par][L.tkind]) + L.job_off;
+    return launch_sweep_batch<T, TC>(L.variant, jobs, b->items_dev + L.item_off, L.nitems, b->stream);
+}
+
+template <typename T, typename TC>
+void batch_fill_typed(biot_batch_s *b, int tk, std::vector<std::vector<SweepJob>> &rec, std::vector<unsigned char> &host)
+{
+    host.resize(b->slots[tk].size() * sizeof(SweepArgs<T, TC>));
+    SweepArgs<T, TC> *out = reinterpret_cast<SweepArgs<T, TC> *>(host.data());
+    for (size_t j = 0; j < b->slots[tk].size(); j++) {
+        const BatchSlot &s = b->slots[tk][j];
+        out[j] = job_args<T, TC>(rec[s.inst][s.op]);
+    }
+}
+
+// Capture one time step of every instance (parity par of the flow buffers).
+int batch_capture(biot_batch_s *b, int par)
+{
+    const int n = (int)b->inst.size();
+    std::vector<std::vector<SweepJob>> rec(n);
+    std::vector<long> l0(n), c0(n);
+    CUDA_TRY(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+    int rc = BIOT_OK;
+    long nl = 0;
+    for (int i = 0; i < n && !rc; i++) {
+        biot_ctx *h = b->inst[i];
+        l0[i] = h->launches;
+        c0[i] = h->total_cycles;
+        h->rec = &rec[i];
+        rc = advance(h);  // flow step and force are launched (captured); the sweeps are recorded
+        h->rec = nullptr;
+        nl += h->launches - l0[i];
+        if (!rc && rec[i].size() != b->nops[i]) rc = fail(BIOT_ERR_CUDA, "batched schedule does not match the recorded sweeps");
+    }
+    for (size_t k = 0; k < b->launches.size() && !rc; k++) {
+        const BatchLaunch &L = b->launches[k];
+        cudaError_t e = L.tkind == 0 ? batch_launch_typed<double, double>(b, par, L)
+                      : L.tkind == 1 ? batch_launch_typed<float, double>(b, par, L)
+                                     : batch_launch_typed<float, float>(b, par, L);
+        if (e != cudaSuccess) rc = fail(BIOT_ERR_CUDA, std::string("batched sweep launch: ") + cudaGetErrorString(e));
+        nl++;
+    }
+    for (int i = 0; i < n && !rc; i++) {
+        biot_ctx *h = b->inst[i];
+        cudaError_t e = cudaMemcpyAsync(h->resmax_host, h->resmax, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, b->stream);
+        if (e != cudaSuccess) rc = fail(BIOT_ERR_CUDA, std::string("cudaMemcpyAsync: ") + cudaGetErrorString(e));
+    }
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(b->stream, &g);
+    if (!rc && e != cudaSuccess) rc = fail(BIOT_ERR_CUDA, std::string("cudaStreamEndCapture: ") + cudaGetErrorString(e));
+    if (!rc) {
+        e = cudaGraphInstantiate(&b->graph[par], g, 0);
+        if (e != cudaSuccess) {
+            b->graph[par] = nullptr;
+            rc = fail(BIOT_ERR_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+        }
+    }
+    if (g) cudaGraphDestroy(g);
+    if (rc) return rc;
+    // job tables of this parity
+    std::vector<unsigned char> host;
+    for (int tk = 0; tk < 3; tk++) {
+        if (b->slots[tk].empty()) continue;
+        if (tk == 0) batch_fill_typed<double, double>(b, tk, rec, host);
+        else if (tk == 1) batch_fill_typed<float, double>(b, tk, rec, host);
+        else batch_fill_typed<float, float>(b, tk, rec, host);
+        CUDA_TRY(cudaMemcpy(b->jobs_dev[par][tk], host.data(), host.size(), cudaMemcpyHostToDevice));
+    }
+    b->launches_per_step = nl;
+    b->epoch[par].clear();
+    for (int i = 0; i < n; i++) b->epoch[par].push_back(b->inst[i]->epoch);
+    // capture recorded the state transitions; replay them from the start state
+    for (int i = 0; i < n; i++) {
+        biot_ctx *h = b->inst[i];
+        h->launches = l0[i];
+        h->total_cycles = c0[i];
+        h->fcur ^= 1;
+        std::swap(h->D1, h->D2);
+        h->nstep -= 1;
+    }
+    return BIOT_OK;
+}
+
+void batch_release(biot_batch_s *b)
+{
+    if (!b) return;
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    for (int i = 0; i < 2; i++)
+        if (b->graph[i]) cudaGraphExecDestroy(b->graph[i]);
+    for (void *p : b->allocs) cudaFree(p);
+    for (biot_ctx *h : b->inst) release(h);
+    if (b->stream) cudaStreamDestroy(b->stream);
+    delete b;
+}
+
+}  // namespace
+
+extern "C" {
+
+int biot_batch_create(int count, const biot_params *params, const biot_side *sides, biot_batch *out)
+{
+    if (!out) return fail(BIOT_ERR_INVALID_ARG, "null output handle");
+    *out = nullptr;
+    if (count < 1 || !params || !sides) return fail(BIOT_ERR_INVALID_ARG, "need count >= 1 and parameter / side arrays");
+    for (int i = 0; i < count; i++) {
+        if (params[i].ne_fixed <= 0) return fail(BIOT_ERR_INVALID_ARG, "batched instances need a fixed number of V-cycles (ne_fixed > 0)");
+        if (params[i].K != params[0].K || params[i].ne_fixed != params[0].ne_fixed)
+            return fail(BIOT_ERR_INVALID_ARG, "batched instances need equal K and ne_fixed");
+    }
+    biot_batch_s *b = new (std::nothrow) biot_batch_s();
+    if (!b) return fail(BIOT_ERR_OOM, "host allocation failed");
+    if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        b->stream = nullptr;
+        delete b;
+        return fail(BIOT_ERR_CUDA, "cudaStreamCreate failed");
+    }
+    b->K = params[0].K;
+    b->ne = params[0].ne_fixed;
+    for (int i = 0; i < count; i++) {
+        biot_handle h = nullptr;
+        int rc = biot_create(&params[i], &sides[4 * i], &h);
+        if (rc) {
+            const std::string msg = "instance " + std::to_string(i) + ": " + g_last_error;
+            batch_release(b);
+            return fail(rc, msg);
+        }
+        b->inst.push_back(h);
+        if (cudaStreamSynchronize(h->stream) != cudaSuccess) {
+            batch_release(b);
+            return fail(BIOT_ERR_CUDA, "instance set-up failed");
+        }
+        h->stream = b->stream;
+        b->Dmax = h->L - 1 > b->Dmax ? h->L - 1 : b->Dmax;
+    }
+    int rc = batch_plan(b);
+    if (rc) {
+        batch_release(b);
+        return rc;
+    }
+    *out = b;
+    return BIOT_OK;
+}
+
+int biot_batch_destroy(biot_batch b)
+{
+    batch_release(b);
+    return BIOT_OK;
+}
+
+int biot_batch_size(biot_batch b, int *count)
+{
+    if (!b || !count) return fail(BIOT_ERR_INVALID_ARG, "null argument");
+    *count = (int)b->inst.size();
+    return BIOT_OK;
+}
+
+int biot_batch_instance(biot_batch b, int i, biot_handle *out)
+{
+    if (!b || !out || i < 0 || i >= (int)b->inst.size()) return fail(BIOT_ERR_INVALID_ARG, "bad batch, index or output");
+    *out = b->inst[i];
+    return BIOT_OK;
+}
+
+int biot_batch_step(biot_batch b, int n)
+{
+    if (!b || n < 0) return fail(BIOT_ERR_INVALID_ARG, "bad batch or step count");
+    int rc;
+    for (biot_ctx *h : b->inst) {
+        if (h->diverged) return fail(BIOT_ERR_DIVERGED, "an instance of the batch has diverged");
+        if (h->stream != b->stream) return fail(BIOT_ERR_INVALID_ARG, "an instance of the batch was moved to another stream");
+        if ((rc = ensure_initialized(h))) return rc;
+        if (!h->solved) {
+            rc = elastic_solve(h);
+            if (rc && rc != BIOT_ERR_NOT_CONVERGED) return rc;
+        }
+    }
+    const int par = b->inst[0]->fcur;
+    for (biot_ctx *h : b->inst)
+        if (h->fcur != par) return fail(BIOT_ERR_INVALID_ARG, "instances of the batch were stepped separately");
+    for (int par2 = 0; par2 < 2; par2++) {  // re-capture after an instance's arguments changed
+        bool stale = false;
+        for (size_t i = 0; i < b->inst.size() && b->graph[par2]; i++)
+            stale = stale || b->epoch[par2][i] != b->inst[i]->epoch;
+        if (stale) {
+            cudaGraphExecDestroy(b->graph[par2]);
+            b->graph[par2] = nullptr;
+        }
+    }
+    for (int s = 0; s < n; s++) {
+        const int p = b->inst[0]->fcur;
+        if (!b->graph[p] && (rc = batch_capture(b, p))) return rc;
+        CUDA_TRY(cudaGraphLaunch(b->graph[p], b->stream));
+        b->kernel_launches += b->launches_per_step;
+        b->nstep++;
+        for (biot_ctx *h : b->inst) {
+            h->fcur ^= 1;
+            std::swap(h->D1, h->D2);
+            h->nstep += 1;
+            h->total_cycles += h->P.ne_fixed;
+            h->last_ne = h->P.ne_fixed;
+            h->solved = true;
+            h->pending_res = true;
+        }
+    }
+    int status = BIOT_OK;
+    for (biot_ctx *h : b->inst)
+        if ((rc = finish_pending(h))) status = rc;
+    return status;
+}
+
+int biot_batch_stats_get(biot_batch b, long *kernel_launches, long *launches_per_step, long *work_items_per_step)
+{
+    if (!b) return fail(BIOT_ERR_INVALID_ARG, "null batch");
+    if (kernel_launches) *kernel_launches = b->kernel_launches;
+    if (launches_per_step) *launches_per_step = b->launches_per_step;
+    if (work_items_per_step) *work_items_per_step = (long)b->items.size();
+    return BIOT_OK;
+}
+
+}  // extern "C"
+
+// ============================================================================
+// Serving: a request loop with continuous batching.
+//
+// A scheduler thread admits queued requests while the device-memory budget and
+// the resident-slot limit allow, keeps every admitted instance (populations and
+// multigrid hierarchy) resident on its own stream, and in each tick launches the
+// next time steps of all resident instances before waiting for any of them, so
+// that their kernels overlap on the GPU.  A finished instance is read out into
+// host memory and freed at once, which admits the next request.
+// ============================================================================
+namespace {
+
+size_t estimate_bytes(const biot_params *p, const biot_side *sides)
+{
+    const bool fp32 = p->precision == BIOT_FP32;
+    const size_t tsz = fp32 ? 4 : 8, np = (size_t)p->nx * p->ny;
+    size_t b = 0;
+    for (int l = 0; l < p->mg_levels; l++) {
+        const int shift = p->mg_levels - 1 - l;
+        const size_t nx = (size_t)(p->nx >> shift), ny = (size_t)(p->ny >> shift), n = nx * ny;
+        const bool fp64 = !fp32 || (l == 0 && p->mg_levels > 1);
+        const size_t esz = fp64 ? 8 : 4;
+        b += 2 * 8 * n * esz;
+        if (!fp64 && l == p->mg_levels - 1) b += 2 * 2 * n * esz;
+        if (l < p->mg_levels - 1) b += 8 * n * esz;
+        for (int s = 0; s < 4; s++)
+            if (sides && sides[s].eta_type == BIOT_DIRICHLET) b += 3 * ((s == BIOT_BOTTOM || s == BIOT_TOP) ? nx : ny) * esz;
+    }
+    b += (2 * 9 + 2 + 2) * np * tsz + 3 * np * 8 + 16;
+    for (int s = 0; s < 4; s++) {
+        const size_t m = 2 * (size_t)((s == BIOT_BOTTOM || s == BIOT_TOP) ? p->nx : p->ny) + 1;
+        if (sides && sides[s].eta_profile) b += 2 * m * 8;
+        if (sides && sides[s].p_profile) b += m * 8;
+    }
+    b += 6 * np * 8;  // read-out buffer
+    return b;
+}
+
+enum { REQ_QUEUED = 0, REQ_RUNNING = 1, REQ_DONE = 2, REQ_FAILED = 3 };
+
+struct Request {
+    uint64_t id = 0;
+    biot_params P{};
+    biot_side sides[4]{};
+    std::vector<double> prof[4][2];  // owned copies of the boundary data
+    long target = 0;                 // physical steps to take
+    size_t bytes = 0;
+    int state = REQ_QUEUED, status = BIOT_OK;
+    std::string error;
+    double t_submit = 0, t_start = 0, t_done = 0;
+    biot_ctx *h = nullptr;
+    std::vector<double> eta, p;
+    double t_result = 0;
+};
+
+}  // namespace
+
+struct biot_server_s {
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::thread worker;
+    bool stop = false;
+    size_t budget = 0, used = 0, peak_used = 0;
+    int max_resident = 0, peak_resident = 0;
+    uint64_t next_id = 1;
+    std::deque<uint64_t> queue;
+    std::map<uint64_t, Request> req;
+    std::vector<Request *> resident;  // worker thread only (map entries are stable)
+    std::chrono::steady_clock::time_point t0;
+    long ticks = 0, graph_launches = 0;
+    int device = 0;
+    double now() const { return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count(); }
+};
+
+namespace {
+
+// Finish a resident request (worker thread, lock not held while reading out).
+void server_finish(biot_server_s *S, Request &r, int status, const std::string &err)
+{
+    if (status == BIOT_OK) {
+        const size_t np = (size_t)r.P.nx * r.P.ny;
+        r.eta.resize(2 * np);
+        r.p.resize(np);
+        int rc = biot_read_u(r.h, r.eta.data(), &r.t_result);
+        if (!rc) rc = biot_read_p(r.h, r.p.data(), nullptr);
+        if (rc) {
+            status = rc;
+            r.error = g_last_error;
+        }
+    } else {
+        r.error = err;
+    }
+    release(r.h);
+    r.h = nullptr;
+    std::lock_guard<std::mutex> lock(S->mu);
+    S->used -= r.bytes;
+    r.status = status;
+    r.state = status == BIOT_OK ? REQ_DONE : REQ_FAILED;
+    r.t_done = S->now();
+    S->cv_done.notify_all();
+}
+
+void server_loop(biot_server_s *S)
+{
+    cudaSetDevice(S->device);
+    for (;;) {
+        // admission: memory budget and resident slots
+        std::vector<Request *> admit;
+        {
+            std::unique_lock<std::mutex> lock(S->mu);
+            if (S->resident.empty())
+                S->cv_work.wait(lock, [&] { return S->stop || !S->queue.empty(); });
+            if (S->stop) break;
+            while (!S->queue.empty() && (int)(S->resident.size() + admit.size()) < S->max_resident) {
+                Request &r = S->req[S->queue.front()];
+                if (S->used + r.bytes > S->budget) break;
+                S->used += r.bytes;
+                S->peak_used = S->used > S->peak_used ? S->used : S->peak_used;
+                r.state = REQ_RUNNING;
+                r.t_start = S->now();
+                admit.push_back(&r);
+                S->queue.pop_front();
+            }
+        }
+        for (Request *r : admit) {
+            biot_handle h = nullptr;
+            int rc = biot_create(&r->P, r->sides, &h);
+            if (!rc) rc = ensure_initialized(h);
+            if (!rc) {
+                rc = elastic_solve(h);  // the solve at t = 0 (launch-only with fixed V-cycles)
+                if (rc == BIOT_ERR_NOT_CONVERGED) rc = BIOT_OK;
+            }
+            r->h = h;
+            if (rc) {
+                const std::string err = g_last_error;
+                if (h) server_finish(S, *r, rc, err);
+                else {
+                    std::lock_guard<std::mutex> lock(S->mu);
+                    S->used -= r->bytes;
+                    r->status = rc;
+                    r->error = err;
+                    r->state = REQ_FAILED;
+                    r->t_done = S->now();
+                    S->cv_done.notify_all();
+                }
+                continue;
+            }
+            S->resident.push_back(r);
+        }
+        {
+            std::lock_guard<std::mutex> lock(S->mu);
+            S->peak_resident = (int)S->resident.size() > S->peak_resident ? (int)S->resident.size() : S->peak_resident;
+        }
+        if (S->resident.empty()) continue;
+        // one tick: launch a few steps of every resident instance, then wait
+        const int per_tick = 4;
+        std::vector<int> st(S->resident.size(), BIOT_OK);
+        for (size_t k = 0; k < S->resident.size(); k++) {
+            Request &r = *S->resident[k];
+            for (int j = 0; j < per_tick && r.h->nstep < r.target && !st[k]; j++) {
+                const bool graphs = r.h->P.ne_fixed > 0 && r.h->use_graphs;
+                st[k] = graphs ? advance_graph(r.h) : advance(r.h);
+                if (st[k] == BIOT_ERR_NOT_CONVERGED) st[k] = BIOT_OK;
+                S->graph_launches++;
+            }
+        }
+        std::vector<Request *> keep;
+        for (size_t k = 0; k < S->resident.size(); k++) {
+            Request &r = *S->resident[k];
+            int rc = st[k];
+            std::string err = rc ? g_last_error : std::string();
+            if (!rc && (rc = finish_pending(r.h))) err = g_last_error;  // synchronises this instance's stream
+            if (rc) server_finish(S, r, rc, err);
+            else if (r.h->nstep >= r.target) server_finish(S, r, BIOT_OK, "");
+            else keep.push_back(&r);
+        }
+        S->resident.swap(keep);
+        S->ticks++;
+    }
+    // shutdown: drop whatever is resident
+    for (Request *r : S->resident) {
+        if (r->h) release(r->h);
+        r->h = nullptr;
+    }
+    S->resident.clear();
+}
+
+}  // namespace
+
+extern "C" {
+
+int biot_estimate_bytes(const biot_params *p, const biot_side sides[4], size_t *bytes)
+{
+    if (!p || !bytes) return fail(BIOT_ERR_INVALID_ARG, "null argument");
+    int rc = check_params(p, sides);
+    if (rc) return rc;
+    *bytes = estimate_bytes(p, sides);
+    return BIOT_OK;
+}
+
+int biot_server_create(size_t mem_budget_bytes, int max_resident, biot_server *out)
+{
+    if (!out) return fail(BIOT_ERR_INVALID_ARG, "null output handle");
+    *out = nullptr;
+    if (mem_budget_bytes == 0 || max_resident < 1) return fail(BIOT_ERR_INVALID_ARG, "need a memory budget and max_resident >= 1");
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+        cudaGetLastError();
+        return fail(BIOT_ERR_NO_DEVICE, "no CUDA device visible");
+    }
+    biot_server_s *S = new (std::nothrow) biot_server_s();
+    if (!S) return fail(BIOT_ERR_OOM, "host allocation failed");
+    S->budget = mem_budget_bytes;
+    S->max_resident = max_resident;
+    S->t0 = std::chrono::steady_clock::now();
+    cudaGetDevice(&S->device);
+    try {
+        S->worker = std::thread(server_loop, S);
+    } catch (...) {
+        delete S;
+        return fail(BIOT_ERR_OOM, "cannot start the scheduler thread");
+    }
+    *out = S;
+    return BIOT_OK;
+}
+
+int biot_server_submit(biot_server S, const biot_params *p, const biot_side sides[4], double T, uint64_t *id)
+{
+    if (!S || !p || !sides || !id) return fail(BIOT_ERR_INVALID_ARG, "null argument");
+    int rc = check_params(p, sides);
+    if (rc) return rc;
+    if (!(T >= 0)) return fail(BIOT_ERR_INVALID_ARG, "end time must be >= 0");
+    Request r;
+    r.P = *p;
+    r.target = (long)std::floor(T / p->dt + 0.5);
+    r.bytes = estimate_bytes(p, sides);
+    for (int s = 0; s < 4; s++) {
+        r.sides[s] = sides[s];
+        const size_t m = 2 * (size_t)((s == BIOT_BOTTOM || s == BIOT_TOP) ? p->nx : p->ny) + 1;
+        if (sides[s].eta_profile) {
+            r.prof[s][0].assign(sides[s].eta_profile, sides[s].eta_profile + 2 * m);
+            r.sides[s].eta_profile = r.prof[s][0].data();
+        }
+        if (sides[s].p_profile) {
+            r.prof[s][1].assign(sides[s].p_profile, sides[s].p_profile + m);
+            r.sides[s].p_profile = r.prof[s][1].data();
+        }
+    }
+    std::lock_guard<std::mutex> lock(S->mu);
+    if (r.bytes > S->budget) return fail(BIOT_ERR_OOM, "the request alone needs more device memory than the server's budget");
+    r.id = S->next_id++;
+    r.t_submit = S->now();
+    *id = r.id;
+    const uint64_t rid = r.id;
+    Request &slot = S->req[rid];
+    slot = std::move(r);
+    for (int s = 0; s < 4; s++) {  // re-point the copies after the move
+        if (!slot.prof[s][0].empty()) slot.sides[s].eta_profile = slot.prof[s][0].data();
+        if (!slot.prof[s][1].empty()) slot.sides[s].p_profile = slot.prof[s][1].data();
+    }
+    S->queue.push_back(rid);
+    S->cv_work.notify_one();
+    return BIOT_OK;
+}
+
+int biot_server_poll(biot_server S, uint64_t id, biot_request_info *info)
+{
+    if (!S || !info) return fail(BIOT_ERR_INVALID_ARG, "null argument");
+    std::lock_guard<std::mutex> lock(S->mu);
+    auto it = S->req.find(id);
+    if (it == S->req.end()) return fail(BIOT_ERR_INVALID_ARG, "unknown request id");
+    const Request &r = it->second;
+    info->state = r.state;
+    info->status = r.status;
+    info->t_submit = r.t_submit;
+    info->t_start = r.t_start;
+    info->t_done = r.t_done;
+    info->nx = r.P.nx;
+    info->ny = r.P.ny;
+    info->steps = r.target;
+    info->device_bytes = r.bytes;
+    return BIOT_OK;
+}
+
+int biot_server_wait(biot_server S, uint64_t id, double timeout_s)
+{
+    if (!S) return fail(BIOT_ERR_INVALID_ARG, "null server");
+    std::unique_lock<std::mutex> lock(S->mu);
+    auto it = S->req.find(id);
+    if (it == S->req.end()) return fail(BIOT_ERR_INVALID_ARG, "unknown request id");
+    const bool ok = S->cv_done.wait_for(lock, std::chrono::duration<double>(timeout_s > 0 ? timeout_s : 0.0), [&] {
+        return it->second.state == REQ_DONE || it->second.state == REQ_FAILED;
+    });
+    if (!ok) return fail(BIOT_ERR_TIMEOUT, "request not finished within the timeout");
+    if (it->second.state == REQ_FAILED) return fail(it->second.status, it->second.error);
+    return BIOT_OK;
+}
+
+int biot_server_fetch(biot_server S, uint64_t id, double *eta, double *p, double *t_out)
+{
+    if (!S) return fail(BIOT_ERR_INVALID_ARG, "null server");
+    std::lock_guard<std::mutex> lock(S->mu);
+    auto it = S->req.find(id);
+    if (it == S->req.end()) return fail(BIOT_ERR_INVALID_ARG, "unknown request id");
+    Request &r = it->second;
+    if (r.state == REQ_FAILED) return fail(r.status, r.error);
+    if (r.state != REQ_DONE) return fail(BIOT_ERR_INVALID_ARG, "request not finished");
+    if (eta) std::memcpy(eta, r.eta.data(), r.eta.size() * sizeof(double));
+    if (p) std::memcpy(p, r.p.data(), r.p.size() * sizeof(double));
+    if (t_out) *t_out = r.t_result;
+    return BIOT_OK;
+}
+
+int biot_server_release(biot_server S, uint64_t id)
+{
+    if (!S) return fail(BIOT_ERR_INVALID_ARG, "null server");
+    std::lock_guard<std::mutex> lock(S->mu);
+    auto it = S->req.find(id);
+    if (it == S->req.end()) return fail(BIOT_ERR_INVALID_ARG, "unknown request id");
+    if (it->second.state != REQ_DONE && it->second.state != REQ_FAILED) return fail(BIOT_ERR_INVALID_ARG, "request not finished");
+    S->req.erase(it);
+    return BIOT_OK;
+}
+
+int biot_server_stats_get(biot_server S, biot_server_stats *o)
+{
+    if (!S || !o) return fail(BIOT_ERR_INVALID_ARG, "null argument");
+    std::lock_guard<std::mutex> lock(S->mu);
+    o->queued = (int)S->queue.size();
+    o->peak_resident = S->peak_resident;
+    o->used_bytes = S->used;
+    o->peak_bytes = S->peak_used;
+    o->ticks = S->ticks;
+    o->graph_launches = S->graph_launches;
+    return BIOT_OK;
+}
+
+int biot_server_destroy(biot_server S)
+{
+    if (!S) return BIOT_OK;
+    {
+        std::lock_guard<std::mutex> lock(S->mu);
+        S->stop = true;
+        S->cv_work.notify_all();
+    }
+    if (S->worker.joinable()) S->worker.join();
+    delete S;
+    return BIOT_OK;
+}
+
+}  // extern "C"

@@ -118,13 +118,21 @@ def manufactured_params(n: int, alpha: float, r: float, ne_fixed=3, K=2):
     return p, sides
 
 
-def batched_instances(count: int = 64, seed: int = 2409):
+def batched_instances(count: int = 64, seed: int = 2409, max_modulus: float = 2.5, max_coupling: float = 4.0):
     """Seeded uneven instances: side uniform in {64,128,256,512} cells, lambda, mu
     log-uniform [0.1, 10], alpha U[0.5, 1], c0 log-U[1e-3, 1], kappa log-U[1e-3, 1],
-    a partial top load on a seeded interval of length >= 1/8, fixed MG(3,4)."""
+    a partial top load on a seeded interval of length >= 1/8, fixed MG(3,4),
+    L = log2(N) - 2 levels, FP32.
+
+    The pseudo-time multigrid of the method diverges when the lattice P-wave
+    modulus c0 (lambda + 2 mu) exceeds about 3, and the coupled scheme when
+    alpha^2 / (c0 (lambda + 2 mu)) is large (checked with the FP64 oracle), so
+    draws with c0 (lambda + 2 mu) > max_modulus or alpha^2 / (c0 (lambda + 2 mu))
+    > max_coupling are drawn again.  The time step gives a lattice permeability
+    kappa dt / (c0 h^2) = 1 (the diffusive scaling dt ~ h^2 of the paper)."""
     rng = np.random.default_rng(seed)
     out = []
-    for _ in range(count):
+    while len(out) < count:
         n = int(rng.choice([64, 128, 256, 512]))
         lam = float(10 ** rng.uniform(-1, 1))
         mu = float(10 ** rng.uniform(-1, 1))
@@ -133,9 +141,35 @@ def batched_instances(count: int = 64, seed: int = 2409):
         kappa = float(10 ** rng.uniform(-3, 0))
         a = float(rng.uniform(0.0, 7.0 / 8.0))
         b = float(rng.uniform(a + 1.0 / 8.0, 1.0))
-        x = np.arange(2 * n + 1) * (1.0 / n) / 2.0
+        modulus = c0 * (lam + 2.0 * mu)
+        if modulus > max_modulus or alpha * alpha / modulus > max_coupling:
+            continue
+        h = 1.0 / n
+        x = np.arange(2 * n + 1) * h / 2.0
         load = np.where((x > a) & (x < b), 1.0, 0.0)
-        p = _params(n, lam=lam, mu=mu, alpha=alpha, c0=c0, kappa=kappa, dt=0.1 / 100,
+        p = _params(n, lam=lam, mu=mu, alpha=alpha, c0=c0, kappa=kappa, dt=c0 * h * h / kappa,
                     levels=int(np.log2(n)) - 2, ne_fixed=3, precision=FP32)
         out.append((p, top_load_sides(n, load)))
+    return out
+
+
+def served_requests(count: int = 200, seed: int = 11382, mean_in_flight: float = 8.0,
+                    mean_service_s: float = 0.05, sizes=(64, 128, 256, 512, 1024), steps: int = 100,
+                    T: float = 0.1):
+    """Seeded Poisson request stream: ``count`` consolidation solves with side
+    uniform in ``sizes`` cells (65..1025 nodes), the material values and
+    boundary conditions of the 4097x4097 Terzaghi case (lambda = mu = 1,
+    alpha = 1, c0 = 0.1, kappa = 1e-2), each to T in ``steps`` steps with fixed
+    MG(3,4) and L = log2(N) - 2 levels, FP32.  Inter-arrival times are
+    exponential with mean mean_service_s / mean_in_flight.  Returns a list of
+    (arrival_s, params, sides, T)."""
+    rng = np.random.default_rng(seed)
+    t = 0.0
+    out = []
+    for _ in range(count):
+        t += float(rng.exponential(mean_service_s / mean_in_flight))
+        n = int(rng.choice(list(sizes)))
+        p = _params(n, lam=1.0, mu=1.0, alpha=1.0, c0=0.1, kappa=1e-2, dt=T / steps,
+                    levels=int(np.log2(n)) - 2, ne_fixed=3, precision=FP32)
+        out.append((t, p, top_load_sides(n, uniform_load(n)), T))
     return out

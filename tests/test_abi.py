@@ -99,3 +99,24 @@ def test_error_strings(lib):
     from paper_2409_11382_gb300 import biot
     for code in (biot.OK, biot.ERR_INVALID_ARG, biot.ERR_DIVERGED, biot.ERR_NO_DEVICE):
         assert lib.biot_error_string(code)
+
+
+def test_estimate_bytes_validates_without_a_device(lib):
+    from paper_2409_11382_gb300 import biot, workloads as W
+    p, sides, _ = W.terzaghi_33(precision=W.FP32)
+    n = biot.estimate_bytes(p, sides)
+    cells = 32 * 32
+    assert n > 100 * cells  # populations of all levels, flow, coupling and read-out planes
+    with pytest.raises(biot.BiotError) as e:
+        biot.estimate_bytes(dict(p, nx=30), sides)
+    assert e.value.code == biot.ERR_INVALID_ARG
+
+
+def test_server_needs_a_device(lib):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a device is present")
+    from paper_2409_11382_gb300 import biot
+    with pytest.raises(biot.BiotError) as e:
+        biot.Server(1 << 30, 4)
+    assert e.value.code in (biot.ERR_NO_DEVICE, biot.ERR_CUDA)
