@@ -226,6 +226,7 @@ def run_ours(args):
     cells = nx * ny
     stream = torch.cuda.current_stream()
     solver = biot.Solver(params, sides, stream=stream.cuda_stream)
+    tuned = solver.autotune() if not args.no_tune else None  # launch shapes (results unchanged)
 
     for _ in range(args.warmup):
         solver.step(1)
@@ -309,7 +310,8 @@ def run_ours(args):
                    "ne_fixed": params["ne_fixed"], "K": params["K"], "gamma": params["gamma"],
                    "precision": "fp32 populations; fp64 residual norms, coarsest level, coupling",
                    "l2": "state (3.4 GB) larger than L2; no flush needed",
-                   "parallelism": f"replicas{world}"},
+                   "parallelism": f"replicas{world}",
+                   "autotuned_strip_rows": tuned},
         "roofline": {"kernel": "k_sweep_mom<float,float> finest level, smoothing", "bound": "hbm",
                      "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "peak_kind": f"{peak_kind} copy bandwidth (burst)",
@@ -490,6 +492,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-tune", action="store_true", help="skip biot_autotune (default launch shapes)")
     ap.add_argument("--n", type=int, default=4096, help="cells per side (4096 = the benchmark workload)")
     ap.add_argument("--workload", choices=["single", "batched", "served"], default="single")
     ap.add_argument("--instances", type=int, default=64, help="batched: number of instances")

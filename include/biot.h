@@ -58,7 +58,10 @@ extern "C" {
                         the finest level kept as double-float (two FP32 planes); FP64
                         for residual norms, the coarsest multigrid level and the
                         divergence / pressure accumulations of the coupling */
-/* In both precisions the elastic state is stored as the MRT moments of the
+#define BIOT_FP32_COARSE64 2  /* BIOT_FP32 on the finest level (elastic state and flow
+                                 populations), FP64 on every coarser multigrid level:
+                                 the coarse-grid corrections are not rounded to FP32 */
+/* In every precision the elastic state is stored as the MRT moments of the
  * populations (an exact change of basis, eqs. moments / moments:stress). */
 
 /* ---- boundary condition types (§3.6) --------------------------------------- */
@@ -191,6 +194,27 @@ BIOT_API const char *biot_last_error(void);
  * device time (ms) and the number of such launches since the last enable. */
 BIOT_API int biot_sweep_timing(biot_handle h, int enable);
 BIOT_API int biot_sweep_timing_get(biot_handle h, double *ms_total, long *launches);
+
+/* Checkpoint / resume.  biot_save writes the resumable state (flow populations,
+ * finest elastic state, explicit force, divergence history, time and counters)
+ * into a host buffer of biot_checkpoint_size bytes; biot_load restores it into an
+ * instance created with the same grid, levels and precision (boundary data and
+ * sources are not part of the checkpoint).  Stepping on from a loaded checkpoint
+ * gives bitwise the result of the uninterrupted run. */
+BIOT_API int biot_checkpoint_size(biot_handle h, size_t *bytes);
+BIOT_API int biot_save(biot_handle h, void *buf, size_t size);
+BIOT_API int biot_load(biot_handle h, const void *buf, size_t size);
+
+/* Autotune the launch shape of the multigrid sweeps: for every level run as
+ * strips (more than 256^2 cells) and both sweep modes (smoothing, residual +
+ * restriction), time candidate strip heights (4 .. 96 rows) on a scratch
+ * instance of the same shape (allocated for the call, then freed) and keep
+ * the fastest for this instance.  Strip heights do not change the arithmetic:
+ * results are bitwise the same as untuned.  rows_out / ms_out (may be NULL)
+ * receive 2 values per level (smoothing, restriction; level 0 = coarsest) for
+ * the first max_levels levels: the rows chosen (0 = not tuned) and the mean
+ * time of one sweep (ms). */
+BIOT_API int biot_autotune(biot_handle h, int *rows_out, double *ms_out, int max_levels);
 
 /* ---- batched execution ----------------------------------------------------------
  * Many independent instances (different grids, materials, boundary data) advanced

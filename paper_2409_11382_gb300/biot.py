@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(_HERE, "libbiot_gb300.so")
 
 OK, ERR_INVALID_ARG, ERR_OOM, ERR_DIVERGED, ERR_NOT_CONVERGED, ERR_CUDA, ERR_TIMEOUT, ERR_NO_DEVICE = (
     0, -1, -2, -3, -4, -5, -6, -7)
-FP64, FP32 = 0, 1
+FP64, FP32, FP32_COARSE64 = 0, 1, 2
 PERIODIC, SYMMETRY, DIRICHLET, NEUMANN = 0, 1, 2, 3
 BOTTOM, RIGHT, TOP, LEFT = 0, 1, 2, 3
 
@@ -32,7 +32,7 @@ API_FUNCTIONS = (
     "biot_batch_step", "biot_batch_stats_get",
     "biot_estimate_bytes", "biot_server_create", "biot_server_submit", "biot_server_poll",
     "biot_server_wait", "biot_server_fetch", "biot_server_release", "biot_server_stats_get",
-    "biot_server_destroy",
+    "biot_server_destroy", "biot_autotune", "biot_checkpoint_size", "biot_save", "biot_load",
 )
 REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_FAILED = 0, 1, 2, 3
 NOALLOC_MAX_CELLS = 262144  # BIOT_NOALLOC_MAX_CELLS of include/biot.h
@@ -116,6 +116,10 @@ def load_library(path: str = LIB_PATH):
     lib.biot_batch_instance.argtypes = [H, C.c_int, C.POINTER(H)]
     lib.biot_batch_step.argtypes = [H, C.c_int]
     lib.biot_batch_stats_get.argtypes = [H, C.POINTER(C.c_long), C.POINTER(C.c_long), C.POINTER(C.c_long)]
+    lib.biot_autotune.argtypes = [H, C.POINTER(C.c_int), P, C.c_int]
+    lib.biot_checkpoint_size.argtypes = [H, C.POINTER(C.c_size_t)]
+    lib.biot_save.argtypes = [H, C.c_void_p, C.c_size_t]
+    lib.biot_load.argtypes = [H, C.c_void_p, C.c_size_t]
     lib.biot_estimate_bytes.argtypes = [C.POINTER(biot_params), C.POINTER(biot_side), C.POINTER(C.c_size_t)]
     lib.biot_server_create.argtypes = [C.c_size_t, C.c_int, C.POINTER(H)]
     lib.biot_server_submit.argtypes = [H, C.POINTER(biot_params), C.POINTER(biot_side), C.c_double,
@@ -272,6 +276,30 @@ class Solver:
     def read_stress(self, out: Optional[np.ndarray] = None):
         out = np.empty((3, self.ny, self.nx)) if out is None else out
         self._check(self._lib.biot_read_stress(self._h, _dptr(out)), "biot_read_stress")
+        return out
+
+    def save(self) -> bytes:
+        """biot_save: the resumable state as bytes."""
+        n = C.c_size_t()
+        self._check(self._lib.biot_checkpoint_size(self._h, C.byref(n)), "biot_checkpoint_size")
+        buf = C.create_string_buffer(n.value)
+        self._check(self._lib.biot_save(self._h, buf, n), "biot_save")
+        return buf.raw
+
+    def load(self, data: bytes):
+        buf = C.create_string_buffer(data, len(data))
+        self._check(self._lib.biot_load(self._h, buf, len(data)), "biot_load")
+
+    def autotune(self, levels: int = 16) -> dict:
+        """biot_autotune: strip height and time per level and sweep mode."""
+        rows = (C.c_int * (2 * levels))()
+        ms = (C.c_double * (2 * levels))()
+        self._check(self._lib.biot_autotune(self._h, rows, ms, levels), "biot_autotune")
+        out = {}
+        for l in range(levels):
+            for m, name in ((0, "smooth"), (1, "restrict")):
+                if rows[2 * l + m]:
+                    out[f"L{l}_{name}"] = (rows[2 * l + m], round(ms[2 * l + m], 5))
         return out
 
     def stats(self) -> dict:

@@ -40,6 +40,7 @@ struct SweepArgs {
     double coef_fstar;           // alpha^2 r / 2 (self-dependence force)
     double c0h;                  // c0 * h (lattice traction per unit traction)
     unsigned long long *resmax;  // [2] ordered bits of max|g - g**| and max|g|, or nullptr
+    int rows;                    // strip height of the launch (0: the default choice)
     // the same coefficients, evaluated once on the host in the storage type:
     T k_fs;   // coef_fstar * dD/dm_s = -(alpha^2 r / 2) * 3 / (2 (3 lm + 1))
     T k_ws;   // 1 - om_s
@@ -80,33 +81,28 @@ struct ForceArgs {
     T k_m3w, k_mah;       // -3 omega and -alpha h in the storage type (host-evaluated)
 };
 
-// Divergence, effective source and pressure of the flow step (Alg. 3 setup):
-// Dt = D(g), s' of eq. source:implicit, p^ = sum f + s'/2.
+// Fused flow step (Alg. 3) and explicit force of the next time step: D(t) of
+// the final elastic iterate, s' of eq. source:implicit, p^ = sum f + s'/2,
+// collision with source, streaming with the pressure walls, then
+// F~(t + dt) = c0 h^2 f - alpha h [ -3 omega sum_i f_i(t+dt) c_i + 1/2 grad^c s'_exp(t+dt) ]
+// with s'_exp(t+dt) = dt s - (alpha/h)[(1-r)(D(t) - D(t-dt)) - r D(t)].
 template <typename T>
-struct FlowMomentsArgs {
+struct FlowFusedArgs {
     int nx, ny;
-    const T *g;          // finest-level elastic state (final iterate)
-    const T *f;          // flow populations
-    const double *D1, *D2, *src;
-    T *P, *S;            // outputs: p^ and s' per cell (population precision)
-    double *Dnew;        // output D(t) (may alias D2: read before written per cell)
-    double *SEnext;      // output: explicit source of the next step (SexpArgs formula with
-                         // D1 -> D(t), D2 -> D(t - dt)), or nullptr
-    double dt, a_over_h, r, lm;
-    double kD;           // dD/dm_s = -3 / (2 (3 lm + 1)) (host-evaluated)
-};
-
-// Collide + stream + boundary rules of the flow populations.
-template <typename T>
-struct FlowStreamArgs {
-    int nx, ny;
-    const T *f;
-    T *fout;
-    const T *P, *S;
-    const double *pprof[4];  // Dirichlet pressure data per side, 2n+1, or nullptr
-    int bc[4];               // pressure boundary type per side
-    double omega, c0;
-    T k_om, k_src;           // omega and 1 - omega/2 in the storage type (host-evaluated)
+    const T *f;           // flow populations, 9 planes
+    T *fout;              // streamed populations, 9 planes
+    const T *ms;          // m_s plane of the finest elastic state
+    const double *D1, *D2;  // D(t - dt), D(t - 2 dt)
+    double *Dnew;         // D(t) (a third buffer: neighbours still read D1, D2)
+    const double *src;    // fluid source (dimensional) or nullptr
+    const double *fbody;  // body force (2 planes) or nullptr
+    T *Ft;                // explicit force of the next step, 2 planes
+    const double *pprof[4];
+    int bc[4];            // pressure boundary type per side
+    int perx, pery;       // periodic in x / y (displacement sides; equal to the pressure sides)
+    double dt, a_over_h, r, kD, c0, c0h2;
+    T k_om, k_src, k_m3w, k_mah;  // omega, 1 - omega/2, -3 omega, -alpha h
+    T k_a1r, k_ar;                // (alpha/h)(1 - r), (alpha/h) r
 };
 
 // Physical fields of the current state.
@@ -131,6 +127,26 @@ struct InitArgs {
     const double *src, *fbody;
     double dt, c0h2;
 };
+
+// Device-side stopping test of the tolerance mode (the V-cycle loop of a time
+// step runs inside a CUDA-graph WHILE node; no host read per V-cycle).
+struct StopState {
+    long long total;   // V-cycles run by the device loop since creation
+    int ne;            // V-cycles of the current time step
+    int last_ne;       // V-cycles of the last finished time step
+    int notconv;       // time steps that stopped at ne_max
+    int diverged;      // 1 once a non-finite residual was met
+    double last_res, last_gn;
+};
+struct StopArgs {
+    const unsigned long long *resmax;  // ordered bits of max|g - g**| and max|g|
+    StopState *st;
+    double tol;
+    int ne_max;
+    int first;                 // 1: the first V-cycle of the time step
+    unsigned long long cond;   // cudaGraphConditionalHandle of the WHILE node
+};
+cudaError_t launch_stop_test(const StopArgs &a, cudaStream_t s);
 
 template <typename T, typename TC> cudaError_t launch_sweep_mom(const SweepArgs<T, TC> &a, cudaStream_t s);
 // Batched sweep: one launch of n work items of storage kind `variant`
@@ -174,9 +190,8 @@ inline int sweep_strip_rows(int nx, int ny, int slots)
 }
 template <typename T> cudaError_t launch_sexp(const SexpArgs<T> &a, cudaStream_t s);
 template <typename T> cudaError_t launch_force(const ForceArgs<T> &a, cudaStream_t s);
-template <typename T> cudaError_t launch_flow_moments(const FlowMomentsArgs<T> &a, cudaStream_t s);
-template <typename T> cudaError_t launch_flow_stream(const FlowStreamArgs<T> &a, cudaStream_t s);
 template <typename T> cudaError_t launch_readout(const ReadoutArgs<T> &a, cudaStream_t s);
+template <typename T> cudaError_t launch_flow_fused(const FlowFusedArgs<T> &a, cudaStream_t s);
 template <typename T> cudaError_t launch_init(const InitArgs<T> &a, cudaStream_t s);
 
 }  // namespace biot

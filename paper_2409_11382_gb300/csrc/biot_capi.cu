@@ -66,6 +66,7 @@ struct Level {
     int nx = 0, ny = 0;
     size_t np = 0;
     bool fp64 = true;
+    int rows[2] = {0, 0};  // strip height per sweep mode chosen by biot_autotune (0: default)
     void *g[2] = {nullptr, nullptr};
     void *glo[2] = {nullptr, nullptr};  // low parts of m_10, m_01 (finest FP32 level)
     int cur = 0;
@@ -87,17 +88,24 @@ struct biot_ctx {
     void *f[2]{};
     int fcur = 0;
     double *D1 = nullptr, *D2 = nullptr, *SE = nullptr;
-    void *Pp = nullptr, *Ss = nullptr;  // p^ and s' of the flow step (population type)
     void *Ft = nullptr;
     double *src = nullptr, *fbody = nullptr;
     bool has_src = false, has_fbody = false;
     double *out = nullptr;  // readout scratch, 6 planes
     unsigned long long *resmax = nullptr;      // device [2]
     unsigned long long *resmax_host = nullptr; // pinned [2]
+    // device-side stopping test (tolerance mode inside graphs)
+    StopState *stop = nullptr;                 // device
+    StopState *stop_host = nullptr;            // pinned mirror, copied at the end of each step
+    bool pending_stop = false;                 // the mirror holds counters not yet applied
+    long long stop_total_seen = 0;
+    int stop_notconv_seen = 0;
+    cudaStream_t aux_stream = nullptr;         // captures the WHILE node's body
     cudaStream_t stream = nullptr, own_stream = nullptr;
     long nstep = 0;
     bool solved = false, initialized = false, pending_res = false;
-    bool se_stale = true;  // SE must be recomputed from D1, D2 (else the last flow step wrote it)
+    bool se_stale = true;   // SE must be recomputed from D1, D2 before k_force
+    bool ft_fresh = false;  // the last flow step computed F~ of the next elastic solve
     // statistics
     int last_ne = 0;
     double last_res = 0;
@@ -166,7 +174,8 @@ int check_params(const biot_params *p, const biot_side *s)
     if (p->K < 1) return fail(BIOT_ERR_INVALID_ARG, "K must be >= 1");
     if (!(p->gamma > 0 && p->gamma <= 1)) return fail(BIOT_ERR_INVALID_ARG, "gamma must lie in (0, 1]");
     if (p->ne_fixed <= 0 && (p->ne_max < 1 || !(p->tol > 0))) return fail(BIOT_ERR_INVALID_ARG, "tolerance mode needs tol > 0 and ne_max >= 1");
-    if (p->precision != BIOT_FP64 && p->precision != BIOT_FP32) return fail(BIOT_ERR_INVALID_ARG, "unknown precision");
+    if (p->precision != BIOT_FP64 && p->precision != BIOT_FP32 && p->precision != BIOT_FP32_COARSE64)
+        return fail(BIOT_ERR_INVALID_ARG, "unknown precision");
     for (int i = 0; i < 4; i++) {
         if (s[i].eta_type < BIOT_PERIODIC || s[i].eta_type > BIOT_NEUMANN || s[i].p_type < BIOT_PERIODIC || s[i].p_type > BIOT_NEUMANN)
             return fail(BIOT_ERR_INVALID_ARG, "unknown boundary type");
@@ -239,6 +248,7 @@ int sweep_typed(biot_ctx *h, int l, int mode, bool zero_init, bool prolong, bool
     a.coef_fstar = 0.5 * h->P.alpha * h->P.alpha * h->P.r_coupling;
     a.c0h = h->P.c0 * h->h;
     a.resmax = want_res ? h->resmax : nullptr;
+    a.rows = Lv.rows[mode];
     a.k_fs = T(a.coef_fstar * (-1.5 / (3.0 * a.lm + 1.0)));
     a.k_ws = T(1.0 - a.om_s);
     a.k_wd = T(1.0 - a.om_d);
@@ -307,6 +317,10 @@ int vcycle(biot_ctx *h, int l, bool zero_start)
 template <typename T>
 int force_typed(biot_ctx *h)
 {
+    if (h->ft_fresh) {  // computed by the fused flow step
+        h->ft_fresh = false;
+        return BIOT_OK;
+    }
     SexpArgs<T> e{};
     e.nx = h->P.nx;
     e.ny = h->P.ny;
@@ -344,6 +358,21 @@ int force_typed(biot_ctx *h)
 int read_residual(biot_ctx *h)
 {
     CUDA_TRY(cudaStreamSynchronize(h->stream));
+    if (h->pending_stop) {  // counters of device-driven tolerance-mode steps
+        const StopState st = *h->stop_host;
+        h->total_cycles += st.total - h->stop_total_seen;
+        h->stop_total_seen = st.total;
+        h->last_ne = st.last_ne;
+        h->notconv_steps += st.notconv - h->stop_notconv_seen;
+        h->stop_notconv_seen = st.notconv;
+        h->pending_stop = false;
+        if (st.diverged) {
+            h->diverged = 1;
+            h->pending_res = false;
+            h->last_res = st.last_res;
+            return fail(BIOT_ERR_DIVERGED, "non-finite pseudo-time residual: the coupled iteration diverged");
+        }
+    }
     double res, gn;
     std::memcpy(&res, &h->resmax_host[0], sizeof(double));
     std::memcpy(&gn, &h->resmax_host[1], sizeof(double));
@@ -358,6 +387,8 @@ int read_residual(biot_ctx *h)
 }
 
 // Elasticity update of Alg. 5 at the current time.
+int elastic_solve_device_loop(biot_ctx *h);
+
 int elastic_solve(biot_ctx *h)
 {
     int rc;
@@ -365,6 +396,11 @@ int elastic_solve(biot_ctx *h)
     if (rc) return rc;
     h->lv[h->L - 1].hist_valid = 0;
     const bool fixed = h->P.ne_fixed > 0;
+    if (!fixed && !h->rec) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        CUDA_TRY(cudaStreamIsCapturing(h->stream, &cs));
+        if (cs == cudaStreamCaptureStatusActive) return elastic_solve_device_loop(h);
+    }
     int ne = 0, status = BIOT_OK;
     for (;;) {
         const bool measure = !fixed || (ne + 1 == h->P.ne_fixed);
@@ -399,49 +435,116 @@ int elastic_solve(biot_ctx *h)
     return status;
 }
 
+// Tolerance mode inside a graph capture: the first V-cycle and its stopping
+// test, then a WHILE node whose body is one more V-cycle and the test; the
+// test kernel sets the node's condition.  Every V-cycle after the first of a
+// step sees the same state transitions (each level's ping-pong parity returns
+// after its 2K smoothing sweeps; the finest history is valid), so the body
+// recorded once is exact for every iteration.
+int stop_test(biot_ctx *h, int first, cudaGraphConditionalHandle cond)
+{
+    StopArgs a{};
+    a.resmax = h->resmax;
+    a.st = h->stop;
+    a.tol = h->P.tol;
+    a.ne_max = h->P.ne_max;
+    a.first = first;
+    a.cond = (unsigned long long)cond;
+    CUDA_TRY(launch_stop_test(a, h->stream));
+    h->launches++;
+    return BIOT_OK;
+}
+
+int elastic_solve_device_loop(biot_ctx *h)
+{
+    int rc;
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t cg = nullptr;
+    const cudaGraphNode_t *deps = nullptr;
+    size_t ndeps = 0;
+    CUDA_TRY(cudaStreamGetCaptureInfo(h->stream, &cs, nullptr, &cg, &deps, nullptr, &ndeps));
+    cudaGraphConditionalHandle cond;
+    CUDA_TRY(cudaGraphConditionalHandleCreate(&cond, cg, 0, cudaGraphCondAssignDefault));
+    // first V-cycle of the step
+    h->measure_cycle = true;
+    CUDA_TRY(cudaMemsetAsync(h->resmax, 0, 2 * sizeof(unsigned long long), h->stream));
+    if ((rc = vcycle(h, h->L - 1, false))) return rc;
+    if ((rc = stop_test(h, 1, cond))) return rc;
+    // WHILE node after it
+    CUDA_TRY(cudaStreamGetCaptureInfo(h->stream, &cs, nullptr, &cg, &deps, nullptr, &ndeps));
+    cudaGraphNodeParams np{};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = cond;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t node;
+    CUDA_TRY(cudaGraphAddNode(&node, cg, deps, nullptr, ndeps, &np));
+    cudaGraph_t body = np.conditional.phGraph_out[0];
+    CUDA_TRY(cudaStreamBeginCaptureToGraph(h->aux_stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    cudaStream_t main = h->stream;
+    h->stream = h->aux_stream;
+    rc = BIOT_OK;
+    cudaError_t e = cudaMemsetAsync(h->resmax, 0, 2 * sizeof(unsigned long long), h->stream);
+    if (e != cudaSuccess) rc = fail(BIOT_ERR_CUDA, std::string("cudaMemsetAsync: ") + cudaGetErrorString(e));
+    if (!rc) rc = vcycle(h, h->L - 1, false);
+    if (!rc) rc = stop_test(h, 0, cond);
+    h->stream = main;
+    cudaGraph_t body_out = body;
+    e = cudaStreamEndCapture(h->aux_stream, &body_out);
+    if (rc) return rc;
+    if (e != cudaSuccess) return fail(BIOT_ERR_CUDA, std::string("cudaStreamEndCapture (loop body): ") + cudaGetErrorString(e));
+    CUDA_TRY(cudaStreamUpdateCaptureDependencies(h->stream, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+    // counters and the last residual back to the host once per step
+    CUDA_TRY(cudaMemcpyAsync(h->resmax_host, h->resmax, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(cudaMemcpyAsync(h->stop_host, h->stop, sizeof(StopState), cudaMemcpyDeviceToHost, h->stream));
+    h->pending_res = true;
+    h->pending_stop = true;
+    h->solved = true;
+    return BIOT_OK;
+}
+
 template <typename T>
 int flow_typed(biot_ctx *h)
 {
     const Level &Lf = h->lv[h->L - 1];
-    FlowMomentsArgs<T> m{};
-    m.nx = h->P.nx;
-    m.ny = h->P.ny;
-    m.g = static_cast<const T *>(Lf.g[Lf.cur]);
-    m.f = static_cast<const T *>(h->f[h->fcur]);
-    m.D1 = h->D1;
-    m.D2 = h->D2;
-    m.src = h->has_src ? h->src : nullptr;
-    m.P = static_cast<T *>(h->Pp);
-    m.S = static_cast<T *>(h->Ss);
-    m.Dnew = h->D2;  // D(t) overwrites D(t - 2 dt) cell by cell after it was read
-    m.dt = h->P.dt;
-    m.a_over_h = h->P.alpha / h->h;
-    m.r = h->P.r_coupling;
-    m.lm = h->lm;
-    m.kD = -1.5 / (3.0 * h->lm + 1.0);
-    m.SEnext = h->SE;  // the explicit source of the next elastic solve
-    CUDA_TRY(launch_flow_moments<T>(m, h->stream));
-    h->se_stale = false;
-    h->launches++;
-    std::swap(h->D1, h->D2);  // D1 <- D(t), D2 <- D(t - dt)
-
-    FlowStreamArgs<T> s{};
-    s.nx = h->P.nx;
-    s.ny = h->P.ny;
-    s.f = static_cast<const T *>(h->f[h->fcur]);
-    s.fout = static_cast<T *>(h->f[1 - h->fcur]);
-    s.P = static_cast<const T *>(h->Pp);
-    s.S = static_cast<const T *>(h->Ss);
+    const size_t np = (size_t)h->P.nx * h->P.ny;
+    FlowFusedArgs<T> a{};
+    a.nx = h->P.nx;
+    a.ny = h->P.ny;
+    a.f = static_cast<const T *>(h->f[h->fcur]);
+    a.fout = static_cast<T *>(h->f[1 - h->fcur]);
+    a.ms = static_cast<const T *>(Lf.g[Lf.cur]) + 3 * np;
+    a.D1 = h->D1;
+    a.D2 = h->D2;
+    a.Dnew = h->SE;  // scratch: neighbouring CTAs still read D1, D2
+    a.src = h->has_src ? h->src : nullptr;
+    a.fbody = h->has_fbody ? h->fbody : nullptr;
+    a.Ft = static_cast<T *>(h->Ft);
     for (int i = 0; i < 4; i++) {
-        s.pprof[i] = h->p_prof[i];
-        s.bc[i] = h->bc_p[i];
+        a.pprof[i] = h->p_prof[i];
+        a.bc[i] = h->bc_p[i];
     }
-    s.omega = h->omega;
-    s.c0 = h->P.c0;
-    s.k_om = T(h->omega);
-    s.k_src = T(1.0 - 0.5 * h->omega);
-    CUDA_TRY(launch_flow_stream<T>(s, h->stream));
+    a.perx = h->bc_eta[BIOT_LEFT] == BIOT_PERIODIC;
+    a.pery = h->bc_eta[BIOT_BOTTOM] == BIOT_PERIODIC;
+    a.dt = h->P.dt;
+    a.a_over_h = h->P.alpha / h->h;
+    a.r = h->P.r_coupling;
+    a.kD = -1.5 / (3.0 * h->lm + 1.0);
+    a.c0 = h->P.c0;
+    a.c0h2 = h->P.c0 * h->h * h->h;
+    a.k_om = T(h->omega);
+    a.k_src = T(1.0 - 0.5 * h->omega);
+    a.k_m3w = T(-3.0 * h->omega);
+    a.k_mah = T(-(h->P.alpha * h->h));
+    a.k_a1r = T(a.a_over_h * (1.0 - a.r));
+    a.k_ar = T(a.a_over_h * a.r);
+    CUDA_TRY(launch_flow_fused<T>(a, h->stream));
     h->launches++;
+    // D(t) into the buffer of D(t - 2 dt), then D1 <- D(t), D2 <- D(t - dt)
+    CUDA_TRY(cudaMemcpyAsync(h->D2, h->SE, np * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+    std::swap(h->D1, h->D2);
+    h->ft_fresh = true;   // F~ of the next elastic solve is computed
+    h->se_stale = true;   // the s'_exp buffer was used as scratch
     h->fcur ^= 1;
     h->nstep++;
     return BIOT_OK;
@@ -593,8 +696,12 @@ int advance_graph(biot_ctx *h)
     h->fcur ^= 1;
     std::swap(h->D1, h->D2);
     h->nstep += 1;
-    h->total_cycles += h->P.ne_fixed;
-    h->last_ne = h->P.ne_fixed;
+    if (h->P.ne_fixed > 0) {
+        h->total_cycles += h->P.ne_fixed;
+        h->last_ne = h->P.ne_fixed;
+    } else {
+        h->pending_stop = true;  // counters arrive with the step's read-back
+    }
     h->solved = true;
     h->pending_res = true;
     return BIOT_OK;
@@ -608,6 +715,8 @@ void release(biot_ctx *h)
     for (void *p : h->allocs) cudaFree(p);
     h->allocs.clear();
     if (h->resmax_host) cudaFreeHost(h->resmax_host);
+    if (h->stop_host) cudaFreeHost(h->stop_host);
+    if (h->aux_stream) cudaStreamDestroy(h->aux_stream);
     for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
     if (h->own_stream) cudaStreamDestroy(h->own_stream);
     delete h;
@@ -652,7 +761,7 @@ int biot_create(const biot_params *p, const biot_side sides[4], biot_handle *out
     if (!h) return fail(BIOT_ERR_OOM, "host allocation failed");
     h->P = *p;
     h->L = p->mg_levels;
-    h->fp32 = p->precision == BIOT_FP32;
+    h->fp32 = p->precision != BIOT_FP64;  // finest level and flow populations in FP32
     h->h = p->lx / p->nx;
     h->lam = p->c0 * p->lambda;
     h->mu = p->c0 * p->mu;
@@ -681,7 +790,8 @@ int biot_create(const biot_params *p, const biot_side sides[4], biot_handle *out
         Lv.nx = p->nx >> shift;
         Lv.ny = p->ny >> shift;
         Lv.np = (size_t)Lv.nx * Lv.ny;
-        Lv.fp64 = !h->fp32 || (l == 0 && h->L > 1);  // coarsest level in FP64
+        // coarsest level in FP64; with BIOT_FP32_COARSE64 every level below the finest
+        Lv.fp64 = !h->fp32 || (l == 0 && h->L > 1) || (p->precision == BIOT_FP32_COARSE64 && l < h->L - 1);
         const size_t esz = Lv.fp64 ? sizeof(double) : sizeof(float);
         TRY_RC(dev_alloc(h, &Lv.g[0], 8 * Lv.np * esz));
         TRY_RC(dev_alloc(h, &Lv.g[1], 8 * Lv.np * esz));
@@ -702,14 +812,20 @@ int biot_create(const biot_params *p, const biot_side sides[4], biot_handle *out
     TRY_RC(dev_alloc(h, (void **)&h->D1, np * sizeof(double)));
     TRY_RC(dev_alloc(h, (void **)&h->D2, np * sizeof(double)));
     TRY_RC(dev_alloc(h, (void **)&h->SE, np * sizeof(double)));
-    TRY_RC(dev_alloc(h, &h->Pp, np * tsz));
-    TRY_RC(dev_alloc(h, &h->Ss, np * tsz));
     TRY_RC(dev_alloc(h, (void **)&h->resmax, 2 * sizeof(unsigned long long)));
-    if (cudaMallocHost((void **)&h->resmax_host, 2 * sizeof(unsigned long long)) != cudaSuccess) {
+    TRY_RC(dev_alloc(h, (void **)&h->stop, sizeof(StopState)));
+    if (cudaMallocHost((void **)&h->resmax_host, 2 * sizeof(unsigned long long)) != cudaSuccess ||
+        cudaMallocHost((void **)&h->stop_host, sizeof(StopState)) != cudaSuccess) {
         cudaGetLastError();
-        h->resmax_host = nullptr;
         release(h);
         return fail(BIOT_ERR_OOM, "pinned host allocation failed");
+    }
+    std::memset(h->stop_host, 0, sizeof(StopState));
+    if (cudaStreamCreateWithFlags(&h->aux_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        h->aux_stream = nullptr;
+        release(h);
+        return fail(BIOT_ERR_CUDA, "cudaStreamCreate failed");
     }
     for (int s = 0; s < 4; s++) TRY_RC(set_profiles(h, s, sides[s].eta_profile, sides[s].p_profile));
 #undef TRY_RC
@@ -747,6 +863,7 @@ int biot_set_sources(biot_handle h, const double *f_body, const double *s)
     }
     h->has_src = s != nullptr;
     h->se_stale = true;
+    h->ft_fresh = false;
     CUDA_TRY(cudaStreamSynchronize(h->stream));
     drop_graphs(h);
     h->solved = false;
@@ -776,16 +893,19 @@ int biot_step(biot_handle h, int n)
         if (rc == BIOT_ERR_NOT_CONVERGED) status = rc;
         else if (rc) return rc;
     }
-    // with a fixed number of V-cycles nothing is read back until the end: a
-    // diverged state stays non-finite, so the last residual reveals it
-    const bool graphs = h->P.ne_fixed > 0 && h->use_graphs && !h->timing;
+    // Each step is one graph launch (fixed V-cycles, or the tolerance mode's
+    // device-side loop); nothing is read back until the end: a diverged state
+    // stays non-finite, so the last residual reveals it.
+    const bool graphs = h->use_graphs && !h->timing;
+    const int notconv0 = h->notconv_steps;
     for (int i = 0; i < n; i++) {
-        if (h->P.ne_fixed <= 0 && (rc = finish_pending(h))) return rc;
+        if (!graphs && h->P.ne_fixed <= 0 && (rc = finish_pending(h))) return rc;
         rc = graphs ? advance_graph(h) : advance(h);
         if (rc == BIOT_ERR_NOT_CONVERGED) status = rc;
         else if (rc) return rc;
     }
     if ((rc = finish_pending(h))) return rc;
+    if (h->notconv_steps > notconv0) status = BIOT_ERR_NOT_CONVERGED;
     return status;
 }
 
@@ -1331,13 +1451,13 @@ namespace {
 
 size_t estimate_bytes(const biot_params *p, const biot_side *sides)
 {
-    const bool fp32 = p->precision == BIOT_FP32;
+    const bool fp32 = p->precision != BIOT_FP64;
     const size_t tsz = fp32 ? 4 : 8, np = (size_t)p->nx * p->ny;
     size_t b = 0;
     for (int l = 0; l < p->mg_levels; l++) {
         const int shift = p->mg_levels - 1 - l;
         const size_t nx = (size_t)(p->nx >> shift), ny = (size_t)(p->ny >> shift), n = nx * ny;
-        const bool fp64 = !fp32 || (l == 0 && p->mg_levels > 1);
+        const bool fp64 = !fp32 || (l == 0 && p->mg_levels > 1) || (p->precision == BIOT_FP32_COARSE64 && l < p->mg_levels - 1);
         const size_t esz = fp64 ? 8 : 4;
         b += 2 * 8 * n * esz;
         if (!fp64 && l == p->mg_levels - 1) b += 2 * 2 * n * esz;
@@ -1345,7 +1465,7 @@ size_t estimate_bytes(const biot_params *p, const biot_side *sides)
         for (int s = 0; s < 4; s++)
             if (sides && sides[s].eta_type == BIOT_DIRICHLET) b += 3 * ((s == BIOT_BOTTOM || s == BIOT_TOP) ? nx : ny) * esz;
     }
-    b += (2 * 9 + 2 + 2) * np * tsz + 3 * np * 8 + 16;
+    b += (2 * 9 + 2) * np * tsz + 3 * np * 8 + 16 + sizeof(StopState);
     for (int s = 0; s < 4; s++) {
         const size_t m = 2 * (size_t)((s == BIOT_BOTTOM || s == BIOT_TOP) ? p->nx : p->ny) + 1;
         if (sides && sides[s].eta_profile) b += 2 * m * 8;
@@ -1477,7 +1597,7 @@ void server_loop(biot_server_s *S)
         for (size_t k = 0; k < S->resident.size(); k++) {
             Request &r = *S->resident[k];
             for (int j = 0; j < per_tick && r.h->nstep < r.target && !st[k]; j++) {
-                const bool graphs = r.h->P.ne_fixed > 0 && r.h->use_graphs;
+                const bool graphs = r.h->use_graphs;
                 st[k] = graphs ? advance_graph(r.h) : advance(r.h);
                 if (st[k] == BIOT_ERR_NOT_CONVERGED) st[k] = BIOT_OK;
                 S->graph_launches++;
@@ -1664,6 +1784,188 @@ int biot_server_destroy(biot_server S)
     }
     if (S->worker.joinable()) S->worker.join();
     delete S;
+    return BIOT_OK;
+}
+
+}  // extern "C"
+
+// ============================================================================
+// Autotuning of the sweep launch shape.
+// ============================================================================
+extern "C" int biot_autotune(biot_handle h, int *rows_out, double *ms_out, int max_levels)
+{
+    if (!h) return fail(BIOT_ERR_INVALID_ARG, "null handle");
+    int rc;
+    CUDA_TRY(cudaStreamSynchronize(h->stream));
+    // a scratch instance of the same shape: timing does not touch the caller's state
+    biot_side sides[4];
+    for (int i = 0; i < 4; i++) sides[i] = biot_side{h->bc_eta[i], h->bc_p[i], nullptr, nullptr};
+    biot_handle c = nullptr;
+    if ((rc = biot_create(&h->P, sides, &c))) return rc;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        cudaGetLastError();
+        release(c);
+        return fail(BIOT_ERR_CUDA, "cudaEventCreate failed");
+    }
+    static const int cand[] = {4, 8, 16, 24, 32, 48, 64, 96};
+    int status = BIOT_OK;
+    for (int l = 0; l < h->L && !status; l++) {
+        Level &Lv = h->lv[l];
+        for (int mode = 0; mode < 2 && !status; mode++) {
+            if (mode == SWEEP_RESTRICT && l == 0) continue;
+            int best = 0;
+            double best_ms = 1e30;
+            // tile-sized levels are not launched as strips: nothing to choose
+            const bool strips = (long)Lv.nx * Lv.ny > (long)256 * 256;
+            for (int k = 0; strips && k < (int)(sizeof(cand) / sizeof(cand[0])) && !status; k++) {
+                if (cand[k] > Lv.ny) break;
+                c->lv[l].rows[mode] = cand[k];
+                for (int w = 0; w < 2 && !status; w++) status = sweep(c, l, mode, false, false, false);
+                if (status) break;
+                if (cudaEventRecord(e0, c->stream) != cudaSuccess) status = fail(BIOT_ERR_CUDA, "cudaEventRecord");
+                const int reps = 4;
+                for (int r = 0; r < reps && !status; r++) status = sweep(c, l, mode, false, false, false);
+                if (status) break;
+                float ms = 0.f;
+                if (cudaEventRecord(e1, c->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                    cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess)
+                    status = fail(BIOT_ERR_CUDA, "timing the sweep failed");
+                else if (ms / reps < best_ms) {
+                    best_ms = ms / reps;
+                    best = cand[k];
+                }
+            }
+            Lv.rows[mode] = best;
+            if (rows_out && l < max_levels) rows_out[2 * l + mode] = best;
+            if (ms_out && l < max_levels) ms_out[2 * l + mode] = best ? best_ms : 0.0;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    release(c);
+    drop_graphs(h);  // graphs captured with the old shapes
+    return status;
+}
+
+// ============================================================================
+// Checkpoint / resume.
+//
+// The resumable state of an instance after a completed step is the current
+// flow populations, the finest elastic state (moments and, in FP32, the low
+// parts of the first moments), the explicit force F~ of the last solve and the
+// divergence history D(t - dt), D(t - 2 dt); the coarse levels, residuals and
+// bounce-back histories are rebuilt inside every time step.
+// ============================================================================
+namespace {
+
+struct CkptHeader {
+    uint64_t magic;  // "BIOTCKP1"
+    int32_t nx, ny, levels, precision;
+    int64_t nstep;
+    int32_t solved, initialized, last_ne, notconv;
+    int64_t total_cycles;
+    double last_res;
+    uint64_t payload;  // bytes after the header
+};
+constexpr uint64_t CKPT_MAGIC = 0x3150434B544F4942ull;
+
+struct CkptPart {
+    void *dev;
+    size_t bytes;
+};
+
+std::vector<CkptPart> ckpt_parts(biot_ctx *h)
+{
+    const Level &Lf = h->lv[h->L - 1];
+    const size_t np = (size_t)h->P.nx * h->P.ny;
+    const size_t tsz = h->fp32 ? 4 : 8, esz = Lf.fp64 ? 8 : 4;
+    std::vector<CkptPart> v;
+    v.push_back({h->f[h->fcur], 9 * np * tsz});
+    v.push_back({Lf.g[Lf.cur], 8 * np * esz});
+    if (Lf.glo[Lf.cur]) v.push_back({Lf.glo[Lf.cur], 2 * np * esz});
+    v.push_back({h->Ft, 2 * np * tsz});
+    v.push_back({h->D1, np * sizeof(double)});
+    v.push_back({h->D2, np * sizeof(double)});
+    return v;
+}
+
+}  // namespace
+
+extern "C" {
+
+int biot_checkpoint_size(biot_handle h, size_t *bytes)
+{
+    if (!h || !bytes) return fail(BIOT_ERR_INVALID_ARG, "null argument");
+    size_t n = sizeof(CkptHeader);
+    for (const CkptPart &p : ckpt_parts(h)) n += p.bytes;
+    *bytes = n;
+    return BIOT_OK;
+}
+
+int biot_save(biot_handle h, void *buf, size_t size)
+{
+    if (!h || !buf) return fail(BIOT_ERR_INVALID_ARG, "null argument");
+    int rc;
+    if ((rc = finish_pending(h))) return rc;
+    size_t need = 0;
+    biot_checkpoint_size(h, &need);
+    if (size < need) return fail(BIOT_ERR_INVALID_ARG, "checkpoint buffer too small (see biot_checkpoint_size)");
+    CkptHeader hd{};
+    hd.magic = CKPT_MAGIC;
+    hd.nx = h->P.nx;
+    hd.ny = h->P.ny;
+    hd.levels = h->L;
+    hd.precision = h->P.precision;
+    hd.nstep = h->nstep;
+    hd.solved = h->solved;
+    hd.initialized = h->initialized;
+    hd.last_ne = h->last_ne;
+    hd.notconv = h->notconv_steps;
+    hd.total_cycles = h->total_cycles;
+    hd.last_res = h->last_res;
+    hd.payload = need - sizeof(CkptHeader);
+    std::memcpy(buf, &hd, sizeof(hd));
+    unsigned char *out = static_cast<unsigned char *>(buf) + sizeof(hd);
+    for (const CkptPart &p : ckpt_parts(h)) {
+        CUDA_TRY(cudaMemcpyAsync(out, p.dev, p.bytes, cudaMemcpyDeviceToHost, h->stream));
+        out += p.bytes;
+    }
+    CUDA_TRY(cudaStreamSynchronize(h->stream));
+    return BIOT_OK;
+}
+
+int biot_load(biot_handle h, const void *buf, size_t size)
+{
+    if (!h || !buf || size < sizeof(CkptHeader)) return fail(BIOT_ERR_INVALID_ARG, "null argument or short buffer");
+    CkptHeader hd;
+    std::memcpy(&hd, buf, sizeof(hd));
+    size_t need = 0;
+    biot_checkpoint_size(h, &need);
+    if (hd.magic != CKPT_MAGIC) return fail(BIOT_ERR_INVALID_ARG, "not a checkpoint of this library");
+    if (hd.nx != h->P.nx || hd.ny != h->P.ny || hd.levels != h->L || hd.precision != h->P.precision ||
+        hd.payload + sizeof(CkptHeader) != need || size < need)
+        return fail(BIOT_ERR_INVALID_ARG, "checkpoint of a different grid, hierarchy or precision");
+    CUDA_TRY(cudaStreamSynchronize(h->stream));
+    const unsigned char *in = static_cast<const unsigned char *>(buf) + sizeof(hd);
+    for (const CkptPart &p : ckpt_parts(h)) {
+        CUDA_TRY(cudaMemcpyAsync(p.dev, in, p.bytes, cudaMemcpyHostToDevice, h->stream));
+        in += p.bytes;
+    }
+    CUDA_TRY(cudaStreamSynchronize(h->stream));
+    h->nstep = hd.nstep;
+    h->solved = hd.solved != 0;
+    h->initialized = hd.initialized != 0;
+    h->last_ne = hd.last_ne;
+    h->notconv_steps = hd.notconv;
+    h->total_cycles = hd.total_cycles;
+    h->last_res = hd.last_res;
+    h->diverged = 0;
+    h->pending_res = false;
+    h->pending_stop = false;
+    h->ft_fresh = false;  // F~ belongs to the solve at the saved time
+    h->se_stale = true;
+    drop_graphs(h);
     return BIOT_OK;
 }
 

@@ -64,94 +64,6 @@ __global__ void __launch_bounds__(256) k_force(const ForceArgs<T> a)
 }
 
 // ---------------------------------------------------------------------------
-// Flow step, part 1: D(t) of the final elastic iterate (eq. LBM:divergence), s' of
-// eq. source:implicit and p^ = sum_i f_i + s'/2 (eq. pressure), all in FP64.
-// ---------------------------------------------------------------------------
-template <typename T>
-__global__ void __launch_bounds__(256) k_flow_moments(const FlowMomentsArgs<T> a)
-{
-    const size_t NP = (size_t)a.nx * a.ny;
-    const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= NP) return;
-    const double dt_ = a.kD * (double)a.g[3 * NP + idx];
-    const double d1 = a.D1[idx], d2 = a.D2[idx];
-    const double s0 = a.src ? a.dt * a.src[idx] : 0.0;
-    const double sp = s0 - a.a_over_h * ((1.0 - a.r) * (d1 - d2) + a.r * (dt_ - d1));
-    T sum = T(0);
-#pragma unroll
-    for (int i = 0; i < 9; i++) sum += a.f[i * NP + idx];
-    a.P[idx] = T((double)sum + 0.5 * sp);
-    a.S[idx] = T(sp);
-    a.Dnew[idx] = dt_;
-    // explicit source of the next time step, from D(t) and D(t - dt) (k_sexp's formula)
-    if (a.SEnext) a.SEnext[idx] = s0 - a.a_over_h * ((1.0 - a.r) * (dt_ - d1) - a.r * dt_);
-}
-
-// Flow step, part 2: BGK collision with source (eqs. pressure:equilibrium,
-// pressure:collision, pressure:collision:source), pull streaming and the
-// pressure wall rules (eqs. BC:pressure, BC:noFlow; SYMMETRY = mirror).
-template <typename T>
-__device__ __forceinline__ T flow_post(const FlowStreamArgs<T> &a, size_t NP, size_t idx, int i)
-{
-    const T om = a.k_om;
-    const T fi = a.f[(size_t)i * NP + idx];
-    const T wi = T(w9(i));
-    return fi - om * (fi - wi * a.P[idx]) + a.k_src * wi * a.S[idx];
-}
-
-template <typename T>
-__global__ void __launch_bounds__(256) k_flow_stream(const FlowStreamArgs<T> a)
-{
-    const int x = blockIdx.x * 32 + (threadIdx.x & 31);
-    const int y = blockIdx.y * 8 + (threadIdx.x >> 5);
-    const int nx = a.nx, ny = a.ny;
-    if (x >= nx || y >= ny) return;
-    const size_t NP = (size_t)nx * ny, idx = (size_t)y * nx + x;
-    const bool perx = a.bc[SIDE_LEFT] == BC_PERIODIC;
-    const bool pery = a.bc[SIDE_BOTTOM] == BC_PERIODIC;
-    a.fout[idx] = flow_post(a, NP, idx, 0);
-#pragma unroll
-    for (int i = 1; i < 9; i++) {
-        const int cx = ex9(i), cy = ey9(i);
-        int sx = x - cx, sy = y - cy;
-        const bool outx = !perx && (sx < 0 || sx >= nx);
-        const bool outy = !pery && (sy < 0 || sy >= ny);
-        if (perx) sx = wrapi(sx, nx);
-        if (pery) sy = wrapi(sy, ny);
-        T v;
-        if (!outx && !outy) {
-            v = flow_post(a, NP, (size_t)sy * nx + sx, i);
-        } else {
-            int side = outy ? (sy < 0 ? SIDE_BOTTOM : SIDE_TOP) : (sx < 0 ? SIDE_LEFT : SIDE_RIGHT);
-            if (outy && outx) {
-                const int vert = sx < 0 ? SIDE_LEFT : SIDE_RIGHT;
-                if (a.bc[side] == BC_SYMMETRY && a.bc[vert] != BC_SYMMETRY) side = vert;
-            }
-            const int iout = opp9(i);
-            const int type = a.bc[side];
-            if (type == BC_SYMMETRY) {
-                if (outy) {
-                    if (outx) v = flow_post(a, NP, idx, dir9(-cx, -cy));
-                    else      v = flow_post(a, NP, (size_t)y * nx + sx, dir9(cx, -cy));
-                } else {
-                    v = flow_post(a, NP, (size_t)sy * nx + x, dir9(-cx, cy));
-                }
-            } else if (type == BC_NEUMANN) {
-                v = flow_post(a, NP, idx, iout);
-            } else {  // BC_DIRICHLET
-                v = -flow_post(a, NP, idx, iout);
-                if (a.pprof[side]) {
-                    const bool horiz = (side == SIDE_BOTTOM || side == SIDE_TOP);
-                    const int kk = horiz ? 2 * x + 1 - cx : 2 * y + 1 - cy;
-                    v += T(2.0 * w9(i) * a.c0 * a.pprof[side][kk]);
-                }
-            }
-        }
-        a.fout[(size_t)i * NP + idx] = v;
-    }
-}
-
-// ---------------------------------------------------------------------------
 // Physical fields of the current state (FP64 outputs):
 //   eta = mbar_10,01 with mbar = m + F/2, F = F~ + F_*(g)   (eq. displacement)
 //   sigma = -(1/(2 c0 h)) [[mbar_s+mbar_d, 2 mbar_11], [2 mbar_11, mbar_s-mbar_d]]
@@ -237,6 +149,143 @@ __global__ void __launch_bounds__(256) k_init(const InitArgs<T> a)
 }
 
 // ---------------------------------------------------------------------------
+// Fused flow step + explicit force of the next step.  A CTA of 32 x 8 threads
+// owns a 32 x 8 tile; it stages the tile and a 1-cell halo (34 x 10 cells):
+// post-collision populations f* (eqs. pressure, pressure:equilibrium,
+// pressure:collision, pressure:collision:source), and the three fields whose
+// D2Q9 gradient gives grad^c s'_exp(t+dt): s0 = dt s, A = D(t) - D(t-dt) and
+// m_s (D(t) = kD m_s).  Only the divergence history is FP64: D(t) is formed in
+// FP64, differenced with D(t-dt) and D(t-2dt) in FP64, and the differences
+// are rounded to the storage type; the gradient of D(t) itself is taken as
+// kD times the difference of neighbouring m_s values of the state, which is
+// exact for nearby values.  Ghost cells of non-periodic walls are the adjacent
+// cell (even extension), as in the elastic sweep.
+// ---------------------------------------------------------------------------
+constexpr int FF_TX = 32, FF_TY = 8, FF_W = FF_TX + 2, FF_H = FF_TY + 2;
+
+template <typename T>
+__device__ __forceinline__ int ff_src_index(const FlowFusedArgs<T> &a, int x, int y)
+{
+    if (a.perx) x = wrapi(x, a.nx); else x = clampi(x, a.nx);
+    if (a.pery) y = wrapi(y, a.ny); else y = clampi(y, a.ny);
+    return y * a.nx + x;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(FF_TX * FF_TY) k_flow_fused(const FlowFusedArgs<T> a)
+{
+    __shared__ T fs[9][FF_H][FF_W];  // post-collision populations
+    __shared__ T qs0[FF_H][FF_W], qA[FF_H][FF_W], qms[FF_H][FF_W];
+    const int nx = a.nx, ny = a.ny;
+    const size_t NP = (size_t)nx * ny;
+    const int tid = threadIdx.x;
+    const int x0 = blockIdx.x * FF_TX, y0 = blockIdx.y * FF_TY;
+    // stage: 340 cells over 256 threads
+    for (int i = tid; i < FF_W * FF_H; i += FF_TX * FF_TY) {
+        const int cx = i % FF_W, cy = i / FF_W;
+        const int idx = ff_src_index(a, x0 - 1 + cx, y0 - 1 + cy);
+        T fi[9];
+        T sum = T(0);
+#pragma unroll
+        for (int k = 0; k < 9; k++) {
+            fi[k] = a.f[k * NP + idx];
+            sum += fi[k];
+        }
+        const T msv = a.ms[idx];
+        const double dt_ = a.kD * (double)msv;  // D(t)
+        const double d1 = a.D1[idx], d2 = a.D2[idx];
+        const T dA = T(dt_ - d1), dB = T(d1 - d2);  // FP64 differences of the history
+        const T s0 = a.src ? T(a.dt * a.src[idx]) : T(0);
+        const T sp = s0 - (a.k_a1r * dB + a.k_ar * dA);  // s' of eq. source:implicit
+        const T P = sum + T(0.5) * sp, S = sp;
+#pragma unroll
+        for (int k = 0; k < 9; k++) {
+            const T wk = T(w9(k));
+            fs[k][cy][cx] = fi[k] - a.k_om * (fi[k] - wk * P) + a.k_src * wk * S;
+        }
+        qs0[cy][cx] = s0;
+        qA[cy][cx] = dA;
+        qms[cy][cx] = msv;
+        const int gx = x0 - 1 + cx, gy = y0 - 1 + cy;
+        if (cx >= 1 && cx <= FF_TX && cy >= 1 && cy <= FF_TY && gx < nx && gy < ny) a.Dnew[idx] = dt_;
+    }
+    __syncthreads();
+    const int tx = tid % FF_TX, ty = tid / FF_TX;
+    const int x = x0 + tx, y = y0 + ty;
+    if (x >= nx || y >= ny) return;
+    const size_t idx = (size_t)y * nx + x;
+    const int cx = tx + 1, cy = ty + 1;
+    const bool perx = a.bc[SIDE_LEFT] == BC_PERIODIC;
+    const bool pery = a.bc[SIDE_BOTTOM] == BC_PERIODIC;
+    T fn[9];
+    fn[0] = fs[0][cy][cx];
+#pragma unroll
+    for (int i = 1; i < 9; i++) {
+        const int ex = ex9(i), ey = ey9(i);
+        const int sx = x - ex, sy = y - ey;
+        const bool outx = !perx && (sx < 0 || sx >= nx);
+        const bool outy = !pery && (sy < 0 || sy >= ny);
+        T v;
+        if (!outx && !outy) {
+            v = fs[i][cy - ey][cx - ex];
+        } else {
+            int side = outy ? (sy < 0 ? SIDE_BOTTOM : SIDE_TOP) : (sx < 0 ? SIDE_LEFT : SIDE_RIGHT);
+            if (outy && outx) {
+                const int vert = sx < 0 ? SIDE_LEFT : SIDE_RIGHT;
+                if (a.bc[side] == BC_SYMMETRY && a.bc[vert] != BC_SYMMETRY) side = vert;
+            }
+            const int iout = opp9(i);
+            const int type = a.bc[side];
+            if (type == BC_SYMMETRY) {
+                if (outy) {
+                    if (outx) v = fs[dir9(-ex, -ey)][cy][cx];
+                    else      v = fs[dir9(ex, -ey)][cy][cx - ex];
+                } else {
+                    v = fs[dir9(-ex, ey)][cy - ey][cx];
+                }
+            } else if (type == BC_NEUMANN) {
+                v = fs[iout][cy][cx];
+            } else {  // BC_DIRICHLET
+                v = -fs[iout][cy][cx];
+                if (a.pprof[side]) {
+                    const bool horiz = (side == SIDE_BOTTOM || side == SIDE_TOP);
+                    const int kk = horiz ? 2 * x + 1 - ex : 2 * y + 1 - ey;
+                    v += T(2.0 * w9(i) * a.c0 * a.pprof[side][kk]);
+                }
+            }
+        }
+        fn[i] = v;
+    }
+#pragma unroll
+    for (int i = 0; i < 9; i++) a.fout[i * NP + idx] = fn[i];
+    // explicit force of the next step
+    const T jx = (fn[1] - fn[3]) + (fn[5] - fn[6]) + (fn[8] - fn[7]);
+    const T jy = (fn[2] - fn[4]) + (fn[5] + fn[6]) - (fn[7] + fn[8]);
+    auto grad = [&](const T (&q)[FF_H][FF_W], T &gx, T &gy) {
+        gx = (q[cy][cx + 1] - q[cy][cx - 1]) * T(1.0 / 3.0) +
+             ((q[cy + 1][cx + 1] - q[cy + 1][cx - 1]) + (q[cy - 1][cx + 1] - q[cy - 1][cx - 1])) * T(1.0 / 12.0);
+        gy = (q[cy + 1][cx] - q[cy - 1][cx]) * T(1.0 / 3.0) +
+             ((q[cy + 1][cx + 1] - q[cy - 1][cx + 1]) + (q[cy + 1][cx - 1] - q[cy - 1][cx - 1])) * T(1.0 / 12.0);
+    };
+    T g0x, g0y, gAx, gAy, gmx, gmy;
+    grad(qs0, g0x, g0y);
+    grad(qA, gAx, gAy);
+    grad(qms, gmx, gmy);
+    // grad s'_exp = grad s0 - (alpha/h) [(1-r) grad A - r kD grad m_s]
+    const T c1 = T(a.a_over_h * (1.0 - a.r)), c2 = T(a.a_over_h * a.r * a.kD);
+    const T gx_ = (g0x - c1 * gAx) + c2 * gmx;
+    const T gy_ = (g0y - c1 * gAy) + c2 * gmy;
+    T fx = a.k_mah * (a.k_m3w * jx + T(0.5) * gx_);
+    T fy = a.k_mah * (a.k_m3w * jy + T(0.5) * gy_);
+    if (a.fbody) {
+        fx += T(a.c0h2 * a.fbody[idx]);
+        fy += T(a.c0h2 * a.fbody[NP + idx]);
+    }
+    a.Ft[idx] = fx;
+    a.Ft[NP + idx] = fy;
+}
+
+// ---------------------------------------------------------------------------
 // Launchers.
 // ---------------------------------------------------------------------------
 template <typename T>
@@ -256,26 +305,18 @@ cudaError_t launch_force_impl(const ForceArgs<T> &a, cudaStream_t s)
 }
 
 template <typename T>
-cudaError_t launch_flow_moments_impl(const FlowMomentsArgs<T> &a, cudaStream_t s)
-{
-    const size_t n = (size_t)a.nx * a.ny;
-    k_flow_moments<T><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(a);
-    return cudaGetLastError();
-}
-
-template <typename T>
-cudaError_t launch_flow_stream_impl(const FlowStreamArgs<T> &a, cudaStream_t s)
-{
-    dim3 grid((a.nx + 31) / 32, (a.ny + 7) / 8);
-    k_flow_stream<T><<<grid, 256, 0, s>>>(a);
-    return cudaGetLastError();
-}
-
-template <typename T>
 cudaError_t launch_readout_impl(const ReadoutArgs<T> &a, cudaStream_t s)
 {
     dim3 grid((a.nx + 31) / 32, (a.ny + 7) / 8);
     k_readout<T><<<grid, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_flow_fused_impl(const FlowFusedArgs<T> &a, cudaStream_t s)
+{
+    dim3 grid((a.nx + FF_TX - 1) / FF_TX, (a.ny + FF_TY - 1) / FF_TY);
+    k_flow_fused<T><<<grid, FF_TX * FF_TY, 0, s>>>(a);
     return cudaGetLastError();
 }
 

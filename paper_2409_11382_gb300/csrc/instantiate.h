@@ -16,11 +16,9 @@
     { return biot::launch_sexp_impl<T>(a, s); }                                                        \
     template <> cudaError_t biot::launch_force<T>(const biot::ForceArgs<T> &a, cudaStream_t s)           \
     { return biot::launch_force_impl<T>(a, s); }                                                       \
-    template <> cudaError_t biot::launch_flow_stream<T>(const biot::FlowStreamArgs<T> &a, cudaStream_t s) \
-    { return biot::launch_flow_stream_impl<T>(a, s); }                                                 \
-    template <> cudaError_t biot::launch_flow_moments<T>(const biot::FlowMomentsArgs<T> &a, cudaStream_t s) \
-    { return biot::launch_flow_moments_impl<T>(a, s); }                                                \
     template <> cudaError_t biot::launch_readout<T>(const biot::ReadoutArgs<T> &a, cudaStream_t s)       \
     { return biot::launch_readout_impl<T>(a, s); }                                                     \
     template <> cudaError_t biot::launch_init<T>(const biot::InitArgs<T> &a, cudaStream_t s)             \
-    { return biot::launch_init_impl<T>(a, s); }
+    { return biot::launch_init_impl<T>(a, s); }                                                        \
+    template <> cudaError_t biot::launch_flow_fused<T>(const biot::FlowFusedArgs<T> &a, cudaStream_t s) \
+    { return biot::launch_flow_fused_impl<T>(a, s); }

@@ -5,3 +5,34 @@
 
 BIOT_SWEEP_MOM(double, double)
 BIOT_FIELDS(double)
+
+// Stopping test of one V-cycle (tolerance mode, inside a CUDA graph):
+// converged when max|g - ELASTIC_STEP(g)| <= tol * max(1, max|g|); the loop also
+// stops at ne_max V-cycles or at a non-finite residual.  Sets the WHILE node's
+// condition and the per-instance counters the host reads once per biot_step.
+__global__ void k_stop_test(const biot::StopArgs a)
+{
+    biot::StopState &s = *a.st;
+    if (a.first) s.ne = 0;
+    s.ne += 1;
+    s.total += 1;
+    const double res = __longlong_as_double((long long)a.resmax[0]);
+    const double gn = __longlong_as_double((long long)a.resmax[1]);
+    s.last_res = res;
+    s.last_gn = gn;
+    const bool finite = (res == res) && res <= 1.7976931348623157e308;
+    const bool conv = finite && res <= a.tol * (gn > 1.0 ? gn : 1.0);
+    const bool cont = finite && !conv && s.ne < a.ne_max;
+    if (!cont) {
+        s.last_ne = s.ne;
+        if (!finite) s.diverged = 1;
+        else if (!conv) s.notconv += 1;
+    }
+    cudaGraphSetConditional((cudaGraphConditionalHandle)a.cond, cont ? 1u : 0u);
+}
+
+cudaError_t biot::launch_stop_test(const biot::StopArgs &a, cudaStream_t s)
+{
+    k_stop_test<<<1, 1, 0, s>>>(a);
+    return cudaGetLastError();
+}

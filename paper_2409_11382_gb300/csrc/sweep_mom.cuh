@@ -796,7 +796,7 @@ cudaError_t launch_rows(const SweepArgs<T, TC> &a, cudaStream_t s)
     using SK = SweepKernel<T, TC, KIND, LO, RESTRICT>;
     const int slots = SK::slots();
     if (!slots) return cudaGetLastError() != cudaSuccess ? cudaErrorUnknown : cudaErrorInvalidConfiguration;
-    const int ty = sweep_strip_rows(a.nx, a.ny, slots);
+    int ty = a.rows > 0 ? a.rows + (a.rows & 1) : sweep_strip_rows(a.nx, a.ny, slots);
     dim3 grid((a.nx + SWEEP_NT - 5) / (SWEEP_NT - 4), (a.ny + ty - 1) / ty);
     k_sweep_mom<T, TC, SWEEP_NT, KIND, LO, RESTRICT><<<grid, SWEEP_NT, SK::smem, s>>>(a, ty);
     return cudaGetLastError();

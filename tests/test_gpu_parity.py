@@ -234,6 +234,54 @@ def test_terzaghi_4097_full_size_fp32():
     assert rel(p[:, :512], p_o) < TOL32
 
 
+def test_tolerance_mode_device_loop_matches_host_loop():
+    """Tolerance mode: the V-cycle loop of a step runs on the device (a CUDA-graph
+    WHILE node whose condition a stopping-test kernel sets) and gives bitwise the
+    result, and the same V-cycle counts, as the host-driven loop."""
+    params, sides, _ = W.terzaghi_33()
+    out = []
+    for direct in (False, True):
+        with biot.Solver(params, sides) as s:
+            if direct:
+                s.sweep_timing(True)  # instrumentation forces direct launches and the host loop
+            nes = []
+            for _ in range(6):
+                s.step(1)
+                nes.append(s.stats()["last_ne"])
+            s.step(4)
+            st = s.stats()
+            out.append((s.read_u()[0], s.read_p()[0], nes, st["total_cycles"], st["last_ne"]))
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+    assert out[0][2] == out[1][2] and min(out[0][2]) >= 1
+    assert out[0][3] == out[1][3] and out[0][4] == out[1][4]
+
+
+def test_tolerance_mode_not_converged_is_reported_from_the_device_loop():
+    params, sides, _ = W.terzaghi_33()
+    params = dict(params, tol=1e-30, ne_max=2)  # unreachable tolerance
+    with biot.Solver(params, sides) as s:
+        assert s.step(1) == biot.ERR_NOT_CONVERGED   # first solve: host loop
+        assert s.step(3) == biot.ERR_NOT_CONVERGED   # device loop
+        st = s.stats()
+        assert st["last_ne"] == 2 and st["notconv_steps"] == 5  # t = 0 solve + 4 steps
+
+
+def test_autotuned_launch_shapes_do_not_change_results():
+    """biot_autotune picks strip heights per level and sweep mode; the arithmetic
+    per cell is the same for every strip height, so results are bitwise equal."""
+    params, sides, _ = W.step_load_257(alpha=1.0, precision=W.FP32, n=1024, ne_fixed=3)
+    params = dict(params, c0=0.1)
+    out = []
+    for tune in (False, True):
+        with biot.Solver(params, sides) as s:
+            if tune:
+                shapes = s.autotune()
+                assert shapes and all(r >= 4 for r, _ in shapes.values())
+            s.step(2)
+            out.append((s.read_u()[0], s.read_p()[0]))
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+
+
 def test_graph_replay_matches_direct_launches():
     """Fixed-cycle steps replayed from captured CUDA graphs (both flow-buffer
     parities) give bitwise the result of launching every kernel directly."""
@@ -250,3 +298,27 @@ def test_graph_replay_matches_direct_launches():
     assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
     assert out[0][2]["total_cycles"] == out[1][2]["total_cycles"]
     assert out[0][2]["kernel_launches"] == out[1][2]["kernel_launches"]
+
+
+@pytest.mark.parametrize("precision", [W.FP64, W.FP32])
+def test_checkpoint_resume_is_bitwise(precision):
+    """Saving after k steps and resuming in a fresh instance gives bitwise the
+    uninterrupted run (§5 checkpoint / resume)."""
+    params, sides, _ = W.step_load_257(alpha=1.0, precision=precision, n=64)
+    params = dict(params, c0=0.1)
+    with biot.Solver(params, sides) as a:
+        a.step(4)
+        blob = a.save()
+        a.step(3)
+        ref = (a.read_u(), a.read_p()[0], a.stats()["total_cycles"])
+    with biot.Solver(params, sides) as b:
+        b.load(blob)
+        assert b.read_u()[1] == pytest.approx(4 * params["dt"])
+        b.step(3)
+        got = (b.read_u(), b.read_p()[0], b.stats()["total_cycles"])
+    assert np.array_equal(got[0][0], ref[0][0]) and got[0][1] == ref[0][1]
+    assert np.array_equal(got[1], ref[1]) and got[2] == ref[2]
+    with biot.Solver(dict(params, nx=32, ny=32, levels=3), W.top_load_sides(32, W.step_load(32))) as c:
+        with pytest.raises(biot.BiotError) as e:
+            c.load(blob)
+        assert e.value.code == biot.ERR_INVALID_ARG
