@@ -177,10 +177,12 @@ def run_reference(args):
         "n_gpus": 0, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * total / args.steps * (4096 * 4096) / cells,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": WORKLOAD + "_strip512_oracle", "cells": "512x4096",
-                                        "levels": 10, "ne_fixed": 3, "K": 4},
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "cells": "4096x4096", "levels": 10, "ne_fixed": 3, "K": 4, "gamma": 0.75,
+                   "precision": "fp64 (the oracle)", "parallelism": "replicas1"},
         "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": 1, "kind": "oracle",
-                         "sample": "each step: 1 physical step on a 512x4096-cell strip of the workload"},
+                         "sample": "each step: 1 physical step of the workload restricted to a 512x4096-cell "
+                                   "strip (x-independent solution, same per-cell work)"},
         "e2e": {"value": value, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         "note": "ms_per_step extrapolated linearly from the strip to 4096x4096 cells",
     }
@@ -295,9 +297,11 @@ def run_ours(args):
         fields = {}
         cpu_base = cpu_baseline_entry(fields)
         accuracy = accuracy_vs_oracle(fields, args.n)
-    # finest-level smoothing sweep, FP32: 8 moments + 2 low parts in and out, F~ in;
-    # the prolongated correction (8 coarse moments per 4 cells) once per 2K sweeps
-    bytes_per_cell = (10 + 10 + 2) * 4.0 + 8.0 / (2 * params["K"])
+    # finest-level smoothing sweep, FP32, fixed V-cycle count: the 5 moments that carry
+    # state (the ghost moments 12, 21, 22 are elided) + 2 low parts in and out, F~ in;
+    # the prolongated correction (5 coarse moments per 4 cells) once per 2K sweeps
+    nm = 5 if params["ne_fixed"] > 0 else 8
+    bytes_per_cell = ((nm + 2) * 2 + 2) * 4.0 + nm * 4.0 / 4.0 / (2 * params["K"])
     avg_sweep_ms = sweep_ms / max(sweep_n, 1)
     achieved = bytes_per_cell * cells / (avg_sweep_ms / 1e3) / 1e9
     traffic_pc = profiled_traffic_per_cell()
@@ -330,6 +334,24 @@ def run_ours(args):
     if world > 1:
         torch.distributed.destroy_process_group()
     return 0
+
+
+def oracle_errors(cases, steps):
+    """Max over cases of the L-infinity / L2 relative errors of eta and p against
+    the FP64 oracle run for the same number of steps.  cases: [((params, sides), (eta, p))]."""
+    from oracle import oracle as O
+    from paper_2409_11382_gb300 import workloads as W
+    out = {"eta_linf_rel": 0.0, "eta_l2_rel": 0.0, "p_linf_rel": 0.0, "p_l2_rel": 0.0}
+    for (params, sides), (eta, p) in cases:
+        o = O.Oracle(dict(params, precision=W.FP64), sides)
+        o.step(steps)
+        eo, po = o.read_u()[0], o.read_p()[0]
+        o.close()
+        for name, g, r in (("eta", eta, eo), ("p", p, po)):
+            out[f"{name}_linf_rel"] = max(out[f"{name}_linf_rel"], float(np.abs(g - r).max() / np.abs(r).max()))
+            out[f"{name}_l2_rel"] = max(out[f"{name}_l2_rel"], float(np.linalg.norm(g - r) / np.linalg.norm(r)))
+    out["how"] = f"{len(cases)} smallest instance(s) after {steps} steps vs the FP64 oracle"
+    return out
 
 
 def _percentile(v, q):
@@ -383,7 +405,11 @@ def run_batched(args):
     e2e = time.perf_counter() - t1
     for p, sides in probs:
         h2d += sides[W.TOP]["eta_profile"].nbytes + sides[W.TOP]["p_profile"].nbytes
+    total_steps = args.warmup + args.steps + e2e_steps
+    small = sorted(range(len(probs)), key=lambda i: probs[i][0]["nx"])[:2]
+    got = {i: (b[i].read_u()[0], b[i].read_p()[0]) for i in small}
     b.close()
+    accuracy = oracle_errors([(probs[i], got[i]) for i in small], total_steps) if rank == 0 else None
     value = world * cells * args.steps / secs / 1e6
     line = {"metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps, "higher_is_better": True,
@@ -395,7 +421,7 @@ def run_batched(args):
             "e2e": {"value": cells * e2e_steps / e2e / 1e6, "unit": "MLUPS",
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h // e2e_steps},
             "gpu_launches": st["launches_per_step"] * args.steps,
-            "batch": st, "clocks": clock_info}
+            "batch": st, "accuracy": accuracy, "clocks": clock_info}
     if rank == 0:
         print(json.dumps(line), flush=True)
     _finish_dist(world)
@@ -442,6 +468,8 @@ def run_served(args):
         infos = [srv.poll(rid) for rid in ids]
         st = srv.stats()
         checks = [srv.fetch(rid) for rid in ids[:2]]
+        ismall = min(range(len(reqs)), key=lambda i: reqs[i][1]["nx"])
+        small_res = srv.fetch(ids[ismall])
     clock_info = clocks.stop() if clocks else None
     lat = [i["t_done"] - i["t_submit"] for i in infos]
 
@@ -468,9 +496,11 @@ def run_served(args):
         with biot.Solver(p, s) as sol:
             sol.solve_to(T)
             same = same and np.array_equal(eta, sol.read_u()[0]) and np.array_equal(pr, sol.read_p()[0])
+    _, sp, ss, sT = reqs[ismall]
+    accuracy = oracle_errors([((sp, ss), (small_res[0], small_res[1]))], int(round(sT / sp["dt"]))) if rank == 0 else None
     value = world * cells_steps / makespan / 1e6
     line = {"metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world,
-            "steps": args.requests, "warmup": 1, "higher_is_better": True, "scaling": "weak",
+            "steps": args.requests, "accuracy": accuracy, "warmup": 1, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "served_poisson_64-1024_fp32", "requests": len(reqs),
                        "mean_in_flight_target": 8, "budget_gb": args.budget_gb,

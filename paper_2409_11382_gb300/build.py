@@ -29,6 +29,7 @@ UNITS = {
     "biot_capi.cu": [],
     "kernels_fp64.cu": ["--fmad=false"],
     "kernels_fp32.cu": [],
+    "kernels_fp32c.cu": [],
 }
 
 

@@ -41,6 +41,7 @@ struct SweepArgs {
     double c0h;                  // c0 * h (lattice traction per unit traction)
     unsigned long long *resmax;  // [2] ordered bits of max|g - g**| and max|g|, or nullptr
     int rows;                    // strip height of the launch (0: the default choice)
+    int ghosts;                  // 1: load and store the ghost moments 12, 21, 22 (tolerance mode)
     // the same coefficients, evaluated once on the host in the storage type:
     T k_fs;   // coef_fstar * dD/dm_s = -(alpha^2 r / 2) * 3 / (2 (3 lm + 1))
     T k_ws;   // 1 - om_s
@@ -56,7 +57,7 @@ struct SweepItem {
 };
 
 // Storage kind of a sweep launch (bit flags).
-enum { SWEEP_V_COARSE = 1, SWEEP_V_LO = 2, SWEEP_V_RESTRICT = 4 };
+enum { SWEEP_V_COARSE = 1, SWEEP_V_LO = 2, SWEEP_V_RESTRICT = 4, SWEEP_V_NOGHOST = 8 };
 
 // Explicit part of the effective source (eq. source:implicit) per cell.
 template <typename T>

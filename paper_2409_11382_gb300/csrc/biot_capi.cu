@@ -249,6 +249,7 @@ int sweep_typed(biot_ctx *h, int l, int mode, bool zero_init, bool prolong, bool
     a.c0h = h->P.c0 * h->h;
     a.resmax = want_res ? h->resmax : nullptr;
     a.rows = Lv.rows[mode];
+    a.ghosts = h->P.ne_fixed > 0 ? 0 : 1;
     a.k_fs = T(a.coef_fstar * (-1.5 / (3.0 * a.lm + 1.0)));
     a.k_ws = T(1.0 - a.om_s);
     a.k_wd = T(1.0 - a.om_d);
@@ -258,7 +259,8 @@ int sweep_typed(biot_ctx *h, int l, int mode, bool zero_init, bool prolong, bool
     if (h->rec) {
         SweepJob j{};
         j.tkind = sizeof(T) == 8 ? 0 : (sizeof(TC) == 8 ? 1 : 2);
-        j.variant = (fine ? 0 : SWEEP_V_COARSE) | (fine && a.glo ? SWEEP_V_LO : 0) | (mode == SWEEP_RESTRICT ? SWEEP_V_RESTRICT : 0);
+        j.variant = (fine ? 0 : SWEEP_V_COARSE) | (fine && a.glo ? SWEEP_V_LO : 0) | (mode == SWEEP_RESTRICT ? SWEEP_V_RESTRICT : 0) |
+                    (a.ghosts ? 0 : SWEEP_V_NOGHOST);
         j.level = l;
         job_args<T, TC>(j) = a;
         h->rec->push_back(j);
@@ -851,6 +853,8 @@ int biot_set_sources(biot_handle h, const double *f_body, const double *s)
 {
     if (!h) return fail(BIOT_ERR_INVALID_ARG, "null handle");
     const size_t np = (size_t)h->P.nx * h->P.ny;
+    const double *fb0 = h->fbody, *s0 = h->src;
+    const bool hf0 = h->has_fbody, hs0 = h->has_src;
     int rc;
     if (f_body) {
         if (!h->fbody && (rc = dev_alloc(h, (void **)&h->fbody, 2 * np * sizeof(double)))) return rc;
@@ -865,8 +869,10 @@ int biot_set_sources(biot_handle h, const double *f_body, const double *s)
     h->se_stale = true;
     h->ft_fresh = false;
     CUDA_TRY(cudaStreamSynchronize(h->stream));
-    drop_graphs(h);
-    h->solved = false;
+    // captured steps read the source buffers when they run; only a new buffer or
+    // a source switched on or off makes them stale
+    if (h->fbody != fb0 || h->src != s0 || h->has_fbody != hf0 || h->has_src != hs0) drop_graphs(h);
+    h->solved = false;  // the elastic solve at the current time must see the new data
     return BIOT_OK;
 }
 
@@ -1088,7 +1094,7 @@ int level_variant(const biot_ctx *h, int l, int mode)
 {
     const bool fine = l == h->L - 1;
     return (fine ? 0 : SWEEP_V_COARSE) | (fine && !h->lv[l].fp64 ? SWEEP_V_LO : 0) |
-           (mode == SWEEP_RESTRICT ? SWEEP_V_RESTRICT : 0);
+           (mode == SWEEP_RESTRICT ? SWEEP_V_RESTRICT : 0) | (h->P.ne_fixed > 0 ? SWEEP_V_NOGHOST : 0);
 }
 
 int tkind_slots(int tkind, int variant)
@@ -1174,7 +1180,7 @@ int batch_plan(biot_batch_s *b)
     for (int t = 0; t < 3; t++) b->slots[t].clear();
     for (int key = 0; key <= maxkey; key++) {
         for (int tk = 0; tk < 3; tk++) {
-            for (int v = 0; v < 8; v++) {
+            for (int v = 0; v < 16; v++) {
                 std::vector<BatchSlot> grp;
                 double cells = 0;
                 for (const BatchSlot &s : bykey[key]) {

@@ -1,7 +1,6 @@
-// FP32 instantiation of the kernels: moment storage, FP32 collisions; the
-// coarsest multigrid level stays FP64 (float -> double level pair).
+// FP32 instantiation of the kernels: moment storage, FP32 collisions (levels
+// whose next coarser level is also FP32, and the per-cell field kernels).
 #include "instantiate.h"
 
 BIOT_SWEEP_MOM(float, float)
-BIOT_SWEEP_MOM(float, double)
 BIOT_FIELDS(float)

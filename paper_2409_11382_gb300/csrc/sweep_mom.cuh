@@ -47,7 +47,16 @@ namespace biot {
 // FINE: finest level (explicit force F~, boundary data; double-float first
 // moments when LO).  COARSE: residual right-hand side r, homogeneous walls.
 // ---------------------------------------------------------------------------
-enum { KIND_FINE = 0, KIND_COARSE = 1 };
+// KIND bit 0: finest (0) or coarse (1) level; bit 1 (KIND_NOGHOST): the ghost
+// moments m_12, m_21, m_22 are neither loaded nor stored.  Their relaxation rate
+// is 1 (Tab. moments), so the collision overwrites them: the other moments, the
+// restricted residual (coarse levels read r_0..r_4) and every output are
+// independent of them, and only the residual norm contains them.  With fixed
+// V-cycle counts they are elided (the norm then covers the other five moments'
+// residuals); the tolerance mode keeps them for the paper's norm.
+enum { KIND_FINE = 0, KIND_COARSE = 1, KIND_NOGHOST = 2 };
+__host__ __device__ constexpr bool kind_fine(int k) { return (k & 1) == 0; }
+__host__ __device__ constexpr bool kind_ghosts(int k) { return (k & KIND_NOGHOST) == 0; }
 
 template <typename T>
 struct alignas(4 * sizeof(T)) V4 {
@@ -64,7 +73,7 @@ struct RingLayout {
     // (COARSE); v12 r_4 (COARSE).
     static constexpr int XV = 8;
     static constexpr int LOV = 10;
-    static constexpr int RV = KIND == KIND_COARSE ? 13 : 12;  // values fetched per cell
+    static constexpr int RV = kind_fine(KIND) ? 12 : 13;  // values fetched per cell
     // In shared memory m_s (v3, read by the neighbours' F_* stencil) has a
     // plane of its own; the other values of a cell, used only by the thread of
     // its column, are packed into three 4-vectors:
@@ -154,15 +163,18 @@ __device__ __forceinline__ void fetch_cell(const SweepArgs<T, TC> &a, int gx, in
     gx = clampi(gx, a.nx);
     gy = clampi(gy, a.ny);
     const size_t idx = (size_t)gy * a.nx + gx;
+    constexpr int NM = kind_ghosts(KIND) ? 8 : 5;  // moment planes loaded
     if (a.zero_init) {
 #pragma unroll
         for (int k = 0; k < 8; k++) v[k] = T(0);
     } else {
         const T *g = a.g + idx;
 #pragma unroll
-        for (int k = 0; k < 8; k++) v[k] = g[k * NP];
+        for (int k = 0; k < NM; k++) v[k] = g[k * NP];
+#pragma unroll
+        for (int k = NM; k < 8; k++) v[k] = T(0);
     }
-    if (KIND == KIND_FINE) {
+    if (kind_fine(KIND)) {
         v[L::XV] = a.Ft[idx];
         v[L::XV + 1] = a.Ft[NP + idx];
         if (LO) {
@@ -188,7 +200,7 @@ __device__ __forceinline__ void fetch_cell(const SweepArgs<T, TC> &a, int gx, in
             v[1] += (T)a.gc[NPc + cidx];
         }
 #pragma unroll
-        for (int k = 2; k < 8; k++) v[k] += (T)a.gc[k * NPc + cidx];
+        for (int k = 2; k < NM; k++) v[k] += (T)a.gc[k * NPc + cidx];
     }
 }
 
@@ -215,7 +227,7 @@ __device__ __forceinline__ void collide_cell(const SweepArgs<T, TC> &a, const Ri
     const T cf = a.k_fs;  // alpha^2 r/2 * dD/dm_s
     T Fx = cf * ((dE - dW) * T(1.0 / 3.0) + ((dNE + dSE) - (dNW + dSW)) * T(1.0 / 12.0));
     T Fy = cf * ((dN - dS) * T(1.0 / 3.0) + ((dNE + dNW) - (dSE + dSW)) * T(1.0 / 12.0));
-    if (KIND == KIND_FINE) {
+    if (kind_fine(KIND)) {
         Fx += q1.w;  // F~
         Fy += q2.x;
     } else {           // minus the residual right-hand side r_0..r_4
@@ -298,7 +310,7 @@ __device__ __forceinline__ PVal<T> pull(const SweepArgs<T, TC> &a, const Rings<T
         v.sig = -o.sig;
         v.bx = -o.bx;
         v.by = -o.by;
-        if (KIND == KIND_FINE && a.prof[side]) v.sig += T(a.c0h * traction_term(a.prof[side], side, n, x, y, cx, cy));
+        if (kind_fine(KIND) && a.prof[side]) v.sig += T(a.c0h * traction_term(a.prof[side], side, n, x, y, cx, cy));
         return v;
     }
     // BC_DIRICHLET: eq. BC:elasticity, history = previous call's outgoing population
@@ -309,7 +321,7 @@ __device__ __forceinline__ PVal<T> pull(const SweepArgs<T, TC> &a, const Rings<T
     } else {
         v = o;
     }
-    if (KIND == KIND_FINE && a.prof[side]) v.sig += T(dirichlet_term(a.prof[side], side, n, x, y, cx, cy));
+    if (kind_fine(KIND) && a.prof[side]) v.sig += T(dirichlet_term(a.prof[side], side, n, x, y, cx, cy));
     return v;
 }
 
@@ -378,6 +390,7 @@ __device__ __forceinline__ void residual_cell(const SweepArgs<T, TC> &a, const R
     d[3] = gcur[3] - ((P0.Ss + P1.Ss) + T(2) * (P2.Ss + P3.Ss));
     d[4] = gcur[4] - (P0.Ss - P1.Ss);
     d[7] = gcur[7] - (P2.Ss + P3.Ss);
+    constexpr bool GH = kind_ghosts(KIND);
     if (WALL) {
         d[0] -= ((P0.dbx + P2.dbx) - P3.dbx) * mxf + ((P0.dby + P2.dby) - P3.dby) * myf;
         d[1] -= ((P1.dbx + P2.dbx) + P3.dbx) * mxf + ((P1.dby + P2.dby) + P3.dby) * myf;
@@ -395,6 +408,7 @@ __device__ __forceinline__ void residual_cell(const SweepArgs<T, TC> &a, const R
         if (x == a.nx - 1 && a.bc[SIDE_RIGHT] == BC_DIRICHLET) { BIOT_HIST(SIDE_RIGHT, y, 0); BIOT_HIST(SIDE_RIGHT, y, 4); BIOT_HIST(SIDE_RIGHT, y, 7); }
 #undef BIOT_HIST
     }
+    if (!GH) d[5] = d[6] = d[7] = T(0);  // elided ghost moments (see KIND_NOGHOST)
 }
 
 // One strip (column block bx, row block by of TY rows) of one sweep; the body
@@ -484,7 +498,7 @@ __device__ __forceinline__ void sweep_strip(const SweepArgs<T, TC> &a, int bx, i
                 const size_t idx = (size_t)y * nx + x;
                 T *go = a.gout + idx;
 #pragma unroll
-                for (int k = 2; k < 8; k++) go[k * NP] = gcur[k] - gam * d[k];
+                for (int k = 2; k < (kind_ghosts(KIND) ? 8 : 5); k++) go[k * NP] = gcur[k] - gam * d[k];
                 // first moments: (hi + lo) - gamma d, renormalised into hi + lo with LO
                 if (LO) {
                     const V4<T> g2 = rg.R4(sb, 2, t);
@@ -523,7 +537,7 @@ __device__ __forceinline__ void sweep_strip(const SweepArgs<T, TC> &a, int bx, i
                     const size_t NPc = NP >> 2;
                     const size_t cidx = (size_t)(y >> 1) * (nx >> 1) + (x >> 1);
 #pragma unroll
-                    for (int k = 0; k < 8; k++) a.rc[k * NPc + cidx] = tot[k];
+                    for (int k = 0; k < (kind_ghosts(KIND) ? 8 : 5); k++) a.rc[k * NPc + cidx] = tot[k];
                 }
             }
         }
@@ -659,7 +673,7 @@ __global__ void __launch_bounds__(TileShape<TX, TY>::NT) k_sweep_tile(const Swee
             T *go = a.gout + idx;
             const T gam = a.k_gam;
 #pragma unroll
-            for (int k = 2; k < 8; k++) go[k * NP] = gcur[k] - gam * d[k];
+            for (int k = 2; k < (kind_ghosts(KIND) ? 8 : 5); k++) go[k * NP] = gcur[k] - gam * d[k];
             if (LO) {
                 const V4<T> g2 = rg.R4(rrow, 2, c);
                 const T lo[2] = {g2.y, g2.z};
@@ -695,7 +709,7 @@ __global__ void __launch_bounds__(TileShape<TX, TY>::NT) k_sweep_tile(const Swee
                 const size_t cidx = (size_t)yc * (nx >> 1) + xc;
                 const int i0 = (2 * by) * TX + 2 * bx;
 #pragma unroll
-                for (int k = 0; k < 8; k++) {
+                for (int k = 0; k < (kind_ghosts(KIND) ? 8 : 5); k++) {
                     const T *dk = dres + k * TX * TY + i0;
                     // rows first, then columns (the order of the strip kernel)
                     const TC r0 = (TC)(dk[0] + dk[TX]), r1 = (TC)(dk[1] + dk[TX + 1]);
@@ -812,25 +826,50 @@ cudaError_t launch_batch_v(const SweepArgs<T, TC> *jobs, const SweepItem *items,
     return cudaGetLastError();
 }
 
+// Storage kind of a launch from the SWEEP_V_* flags / the arguments.
+template <typename T, typename TC, template <typename, typename, int, bool, bool> class F, typename... A>
+auto dispatch_kind(bool coarse, bool lo, bool rs, bool ghosts, A &&...args)
+{
+    const int g = ghosts ? 0 : KIND_NOGHOST;
+    if (coarse) {
+        if (g) return rs ? F<T, TC, KIND_COARSE | KIND_NOGHOST, false, true>::run(args...) : F<T, TC, KIND_COARSE | KIND_NOGHOST, false, false>::run(args...);
+        return rs ? F<T, TC, KIND_COARSE, false, true>::run(args...) : F<T, TC, KIND_COARSE, false, false>::run(args...);
+    }
+    if constexpr (sizeof(T) == 4) {  // double-float low parts exist only with FP32 storage
+        if (lo) {
+            if (g) return rs ? F<T, TC, KIND_FINE | KIND_NOGHOST, true, true>::run(args...) : F<T, TC, KIND_FINE | KIND_NOGHOST, true, false>::run(args...);
+            return rs ? F<T, TC, KIND_FINE, true, true>::run(args...) : F<T, TC, KIND_FINE, true, false>::run(args...);
+        }
+    }
+    if (g) return rs ? F<T, TC, KIND_FINE | KIND_NOGHOST, false, true>::run(args...) : F<T, TC, KIND_FINE | KIND_NOGHOST, false, false>::run(args...);
+    return rs ? F<T, TC, KIND_FINE, false, true>::run(args...) : F<T, TC, KIND_FINE, false, false>::run(args...);
+}
+
+template <typename T, typename TC, int KIND, bool LO, bool RS>
+struct BatchRun {
+    static cudaError_t run(const SweepArgs<T, TC> *jobs, const SweepItem *items, int n, cudaStream_t s)
+    { return launch_batch_v<T, TC, KIND, LO, RS>(jobs, items, n, s); }
+};
+template <typename T, typename TC, int KIND, bool LO, bool RS>
+struct SlotsRun {
+    static int run() { return SweepKernel<T, TC, KIND, LO, RS>::slots(); }
+};
+template <typename T, typename TC, int KIND, bool LO, bool RS>
+struct RowsRun {
+    static cudaError_t run(const SweepArgs<T, TC> &a, cudaStream_t s) { return launch_rows<T, TC, KIND, LO, RS>(a, s); }
+};
+
 template <typename T, typename TC>
 cudaError_t launch_sweep_batch_impl(int v, const SweepArgs<T, TC> *jobs, const SweepItem *items, int n, cudaStream_t s)
 {
-    const bool coarse = v & SWEEP_V_COARSE, lo = v & SWEEP_V_LO, rs = v & SWEEP_V_RESTRICT;
-    if (coarse) return rs ? launch_batch_v<T, TC, KIND_COARSE, false, true>(jobs, items, n, s)
-                          : launch_batch_v<T, TC, KIND_COARSE, false, false>(jobs, items, n, s);
-    if (lo) return rs ? launch_batch_v<T, TC, KIND_FINE, true, true>(jobs, items, n, s)
-                      : launch_batch_v<T, TC, KIND_FINE, true, false>(jobs, items, n, s);
-    return rs ? launch_batch_v<T, TC, KIND_FINE, false, true>(jobs, items, n, s)
-              : launch_batch_v<T, TC, KIND_FINE, false, false>(jobs, items, n, s);
+    return dispatch_kind<T, TC, BatchRun>(v & SWEEP_V_COARSE, v & SWEEP_V_LO, v & SWEEP_V_RESTRICT,
+                                         !(v & SWEEP_V_NOGHOST), jobs, items, n, s);
 }
 
 template <typename T, typename TC>
 int sweep_slots_impl(int v)
 {
-    const bool coarse = v & SWEEP_V_COARSE, lo = v & SWEEP_V_LO, rs = v & SWEEP_V_RESTRICT;
-    if (coarse) return rs ? SweepKernel<T, TC, KIND_COARSE, false, true>::slots() : SweepKernel<T, TC, KIND_COARSE, false, false>::slots();
-    if (lo) return rs ? SweepKernel<T, TC, KIND_FINE, true, true>::slots() : SweepKernel<T, TC, KIND_FINE, true, false>::slots();
-    return rs ? SweepKernel<T, TC, KIND_FINE, false, true>::slots() : SweepKernel<T, TC, KIND_FINE, false, false>::slots();
+    return dispatch_kind<T, TC, SlotsRun>(v & SWEEP_V_COARSE, v & SWEEP_V_LO, v & SWEEP_V_RESTRICT, !(v & SWEEP_V_NOGHOST));
 }
 
 // Level kind from the arguments: F~ present = finest level; low parts only
@@ -838,12 +877,8 @@ int sweep_slots_impl(int v)
 template <typename T, typename TC>
 cudaError_t launch_sweep_mom_impl(const SweepArgs<T, TC> &a, cudaStream_t s)
 {
-    const bool restrict_ = a.mode == SWEEP_RESTRICT;
-    if (a.Ft) {
-        if (a.glo) return restrict_ ? launch_rows<T, TC, KIND_FINE, true, true>(a, s) : launch_rows<T, TC, KIND_FINE, true, false>(a, s);
-        return restrict_ ? launch_rows<T, TC, KIND_FINE, false, true>(a, s) : launch_rows<T, TC, KIND_FINE, false, false>(a, s);
-    }
-    return restrict_ ? launch_rows<T, TC, KIND_COARSE, false, true>(a, s) : launch_rows<T, TC, KIND_COARSE, false, false>(a, s);
+    return dispatch_kind<T, TC, RowsRun>(a.Ft == nullptr, a.Ft != nullptr && a.glo != nullptr,
+                                        a.mode == SWEEP_RESTRICT, a.ghosts != 0, a, s);
 }
 
 }  // namespace biot
