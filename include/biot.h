@@ -220,10 +220,12 @@ BIOT_API int biot_autotune(biot_handle h, int *rows_out, double *ms_out, int max
  * Many independent instances (different grids, materials, boundary data) advanced
  * together.  Each physical step of every instance is Alg. 5 exactly as in
  * biot_step -- same kernels, same arithmetic, bitwise the same result as the
- * instance stepped alone -- but the multigrid sweeps of all instances are
- * regrouped: the V-cycles are aligned by depth below the finest level and each
- * phase is one work-list launch per storage kind whose CTAs process strips of
- * sweeps of different instances and levels; the whole step is one CUDA graph.
+ * instance stepped alone (FP64; FP32 within rounding, the kernel forms can
+ * differ) -- but the launches of all instances are regrouped: the V-cycles are
+ * aligned at the coarsest level and each phase is one work-list launch per
+ * storage kind whose CTAs process strips or tiles of sweeps of different
+ * instances; the flow steps are one work-list launch; the whole step is one
+ * CUDA graph.
  * Instances need a fixed number of V-cycles (ne_fixed > 0) and equal K and
  * ne_fixed.  The batch owns its instances: read them with biot_read_u / _p /
  * _stress / biot_stats_get through biot_batch_instance, do not destroy them or

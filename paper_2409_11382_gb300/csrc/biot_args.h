@@ -57,7 +57,12 @@ struct SweepItem {
 };
 
 // Storage kind of a sweep launch (bit flags).
-enum { SWEEP_V_COARSE = 1, SWEEP_V_LO = 2, SWEEP_V_RESTRICT = 4, SWEEP_V_NOGHOST = 8 };
+enum { SWEEP_V_COARSE = 1, SWEEP_V_LO = 2, SWEEP_V_RESTRICT = 4, SWEEP_V_NOGHOST = 8, SWEEP_V_TILE = 16 };
+// Tile sweeps: levels of at most SWEEP_TILE_CELLS cells (single instance); tile
+// shape per storage type.  The fused flow step works on FLOW_TILE_X x FLOW_TILE_Y tiles.
+constexpr long SWEEP_TILE_CELLS = 256L * 256L;
+inline void sweep_tile_shape(bool fp64, int *tx, int *ty) { *tx = fp64 ? 8 : 32; *ty = fp64 ? 2 : 8; }
+constexpr int FLOW_TILE_X = 32, FLOW_TILE_Y = 8;
 
 // Explicit part of the effective source (eq. source:implicit) per cell.
 template <typename T>
@@ -193,6 +198,16 @@ template <typename T> cudaError_t launch_sexp(const SexpArgs<T> &a, cudaStream_t
 template <typename T> cudaError_t launch_force(const ForceArgs<T> &a, cudaStream_t s);
 template <typename T> cudaError_t launch_readout(const ReadoutArgs<T> &a, cudaStream_t s);
 template <typename T> cudaError_t launch_flow_fused(const FlowFusedArgs<T> &a, cudaStream_t s);
+// Batched flow steps: one work item per FLOW_TILE_X x FLOW_TILE_Y tile of an instance (job).
+template <typename T>
+cudaError_t launch_flow_fused_batch(const FlowFusedArgs<T> *jobs, const SweepItem *items, int n, cudaStream_t s);
+// Batched copies of FP64 planes: one work item per 1024 values of a job.
+struct CopyJob {
+    double *dst;
+    const double *src;
+    size_t n;
+};
+cudaError_t launch_copy_batch(const CopyJob *jobs, const SweepItem *items, int n, cudaStream_t s);
 template <typename T> cudaError_t launch_init(const InitArgs<T> &a, cudaStream_t s);
 
 }  // namespace biot

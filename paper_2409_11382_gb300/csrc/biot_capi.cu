@@ -10,6 +10,7 @@
 
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <atomic>
 #include <chrono>
@@ -37,6 +38,16 @@ struct SweepJob {
     SweepArgs<float, double> fd;
     SweepArgs<float, float> ff;
 };
+// A flow step prepared for a batched launch, with its history copy.
+struct FlowRec {
+    int fp64;
+    FlowFusedArgs<float> f;
+    FlowFusedArgs<double> d;
+    CopyJob copy;
+};
+template <typename T> FlowFusedArgs<T> &flow_args(FlowRec &r);
+template <> FlowFusedArgs<float> &flow_args<float>(FlowRec &r) { return r.f; }
+template <> FlowFusedArgs<double> &flow_args<double>(FlowRec &r) { return r.d; }
 template <typename T, typename TC> SweepArgs<T, TC> &job_args(SweepJob &j);
 template <> SweepArgs<double, double> &job_args<double, double>(SweepJob &j) { return j.dd; }
 template <> SweepArgs<float, double> &job_args<float, double>(SweepJob &j) { return j.fd; }
@@ -61,6 +72,18 @@ int fail(int code, const std::string &msg)
     } while (0)
 
 constexpr int MAX_LEVELS = 16;
+
+// FP32 coarse levels carry their first moments as double-float too (the
+// environment variable BIOT_COARSE_LO=0 turns this off, for comparisons).
+bool coarse_lo()
+{
+    static int v = -1;
+    if (v < 0) {
+        const char *e = getenv("BIOT_COARSE_LO");
+        v = (e && e[0] == '0') ? 0 : 1;
+    }
+    return v != 0;
+}
 
 struct Level {
     int nx = 0, ny = 0;
@@ -129,6 +152,7 @@ struct biot_ctx {
     bool measure_cycle = true;
     // record mode (batched execution): sweeps are appended here instead of launched
     std::vector<biot::SweepJob> *rec = nullptr;
+    std::vector<biot::FlowRec> *frec = nullptr;  // record mode: flow steps appended here
 };
 
 namespace {
@@ -259,7 +283,7 @@ int sweep_typed(biot_ctx *h, int l, int mode, bool zero_init, bool prolong, bool
     if (h->rec) {
         SweepJob j{};
         j.tkind = sizeof(T) == 8 ? 0 : (sizeof(TC) == 8 ? 1 : 2);
-        j.variant = (fine ? 0 : SWEEP_V_COARSE) | (fine && a.glo ? SWEEP_V_LO : 0) | (mode == SWEEP_RESTRICT ? SWEEP_V_RESTRICT : 0) |
+        j.variant = (fine ? 0 : SWEEP_V_COARSE) | (a.glo ? SWEEP_V_LO : 0) | (mode == SWEEP_RESTRICT ? SWEEP_V_RESTRICT : 0) |
                     (a.ghosts ? 0 : SWEEP_V_NOGHOST);
         j.level = l;
         job_args<T, TC>(j) = a;
@@ -540,10 +564,18 @@ int flow_typed(biot_ctx *h)
     a.k_mah = T(-(h->P.alpha * h->h));
     a.k_a1r = T(a.a_over_h * (1.0 - a.r));
     a.k_ar = T(a.a_over_h * a.r);
-    CUDA_TRY(launch_flow_fused<T>(a, h->stream));
-    h->launches++;
-    // D(t) into the buffer of D(t - 2 dt), then D1 <- D(t), D2 <- D(t - dt)
-    CUDA_TRY(cudaMemcpyAsync(h->D2, h->SE, np * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+    if (h->frec) {  // batched step: the batch launches it with the others
+        FlowRec r{};
+        r.fp64 = sizeof(T) == 8;
+        flow_args<T>(r) = a;
+        r.copy = CopyJob{h->D2, h->SE, np};
+        h->frec->push_back(r);
+    } else {
+        CUDA_TRY(launch_flow_fused<T>(a, h->stream));
+        h->launches++;
+        // D(t) into the buffer of D(t - 2 dt), then D1 <- D(t), D2 <- D(t - dt)
+        CUDA_TRY(cudaMemcpyAsync(h->D2, h->SE, np * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+    }
     std::swap(h->D1, h->D2);
     h->ft_fresh = true;   // F~ of the next elastic solve is computed
     h->se_stale = true;   // the s'_exp buffer was used as scratch
@@ -797,7 +829,7 @@ int biot_create(const biot_params *p, const biot_side sides[4], biot_handle *out
         const size_t esz = Lv.fp64 ? sizeof(double) : sizeof(float);
         TRY_RC(dev_alloc(h, &Lv.g[0], 8 * Lv.np * esz));
         TRY_RC(dev_alloc(h, &Lv.g[1], 8 * Lv.np * esz));
-        if (!Lv.fp64 && l == h->L - 1) {  // double-float displacement moments
+        if (!Lv.fp64 && (l == h->L - 1 || coarse_lo())) {  // double-float displacement moments
             TRY_RC(dev_alloc(h, &Lv.glo[0], 2 * Lv.np * esz));
             TRY_RC(dev_alloc(h, &Lv.glo[1], 2 * Lv.np * esz));
         }
@@ -1053,15 +1085,19 @@ extern "C" int biot_read_u_noalloc(biot_handle h, double *eta, double *t_out)
 // ============================================================================
 // Batched execution of many instances (one CUDA graph per time step).
 //
-// Every instance keeps its own state and runs exactly the launch sequence of
-// biot_step; only the sweeps are regrouped.  The V-cycles of all instances are
-// aligned by depth below the finest level: the down-legs start together, the
-// up-legs end together, and an instance with fewer levels does its coarsest
-// sweeps while deeper instances are still going down.  Each phase of that
-// schedule is one work-list launch per storage kind, whose CTAs take strips of
-// sweeps of different instances and levels.
+// Every instance keeps its own state and runs exactly the sweeps and flow steps
+// of biot_step; only their launches are regrouped.  The V-cycles of all
+// instances are aligned at the coarsest level: the down-legs end together and
+// the up-legs start together, so a phase holds one level index of every
+// instance deep enough to have it, and an instance with fewer levels waits in
+// the outer phases.  Each phase is one work-list launch per storage kind, whose
+// CTAs take strips (or, for levels of at most 64^2 cells and FP64 levels,
+// tiles) of sweeps of different instances; the flow steps of all instances are
+// one work-list launch and one batched copy of the divergence history.
 // ============================================================================
 namespace {
+
+constexpr long BATCH_TILE_CELLS = 64L * 64L;
 
 // One sweep of the static schedule of an instance.
 struct PlanOp {
@@ -1069,18 +1105,22 @@ struct PlanOp {
 };
 
 // Mirror of vcycle(): the sweeps of one V-cycle from level l down, with their
-// phase keys (Dmax: coarsest depth over the batch).
+// phase keys.  Instances are aligned at the coarsest level (level index 0): the
+// down-legs end together and the up-legs start together, so every phase holds
+// the same level index -- the same level size for hierarchies with equal
+// coarsest grids -- of all instances deep enough to have it, and the FP64
+// coarsest sweeps of all instances share their 2K phases.  Dmax: deepest
+// coarsest-level index over the batch.
 void plan_vcycle(const biot_ctx *h, int l, int K, int Dmax, std::vector<PlanOp> &out)
 {
-    const int D = h->L - 1, d = h->L - 1 - l;
-    const int up = Dmax * (K + 1) + 2 * K + Dmax * K;
-    for (int k = 0; k < K; k++) out.push_back({l, SWEEP_SMOOTH, l == 0 ? D * (K + 1) + k : d * (K + 1) + k});
+    const int bottom = Dmax * (K + 1);  // first key of the coarsest sweeps
+    for (int k = 0; k < K; k++) out.push_back({l, SWEEP_SMOOTH, l == 0 ? bottom + k : (Dmax - l) * (K + 1) + k});
     if (l > 0) {
-        out.push_back({l, SWEEP_RESTRICT, d * (K + 1) + K});
+        out.push_back({l, SWEEP_RESTRICT, (Dmax - l) * (K + 1) + K});
         plan_vcycle(h, l - 1, K, Dmax, out);
     }
     for (int k = 0; k < K; k++)
-        out.push_back({l, SWEEP_SMOOTH, l == 0 ? D * (K + 1) + K + k : up - (d + 1) * K + k});
+        out.push_back({l, SWEEP_SMOOTH, l == 0 ? bottom + K + k : bottom + 2 * K + (l - 1) * K + k});
 }
 
 int level_tkind(const biot_ctx *h, int l)
@@ -1093,8 +1133,12 @@ int level_tkind(const biot_ctx *h, int l)
 int level_variant(const biot_ctx *h, int l, int mode)
 {
     const bool fine = l == h->L - 1;
-    return (fine ? 0 : SWEEP_V_COARSE) | (fine && !h->lv[l].fp64 ? SWEEP_V_LO : 0) |
-           (mode == SWEEP_RESTRICT ? SWEEP_V_RESTRICT : 0) | (h->P.ne_fixed > 0 ? SWEEP_V_NOGHOST : 0);
+    // in a batch the launches of a phase are large: strips except for the
+    // smallest levels and FP64 levels
+    const bool tile = (long)h->lv[l].nx * h->lv[l].ny <= BATCH_TILE_CELLS || h->lv[l].fp64;
+    return (fine ? 0 : SWEEP_V_COARSE) | (h->lv[l].glo[0] ? SWEEP_V_LO : 0) |
+           (mode == SWEEP_RESTRICT ? SWEEP_V_RESTRICT : 0) | (h->P.ne_fixed > 0 ? SWEEP_V_NOGHOST : 0) |
+           (tile ? SWEEP_V_TILE : 0);
 }
 
 int tkind_slots(int tkind, int variant)
@@ -1129,6 +1173,13 @@ struct biot_batch_s {
     SweepItem *items_dev = nullptr;
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     std::vector<long> epoch[2];                   // instance epochs the graphs were captured at
+    // batched flow steps: per storage type (0 FP32, 1 FP64) the instances and their
+    // tile work items; copy work items of the D(t) history update
+    std::vector<int> flow_inst[2];
+    std::vector<SweepItem> flow_items[2], copy_items;
+    void *flow_dev[2][2] = {};                    // per graph parity, per type: FlowFusedArgs tables
+    CopyJob *copy_dev[2] = {};
+    SweepItem *flow_items_dev[2] = {}, *copy_items_dev = nullptr;
     long launches_per_step = 0, kernel_launches = 0, nstep = 0;
     std::vector<void *> allocs;
 };
@@ -1180,7 +1231,7 @@ int batch_plan(biot_batch_s *b)
     for (int t = 0; t < 3; t++) b->slots[t].clear();
     for (int key = 0; key <= maxkey; key++) {
         for (int tk = 0; tk < 3; tk++) {
-            for (int v = 0; v < 16; v++) {
+            for (int v = 0; v < 32; v++) {
                 std::vector<BatchSlot> grp;
                 double cells = 0;
                 for (const BatchSlot &s : bykey[key]) {
@@ -1191,17 +1242,25 @@ int batch_plan(biot_batch_s *b)
                     cells += (double)h->lv[o.level].np;
                 }
                 if (grp.empty()) continue;
-                const int slots = tkind_slots(tk, v);
+                const bool tile = (v & SWEEP_V_TILE) != 0;
+                const int slots = tile ? 1 : tkind_slots(tk, v & ~SWEEP_V_TILE);
                 if (!slots) return fail(BIOT_ERR_CUDA, "occupancy query of the batched sweep kernel failed");
                 BatchLaunch L{tk, v, b->slots[tk].size(), b->items.size(), (int)grp.size(), 0};
                 for (size_t g = 0; g < grp.size(); g++) {
                     const biot_ctx *h = b->inst[grp[g].inst];
                     const Level &Lv = h->lv[ops[grp[g].inst][grp[g].op].level];
-                    const int share = (int)(slots * (double)Lv.np / cells) + 1;
-                    const int ty = sweep_strip_rows(Lv.nx, Lv.ny, share);
-                    const int sx = (Lv.nx + SWEEP_STRIP_COLS - 1) / SWEEP_STRIP_COLS, sy = (Lv.ny + ty - 1) / ty;
-                    for (int by = 0; by < sy; by++)
-                        for (int bx = 0; bx < sx; bx++) b->items.push_back({(int)g, bx, by, ty});
+                    if (tile) {  // tiles of the tile sweep
+                        int tx, ty;
+                        sweep_tile_shape(tk == 0, &tx, &ty);
+                        for (int by = 0; by < (Lv.ny + ty - 1) / ty; by++)
+                            for (int bx = 0; bx < (Lv.nx + tx - 1) / tx; bx++) b->items.push_back({(int)g, bx, by, 0});
+                    } else {  // strips sized so that the launch fills the GPU
+                        const int share = (int)(slots * (double)Lv.np / cells) + 1;
+                        const int ty = sweep_strip_rows(Lv.nx, Lv.ny, share);
+                        const int sx = (Lv.nx + SWEEP_STRIP_COLS - 1) / SWEEP_STRIP_COLS, sy = (Lv.ny + ty - 1) / ty;
+                        for (int by = 0; by < sy; by++)
+                            for (int bx = 0; bx < sx; bx++) b->items.push_back({(int)g, bx, by, ty});
+                    }
                     b->slots[tk].push_back(grp[g]);
                 }
                 L.nitems = (int)(b->items.size() - L.item_off);
@@ -1209,7 +1268,35 @@ int batch_plan(biot_batch_s *b)
             }
         }
     }
+    // flow steps and history copies: one job per instance
+    for (int t = 0; t < 2; t++) {
+        b->flow_inst[t].clear();
+        b->flow_items[t].clear();
+    }
+    b->copy_items.clear();
+    for (int i = 0; i < n; i++) {
+        const biot_ctx *h = b->inst[i];
+        const int t = h->fp32 ? 0 : 1;
+        const int job = (int)b->flow_inst[t].size();
+        b->flow_inst[t].push_back(i);
+        for (int by = 0; by < (h->P.ny + FLOW_TILE_Y - 1) / FLOW_TILE_Y; by++)
+            for (int bx = 0; bx < (h->P.nx + FLOW_TILE_X - 1) / FLOW_TILE_X; bx++) b->flow_items[t].push_back({job, bx, by, 0});
+        const size_t np = (size_t)h->P.nx * h->P.ny;
+        for (size_t c = 0; c < (np + 1023) / 1024; c++) b->copy_items.push_back({i, (int)c, 0, 0});
+    }
     int rc;
+    for (int par = 0; par < 2; par++) {
+        if ((rc = batch_alloc(b, &b->flow_dev[par][0], b->flow_inst[0].size() * sizeof(FlowFusedArgs<float>)))) return rc;
+        if ((rc = batch_alloc(b, &b->flow_dev[par][1], b->flow_inst[1].size() * sizeof(FlowFusedArgs<double>)))) return rc;
+        if ((rc = batch_alloc(b, (void **)&b->copy_dev[par], n * sizeof(CopyJob)))) return rc;
+    }
+    for (int t = 0; t < 2; t++) {
+        if ((rc = batch_alloc(b, (void **)&b->flow_items_dev[t], b->flow_items[t].size() * sizeof(SweepItem)))) return rc;
+        if (!b->flow_items[t].empty())
+            CUDA_TRY(cudaMemcpy(b->flow_items_dev[t], b->flow_items[t].data(), b->flow_items[t].size() * sizeof(SweepItem), cudaMemcpyHostToDevice));
+    }
+    if ((rc = batch_alloc(b, (void **)&b->copy_items_dev, b->copy_items.size() * sizeof(SweepItem)))) return rc;
+    CUDA_TRY(cudaMemcpy(b->copy_items_dev, b->copy_items.data(), b->copy_items.size() * sizeof(SweepItem), cudaMemcpyHostToDevice));
     for (int par = 0; par < 2; par++)
         for (int tk = 0; tk < 3; tk++)
             if ((rc = batch_alloc(b, &b->jobs_dev[par][tk], b->slots[tk].size() * tkind_size(tk)))) return rc;
@@ -1241,6 +1328,7 @@ int batch_capture(biot_batch_s *b, int par)
 {
     const int n = (int)b->inst.size();
     std::vector<std::vector<SweepJob>> rec(n);
+    std::vector<FlowRec> frec;
     std::vector<long> l0(n), c0(n);
     CUDA_TRY(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
     int rc = BIOT_OK;
@@ -1250,10 +1338,31 @@ int batch_capture(biot_batch_s *b, int par)
         l0[i] = h->launches;
         c0[i] = h->total_cycles;
         h->rec = &rec[i];
-        rc = advance(h);  // flow step and force are launched (captured); the sweeps are recorded
+        h->frec = &frec;
+        rc = advance(h);  // flow steps and sweeps are recorded, launched below for all instances
         h->rec = nullptr;
+        h->frec = nullptr;
+        if (!rc && frec.size() != (size_t)i + 1) rc = fail(BIOT_ERR_CUDA, "batched schedule: flow step not recorded");
         nl += h->launches - l0[i];
         if (!rc && rec[i].size() != b->nops[i]) rc = fail(BIOT_ERR_CUDA, "batched schedule does not match the recorded sweeps");
+    }
+    // flow steps of all instances, then their history copies
+    if (!rc && !b->flow_items[0].empty()) {
+        cudaError_t e = launch_flow_fused_batch<float>(static_cast<const FlowFusedArgs<float> *>(b->flow_dev[par][0]),
+                                                       b->flow_items_dev[0], (int)b->flow_items[0].size(), b->stream);
+        if (e != cudaSuccess) rc = fail(BIOT_ERR_CUDA, std::string("batched flow launch: ") + cudaGetErrorString(e));
+        nl++;
+    }
+    if (!rc && !b->flow_items[1].empty()) {
+        cudaError_t e = launch_flow_fused_batch<double>(static_cast<const FlowFusedArgs<double> *>(b->flow_dev[par][1]),
+                                                        b->flow_items_dev[1], (int)b->flow_items[1].size(), b->stream);
+        if (e != cudaSuccess) rc = fail(BIOT_ERR_CUDA, std::string("batched flow launch: ") + cudaGetErrorString(e));
+        nl++;
+    }
+    if (!rc) {
+        cudaError_t e = launch_copy_batch(b->copy_dev[par], b->copy_items_dev, (int)b->copy_items.size(), b->stream);
+        if (e != cudaSuccess) rc = fail(BIOT_ERR_CUDA, std::string("batched copy launch: ") + cudaGetErrorString(e));
+        nl++;
     }
     for (size_t k = 0; k < b->launches.size() && !rc; k++) {
         const BatchLaunch &L = b->launches[k];
@@ -1288,6 +1397,17 @@ int batch_capture(biot_batch_s *b, int par)
         else if (tk == 1) batch_fill_typed<float, double>(b, tk, rec, host);
         else batch_fill_typed<float, float>(b, tk, rec, host);
         CUDA_TRY(cudaMemcpy(b->jobs_dev[par][tk], host.data(), host.size(), cudaMemcpyHostToDevice));
+    }
+    {
+        std::vector<FlowFusedArgs<float>> ff;
+        std::vector<FlowFusedArgs<double>> fd;
+        std::vector<CopyJob> cj(n);
+        for (int i : b->flow_inst[0]) ff.push_back(frec[i].f);
+        for (int i : b->flow_inst[1]) fd.push_back(frec[i].d);
+        for (int i = 0; i < n; i++) cj[i] = frec[i].copy;
+        if (!ff.empty()) CUDA_TRY(cudaMemcpy(b->flow_dev[par][0], ff.data(), ff.size() * sizeof(ff[0]), cudaMemcpyHostToDevice));
+        if (!fd.empty()) CUDA_TRY(cudaMemcpy(b->flow_dev[par][1], fd.data(), fd.size() * sizeof(fd[0]), cudaMemcpyHostToDevice));
+        CUDA_TRY(cudaMemcpy(b->copy_dev[par], cj.data(), n * sizeof(CopyJob), cudaMemcpyHostToDevice));
     }
     b->launches_per_step = nl;
     b->epoch[par].clear();
@@ -1466,7 +1586,7 @@ size_t estimate_bytes(const biot_params *p, const biot_side *sides)
         const bool fp64 = !fp32 || (l == 0 && p->mg_levels > 1) || (p->precision == BIOT_FP32_COARSE64 && l < p->mg_levels - 1);
         const size_t esz = fp64 ? 8 : 4;
         b += 2 * 8 * n * esz;
-        if (!fp64 && l == p->mg_levels - 1) b += 2 * 2 * n * esz;
+        if (!fp64 && (l == p->mg_levels - 1 || coarse_lo())) b += 2 * 2 * n * esz;
         if (l < p->mg_levels - 1) b += 8 * n * esz;
         for (int s = 0; s < 4; s++)
             if (sides && sides[s].eta_type == BIOT_DIRICHLET) b += 3 * ((s == BIOT_BOTTOM || s == BIOT_TOP) ? nx : ny) * esz;

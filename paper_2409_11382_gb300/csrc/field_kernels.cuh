@@ -162,6 +162,7 @@ __global__ void __launch_bounds__(256) k_init(const InitArgs<T> a)
 // cell (even extension), as in the elastic sweep.
 // ---------------------------------------------------------------------------
 constexpr int FF_TX = 32, FF_TY = 8, FF_W = FF_TX + 2, FF_H = FF_TY + 2;
+static_assert(FF_TX == FLOW_TILE_X && FF_TY == FLOW_TILE_Y, "flow tile shared with the batch planner");
 
 template <typename T>
 __device__ __forceinline__ int ff_src_index(const FlowFusedArgs<T> &a, int x, int y)
@@ -172,14 +173,22 @@ __device__ __forceinline__ int ff_src_index(const FlowFusedArgs<T> &a, int x, in
 }
 
 template <typename T>
-__global__ void __launch_bounds__(FF_TX * FF_TY) k_flow_fused(const FlowFusedArgs<T> a)
+struct FlowSmem {
+    T fs[9][FF_H][FF_W];  // post-collision populations
+    T qs0[FF_H][FF_W], qA[FF_H][FF_W], qms[FF_H][FF_W];
+};
+
+template <typename T>
+__device__ __forceinline__ void flow_tile(const FlowFusedArgs<T> &a, int bx, int by, FlowSmem<T> &sm)
 {
-    __shared__ T fs[9][FF_H][FF_W];  // post-collision populations
-    __shared__ T qs0[FF_H][FF_W], qA[FF_H][FF_W], qms[FF_H][FF_W];
+    auto &fs = sm.fs;
+    auto &qs0 = sm.qs0;
+    auto &qA = sm.qA;
+    auto &qms = sm.qms;
     const int nx = a.nx, ny = a.ny;
     const size_t NP = (size_t)nx * ny;
     const int tid = threadIdx.x;
-    const int x0 = blockIdx.x * FF_TX, y0 = blockIdx.y * FF_TY;
+    const int x0 = bx * FF_TX, y0 = by * FF_TY;
     // stage: 340 cells over 256 threads
     for (int i = tid; i < FF_W * FF_H; i += FF_TX * FF_TY) {
         const int cx = i % FF_W, cy = i / FF_W;
@@ -285,6 +294,27 @@ __global__ void __launch_bounds__(FF_TX * FF_TY) k_flow_fused(const FlowFusedArg
     a.Ft[NP + idx] = fy;
 }
 
+template <typename T>
+__global__ void __launch_bounds__(FF_TX * FF_TY) k_flow_fused(const FlowFusedArgs<T> a)
+{
+    __shared__ FlowSmem<T> sm;
+    flow_tile<T>(a, blockIdx.x, blockIdx.y, sm);
+}
+
+// Batched form: CTA b processes tile (items[b].bx, items[b].by) of the flow step
+// jobs[items[b].job] (one job per instance of a batch).
+template <typename T>
+__global__ void __launch_bounds__(FF_TX * FF_TY)
+    k_flow_fused_batch(const FlowFusedArgs<T> *__restrict__ jobs, const SweepItem *__restrict__ items)
+{
+    __shared__ FlowSmem<T> sm;
+    __shared__ FlowFusedArgs<T> sa;
+    const SweepItem it = items[blockIdx.x];
+    if (threadIdx.x == 0) sa = jobs[it.job];
+    __syncthreads();
+    flow_tile<T>(sa, it.bx, it.by, sm);
+}
+
 // ---------------------------------------------------------------------------
 // Launchers.
 // ---------------------------------------------------------------------------
@@ -317,6 +347,14 @@ cudaError_t launch_flow_fused_impl(const FlowFusedArgs<T> &a, cudaStream_t s)
 {
     dim3 grid((a.nx + FF_TX - 1) / FF_TX, (a.ny + FF_TY - 1) / FF_TY);
     k_flow_fused<T><<<grid, FF_TX * FF_TY, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_flow_fused_batch_impl(const FlowFusedArgs<T> *jobs, const SweepItem *items, int n, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    k_flow_fused_batch<T><<<n, FF_TX * FF_TY, 0, s>>>(jobs, items);
     return cudaGetLastError();
 }
 

@@ -21,4 +21,7 @@
     template <> cudaError_t biot::launch_init<T>(const biot::InitArgs<T> &a, cudaStream_t s)             \
     { return biot::launch_init_impl<T>(a, s); }                                                        \
     template <> cudaError_t biot::launch_flow_fused<T>(const biot::FlowFusedArgs<T> &a, cudaStream_t s) \
-    { return biot::launch_flow_fused_impl<T>(a, s); }
+    { return biot::launch_flow_fused_impl<T>(a, s); } \
+    template <> cudaError_t biot::launch_flow_fused_batch<T>(const biot::FlowFusedArgs<T> *j,            \
+                                                             const biot::SweepItem *it, int n, cudaStream_t s) \
+    { return biot::launch_flow_fused_batch_impl<T>(j, it, n, s); }

@@ -68,25 +68,27 @@ struct alignas(2 * sizeof(T)) V2 {
 };
 template <int KIND, bool LO>
 struct RingLayout {
-    // raw values of a cell: v0..v7 the 8 moments; v8, v9 F~ (FINE) or r_0, r_1
-    // (COARSE); v10, v11 the low parts of m_10, m_01 (FINE, LO) or r_2, r_3
-    // (COARSE); v12 r_4 (COARSE).
+    // raw values of a cell: v0..v7 the 8 moments; FINE: v8, v9 F~, v10, v11 the
+    // low parts of m_10, m_01 (LO); COARSE: v8..v12 r_0..r_4, v13, v14 the low
+    // parts (LO).
     static constexpr int XV = 8;
-    static constexpr int LOV = 10;
-    static constexpr int RV = kind_fine(KIND) ? 12 : 13;  // values fetched per cell
+    static constexpr int LOV = kind_fine(KIND) ? 10 : 13;
+    static constexpr int RV = kind_fine(KIND) ? 12 : (LO ? 15 : 13);  // values fetched per cell
     // In shared memory m_s (v3, read by the neighbours' F_* stencil) has a
     // plane of its own; the other values of a cell, used only by the thread of
-    // its column, are packed into three 4-vectors:
+    // its column, are packed into 4-vectors:
     //   q0 = (m_10, m_01, m_11, m_d), q1 = (m_12, m_21, m_22, v8),
-    //   q2 = (v9, v10, v11, v12 or 0).
+    //   q2 = (v9, v10, v11, v12 or 0), q3 = (v13, v14, 0, 0) (COARSE with LO).
+    static constexpr int NQ = (!kind_fine(KIND) && LO) ? 4 : 3;
 };
 
 template <typename T, int KIND, bool LO, int NT>
 constexpr size_t rows_smem_bytes()
 {
-    // raw: m_s plane + 3 vector planes; post: 4 planes S*_p + 1 vector plane
+    // raw: m_s plane + NQ vector planes; post: 4 planes S*_p + 1 vector plane
     // (m_10, m_01, F_x, F_y) + (LO) a 2-vector plane of low parts; 3 slots each
-    return (size_t)3 * NT * (sizeof(T) + 3 * sizeof(V4<T>) + 4 * sizeof(T) + sizeof(V4<T>) + (LO ? sizeof(V2<T>) : 0));
+    return (size_t)3 * NT *
+           (sizeof(T) + RingLayout<KIND, LO>::NQ * sizeof(V4<T>) + 4 * sizeof(T) + sizeof(V4<T>) + (LO ? sizeof(V2<T>) : 0));
 }
 
 template <typename T>
@@ -108,12 +110,23 @@ struct PostSrc {
 // by the thread of the column or as a whole 4-vector.
 template <typename T, int W, int KIND, bool LO>
 struct Rings {
+    using L = RingLayout<KIND, LO>;
     T *rms;        // [3][W]     m_s
-    V4<T> *raw4;   // [3][3][W]  q0, q1, q2
+    V4<T> *raw4;   // [3][NQ][W]  q0, q1, q2 (, q3)
     T *postS;      // [3][4][W]  S*_0..3
     V4<T> *post4;  // [3][W]     (m_10, m_01, F_x, F_y)
     V2<T> *post2;  // [3][W]     low parts of m_10, m_01 (LO)
-    __device__ __forceinline__ V4<T> &R4(int s, int q, int c) const { return raw4[(s * 3 + q) * W + c]; }
+    __device__ __forceinline__ V4<T> &R4(int s, int q, int c) const { return raw4[(s * L::NQ + q) * W + c]; }
+    // low parts of the first moments of the raw cell (LO)
+    __device__ __forceinline__ V2<T> lo(int s, int c) const
+    {
+        if (kind_fine(KIND)) {
+            const V4<T> q = R4(s, 2, c);
+            return V2<T>{q.y, q.z};
+        }
+        const V4<T> q = R4(s, 3, c);
+        return V2<T>{q.x, q.y};
+    }
     __device__ __forceinline__ T &ms(int s, int c) const { return rms[s * W + c]; }
     __device__ __forceinline__ T &PS(int s, int p, int c) const { return postS[(s * 4 + p) * W + c]; }
     __device__ __forceinline__ V4<T> &P4(int s, int c) const { return post4[s * W + c]; }
@@ -177,17 +190,17 @@ __device__ __forceinline__ void fetch_cell(const SweepArgs<T, TC> &a, int gx, in
     if (kind_fine(KIND)) {
         v[L::XV] = a.Ft[idx];
         v[L::XV + 1] = a.Ft[NP + idx];
-        if (LO) {
-            v[L::LOV] = a.glo[idx];
-            v[L::LOV + 1] = a.glo[NP + idx];
-        } else {
-            v[L::LOV] = T(0);
-            v[L::LOV + 1] = T(0);
-        }
     } else {
         const T *r = a.r + idx;
 #pragma unroll
         for (int k = 0; k < 5; k++) v[L::XV + k] = r[k * NP];
+    }
+    if (LO) {
+        v[L::LOV] = a.zero_init ? T(0) : a.glo[idx];
+        v[L::LOV + 1] = a.zero_init ? T(0) : a.glo[NP + idx];
+    } else if (kind_fine(KIND)) {
+        v[L::LOV] = T(0);
+        v[L::LOV + 1] = T(0);
     }
     if (a.gc) {
         const size_t NPc = NP >> 2;
@@ -210,7 +223,8 @@ __device__ __forceinline__ void store_cell(const Rings<T, W, KIND, LO> &rg, int 
     rg.ms(s, c) = v[3];
     rg.R4(s, 0, c) = V4<T>{v[0], v[1], v[2], v[4]};
     rg.R4(s, 1, c) = V4<T>{v[5], v[6], v[7], v[8]};
-    rg.R4(s, 2, c) = V4<T>{v[9], v[10], v[11], RV > 12 ? v[RV - 1] : T(0)};
+    rg.R4(s, 2, c) = V4<T>{v[9], v[10], v[11], RV > 12 ? v[12] : T(0)};
+    if (RingLayout<KIND, LO>::NQ > 3) rg.R4(s, 3, c) = V4<T>{v[RV > 14 ? 13 : 0], v[RV > 14 ? 14 : 0], T(0), T(0)};
 }
 
 // Collision of the cell in raw slot s, column c (Alg. 2, first six lines, in
@@ -231,8 +245,10 @@ __device__ __forceinline__ void collide_cell(const SweepArgs<T, TC> &a, const Ri
         Fx += q1.w;  // F~
         Fy += q2.x;
     } else {           // minus the residual right-hand side r_0..r_4
-        m0 -= q1.w;
-        m1 -= q2.x;
+        if (!LO) {
+            m0 -= q1.w;
+            m1 -= q2.x;
+        }  // (with LO, r_0 and r_1 come off the low parts below)
         m2 -= q2.y;
         m3 -= q2.z;
         m4 -= q2.w;
@@ -243,7 +259,14 @@ __device__ __forceinline__ void collide_cell(const SweepArgs<T, TC> &a, const Ri
     rg.PS(s, 2, c) = T(0.5) * (m11 + m22);
     rg.PS(s, 3, c) = T(0.5) * (m22 - m11);
     rg.P4(s, c) = V4<T>{m0, m1, Fx, Fy};
-    if (LO) rg.P2(s, c) = V2<T>{q2.y, q2.z};
+    if (LO) {
+        if (kind_fine(KIND)) {
+            rg.P2(s, c) = V2<T>{q2.y, q2.z};
+        } else {
+            const V4<T> q3 = rg.R4(s, 3, c);
+            rg.P2(s, c) = V2<T>{q3.x - q1.w, q3.y - q2.x};
+        }
+    }
 }
 
 // Post-collision population K of a source cell, split relative to the target's
@@ -381,7 +404,14 @@ __device__ __forceinline__ void residual_cell(const SweepArgs<T, TC> &a, const R
     const T mxf = tx + tlx, myf = ty + tly;  // full first moments: beta terms (walls) and the m_12, m_21 residuals
     // odd moments: m**_10 = (A0 + A2 - A3) = small + m_10(x) + dB-terms, etc.
     // (sum_p c_p a_p = (1,0), (0,1), (1/3,0), (0,1/3) for 10, 01, 12, 21)
-    const T r0 = gcur[0] - tx, r1 = gcur[1] - ty;  // = residual rhs r on coarse levels, 0 on the finest
+    // residual rhs r_0, r_1 on coarse levels (0 on the finest): the iterate minus
+    // the collision input, high and low parts differenced separately
+    T r0 = gcur[0] - tx, r1 = gcur[1] - ty;
+    if (LO && !kind_fine(KIND)) {
+        const V2<T> gl = rg.lo(s0, c0);
+        r0 += gl.x - tlx;
+        r1 += gl.y - tly;
+    }
     d[0] = r0 - ((P0.As + P2.As) - P3.As);
     d[1] = r1 - ((P1.As + P2.As) + P3.As);
     d[5] = (gcur[5] - mxf * T(1.0 / 3.0)) - (P2.As - P3.As);
@@ -421,7 +451,7 @@ __device__ __forceinline__ void sweep_strip(const SweepArgs<T, TC> &a, int bx, i
     constexpr int W = NT, RV = L::RV;
     Rings<T, W, KIND, LO> rg;
     rg.raw4 = reinterpret_cast<V4<T> *>(smem_raw);   // vectors first (alignment)
-    rg.post4 = rg.raw4 + 3 * 3 * W;
+    rg.post4 = rg.raw4 + 3 * L::NQ * W;
     rg.post2 = reinterpret_cast<V2<T> *>(rg.post4 + 3 * W);
     rg.rms = reinterpret_cast<T *>(rg.post2 + (LO ? 3 * W : 0));
     rg.postS = rg.rms + 3 * W;
@@ -501,8 +531,8 @@ __device__ __forceinline__ void sweep_strip(const SweepArgs<T, TC> &a, int bx, i
                 for (int k = 2; k < (kind_ghosts(KIND) ? 8 : 5); k++) go[k * NP] = gcur[k] - gam * d[k];
                 // first moments: (hi + lo) - gamma d, renormalised into hi + lo with LO
                 if (LO) {
-                    const V4<T> g2 = rg.R4(sb, 2, t);
-                    const T lo[2] = {g2.y, g2.z};
+                    const V2<T> gl = rg.lo(sb, t);
+                    const T lo[2] = {gl.x, gl.y};
 #pragma unroll
                     for (int k = 0; k < 2; k++) {
                         T hi, lw;
@@ -614,21 +644,21 @@ template <typename T, int TX, int TY, int KIND, bool LO>
 constexpr size_t tile_smem_bytes()
 {
     using S = TileShape<TX, TY>;
-    return (size_t)S::R * S::W * (sizeof(T) + 3 * sizeof(V4<T>) + 4 * sizeof(T) + sizeof(V4<T>) + (LO ? sizeof(V2<T>) : 0)) +
+    return (size_t)S::R * S::W *
+               (sizeof(T) + RingLayout<KIND, LO>::NQ * sizeof(V4<T>) + 4 * sizeof(T) + sizeof(V4<T>) + (LO ? sizeof(V2<T>) : 0)) +
            (size_t)8 * TX * TY * sizeof(T);
 }
 
 template <typename T, typename TC, int TX, int TY, int KIND, bool LO, bool RESTRICT>
-__global__ void __launch_bounds__(TileShape<TX, TY>::NT) k_sweep_tile(const SweepArgs<T, TC> a)
+__device__ __forceinline__ void tile_body(const SweepArgs<T, TC> &a, int bx, int by, unsigned char *smem_raw,
+                                          double (&red)[2][TileShape<TX, TY>::NT / 32])
 {
     using L = RingLayout<KIND, LO>;
     using S = TileShape<TX, TY>;
     constexpr int W = S::W, R = S::R, RV = L::RV, NT = S::NT;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ double red[2][NT / 32];
     Rings<T, W, KIND, LO> rg;  // slot = tile row
     rg.raw4 = reinterpret_cast<V4<T> *>(smem_raw);
-    rg.post4 = rg.raw4 + R * 3 * W;
+    rg.post4 = rg.raw4 + R * L::NQ * W;
     rg.post2 = reinterpret_cast<V2<T> *>(rg.post4 + R * W);
     rg.rms = reinterpret_cast<T *>(rg.post2 + (LO ? R * W : 0));
     rg.postS = rg.rms + R * W;
@@ -641,7 +671,7 @@ __global__ void __launch_bounds__(TileShape<TX, TY>::NT) k_sweep_tile(const Swee
     const int tid = threadIdx.x;
     const bool live = tid < S::CELLS;
     const int c = tid % W, rrow = tid / W;  // ring column and slot
-    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const int x0 = bx * TX, y0 = by * TY;
     const int x = x0 - 2 + c, y = y0 - 2 + rrow;
     const bool xin = perx || (x >= 0 && x < nx);
     const bool yin = pery || (y >= 0 && y < ny);
@@ -675,8 +705,8 @@ __global__ void __launch_bounds__(TileShape<TX, TY>::NT) k_sweep_tile(const Swee
 #pragma unroll
             for (int k = 2; k < (kind_ghosts(KIND) ? 8 : 5); k++) go[k * NP] = gcur[k] - gam * d[k];
             if (LO) {
-                const V4<T> g2 = rg.R4(rrow, 2, c);
-                const T lo[2] = {g2.y, g2.z};
+                const V2<T> gl = rg.lo(rrow, c);
+                const T lo[2] = {gl.x, gl.y};
 #pragma unroll
                 for (int k = 0; k < 2; k++) {
                     T hi, lw;
@@ -742,11 +772,36 @@ __global__ void __launch_bounds__(TileShape<TX, TY>::NT) k_sweep_tile(const Swee
     }
 }
 
+template <typename T, typename TC, int TX, int TY, int KIND, bool LO, bool RESTRICT>
+__global__ void __launch_bounds__(TileShape<TX, TY>::NT) k_sweep_tile(const SweepArgs<T, TC> a)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ double red[2][TileShape<TX, TY>::NT / 32];
+    tile_body<T, TC, TX, TY, KIND, LO, RESTRICT>(a, blockIdx.x, blockIdx.y, smem_raw, red);
+}
+
+// Batched form: CTA b processes tile (items[b].bx, items[b].by) of the sweep
+// jobs[items[b].job] (items[b].ty is unused).
+template <typename T, typename TC, int TX, int TY, int KIND, bool LO, bool RESTRICT>
+__global__ void __launch_bounds__(TileShape<TX, TY>::NT)
+    k_sweep_tile_batch(const SweepArgs<T, TC> *__restrict__ jobs, const SweepItem *__restrict__ items)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ double red[2][TileShape<TX, TY>::NT / 32];
+    __shared__ SweepArgs<T, TC> sa;
+    const SweepItem it = items[blockIdx.x];
+    if (threadIdx.x == 0) sa = jobs[it.job];
+    __syncthreads();
+    tile_body<T, TC, TX, TY, KIND, LO, RESTRICT>(sa, it.bx, it.by, smem_raw, red);
+}
+
 // Tile shape per storage type: FP64 levels use small tiles, so that the few
 // cells of a coarse FP64 level spread over many SMs (FP64 issue rate per SM is
 // the limit there).
 template <typename T> struct TileFor { static constexpr int X = 32, Y = 8; };
 template <> struct TileFor<double> { static constexpr int X = 8, Y = 2; };
+static_assert(TileFor<float>::X == 32 && TileFor<float>::Y == 8 && TileFor<double>::X == 8 && TileFor<double>::Y == 2,
+              "tile shapes shared with the host planner (sweep_tile_shape)");
 
 // Levels of at most this many cells use the tile sweep (default 256^2; the
 // environment variable BIOT_SWEEP_TILE_MAX_CELLS overrides it, 0 disables).
@@ -755,7 +810,7 @@ inline long sweep_tile_max_cells()
     static long v = -1;
     if (v < 0) {
         const char *e = getenv("BIOT_SWEEP_TILE_MAX_CELLS");
-        v = e ? atol(e) : 256L * 256L;
+        v = e ? atol(e) : SWEEP_TILE_CELLS;
         if (v < 0) v = 0;
     }
     return v;
@@ -775,6 +830,23 @@ cudaError_t launch_tile(const SweepArgs<T, TC> &a, cudaStream_t s)
     }
     dim3 grid((a.nx + TX - 1) / TX, (a.ny + TY - 1) / TY);
     kern<<<grid, TileShape<TX, TY>::NT, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <typename T, typename TC, int KIND, bool LO, bool RESTRICT>
+cudaError_t launch_tile_batch(const SweepArgs<T, TC> *jobs, const SweepItem *items, int n, cudaStream_t s)
+{
+    constexpr int TX = TileFor<T>::X, TY = TileFor<T>::Y;
+    constexpr size_t smem = tile_smem_bytes<T, TX, TY, KIND, LO>();
+    auto kern = k_sweep_tile_batch<T, TC, TX, TY, KIND, LO, RESTRICT>;
+    static bool configured = false;
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    if (n <= 0) return cudaSuccess;
+    kern<<<n, TileShape<TX, TY>::NT, smem, s>>>(jobs, items);
     return cudaGetLastError();
 }
 
@@ -832,6 +904,12 @@ auto dispatch_kind(bool coarse, bool lo, bool rs, bool ghosts, A &&...args)
 {
     const int g = ghosts ? 0 : KIND_NOGHOST;
     if (coarse) {
+        if constexpr (sizeof(T) == 4) {
+            if (lo) {
+                if (g) return rs ? F<T, TC, KIND_COARSE | KIND_NOGHOST, true, true>::run(args...) : F<T, TC, KIND_COARSE | KIND_NOGHOST, true, false>::run(args...);
+                return rs ? F<T, TC, KIND_COARSE, true, true>::run(args...) : F<T, TC, KIND_COARSE, true, false>::run(args...);
+            }
+        }
         if (g) return rs ? F<T, TC, KIND_COARSE | KIND_NOGHOST, false, true>::run(args...) : F<T, TC, KIND_COARSE | KIND_NOGHOST, false, false>::run(args...);
         return rs ? F<T, TC, KIND_COARSE, false, true>::run(args...) : F<T, TC, KIND_COARSE, false, false>::run(args...);
     }
@@ -847,8 +925,11 @@ auto dispatch_kind(bool coarse, bool lo, bool rs, bool ghosts, A &&...args)
 
 template <typename T, typename TC, int KIND, bool LO, bool RS>
 struct BatchRun {
-    static cudaError_t run(const SweepArgs<T, TC> *jobs, const SweepItem *items, int n, cudaStream_t s)
-    { return launch_batch_v<T, TC, KIND, LO, RS>(jobs, items, n, s); }
+    static cudaError_t run(bool tile, const SweepArgs<T, TC> *jobs, const SweepItem *items, int n, cudaStream_t s)
+    {
+        return tile ? launch_tile_batch<T, TC, KIND, LO, RS>(jobs, items, n, s)
+                    : launch_batch_v<T, TC, KIND, LO, RS>(jobs, items, n, s);
+    }
 };
 template <typename T, typename TC, int KIND, bool LO, bool RS>
 struct SlotsRun {
@@ -863,7 +944,7 @@ template <typename T, typename TC>
 cudaError_t launch_sweep_batch_impl(int v, const SweepArgs<T, TC> *jobs, const SweepItem *items, int n, cudaStream_t s)
 {
     return dispatch_kind<T, TC, BatchRun>(v & SWEEP_V_COARSE, v & SWEEP_V_LO, v & SWEEP_V_RESTRICT,
-                                         !(v & SWEEP_V_NOGHOST), jobs, items, n, s);
+                                         !(v & SWEEP_V_NOGHOST), (v & SWEEP_V_TILE) != 0, jobs, items, n, s);
 }
 
 template <typename T, typename TC>
@@ -877,8 +958,7 @@ int sweep_slots_impl(int v)
 template <typename T, typename TC>
 cudaError_t launch_sweep_mom_impl(const SweepArgs<T, TC> &a, cudaStream_t s)
 {
-    return dispatch_kind<T, TC, RowsRun>(a.Ft == nullptr, a.Ft != nullptr && a.glo != nullptr,
-                                        a.mode == SWEEP_RESTRICT, a.ghosts != 0, a, s);
+    return dispatch_kind<T, TC, RowsRun>(a.Ft == nullptr, a.glo != nullptr, a.mode == SWEEP_RESTRICT, a.ghosts != 0, a, s);
 }
 
 }  // namespace biot
