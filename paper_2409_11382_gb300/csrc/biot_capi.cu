@@ -73,16 +73,23 @@ int fail(int code, const std::string &msg)
 
 constexpr int MAX_LEVELS = 16;
 
-// FP32 coarse levels carry their first moments as double-float too (the
-// environment variable BIOT_COARSE_LO=0 turns this off, for comparisons).
-bool coarse_lo()
+// Double-float first moments on the FP32 coarse levels.  A V-cycle starts each
+// coarse level from zero, so their low parts carry nothing from one V-cycle to
+// the next and can be switched per solve.  They matter where the coarse
+// corrections are displacement-sized: in the solve at t = 0, which starts from a
+// zero iterate (a cold start); a warm-started step's corrections are of the
+// size of the change over one time step.  Default: the cold-start solve only;
+// BIOT_COARSE_LO=1 takes them in every solve, BIOT_COARSE_LO=0 never (both for
+// comparisons).
+enum { COARSE_LO_OFF = 0, COARSE_LO_COLD = 1, COARSE_LO_ALL = 2 };
+int coarse_lo_mode()
 {
     static int v = -1;
     if (v < 0) {
         const char *e = getenv("BIOT_COARSE_LO");
-        v = (e && e[0] == '0') ? 0 : 1;
+        v = !e ? COARSE_LO_COLD : (e[0] == '0' ? COARSE_LO_OFF : (e[0] == '1' ? COARSE_LO_ALL : COARSE_LO_COLD));
     }
-    return v != 0;
+    return v;
 }
 
 struct Level {
@@ -127,6 +134,7 @@ struct biot_ctx {
     cudaStream_t stream = nullptr, own_stream = nullptr;
     long nstep = 0;
     bool solved = false, initialized = false, pending_res = false;
+    bool cold_solve = false;  // the current elastic solve starts from a zero iterate (t = 0)
     bool se_stale = true;   // SE must be recomputed from D1, D2 before k_force
     bool ft_fresh = false;  // the last flow step computed F~ of the next elastic solve
     // statistics
@@ -241,6 +249,16 @@ int set_profiles(biot_ctx *h, int side, const double *eta, const double *p)
 
 // ---- kernel sequencing --------------------------------------------------------
 
+// Whether the sweeps of level l use the double-float first moments: always on
+// the finest FP32 level, on the coarse FP32 levels as coarse_lo_mode() says.
+bool level_lo(const biot_ctx *h, int l, bool cold)
+{
+    if (!h->lv[l].glo[0]) return false;
+    if (l == h->L - 1) return true;
+    const int m = coarse_lo_mode();
+    return m == COARSE_LO_ALL || (m == COARSE_LO_COLD && cold);
+}
+
 template <typename T, typename TC>
 int sweep_typed(biot_ctx *h, int l, int mode, bool zero_init, bool prolong, bool want_res)
 {
@@ -251,8 +269,9 @@ int sweep_typed(biot_ctx *h, int l, int mode, bool zero_init, bool prolong, bool
     a.ny = Lv.ny;
     a.g = static_cast<const T *>(Lv.g[Lv.cur]);
     a.gout = (mode == SWEEP_SMOOTH) ? static_cast<T *>(Lv.g[1 - Lv.cur]) : nullptr;
-    a.glo = static_cast<const T *>(Lv.glo[Lv.cur]);
-    a.glo_out = (mode == SWEEP_SMOOTH) ? static_cast<T *>(Lv.glo[1 - Lv.cur]) : nullptr;
+    const bool lo = level_lo(h, l, h->cold_solve);
+    a.glo = lo ? static_cast<const T *>(Lv.glo[Lv.cur]) : nullptr;
+    a.glo_out = (lo && mode == SWEEP_SMOOTH) ? static_cast<T *>(Lv.glo[1 - Lv.cur]) : nullptr;
     a.r = fine ? nullptr : static_cast<const T *>(Lv.r);
     a.Ft = fine ? static_cast<const T *>(h->Ft) : nullptr;
     a.gc = prolong ? static_cast<const TC *>(h->lv[l - 1].g[h->lv[l - 1].cur]) : nullptr;
@@ -421,6 +440,7 @@ int elastic_solve(biot_ctx *h)
     rc = h->fp32 ? force_typed<float>(h) : force_typed<double>(h);
     if (rc) return rc;
     h->lv[h->L - 1].hist_valid = 0;
+    h->cold_solve = h->nstep == 0;
     const bool fixed = h->P.ne_fixed > 0;
     if (!fixed && !h->rec) {
         cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
@@ -829,7 +849,7 @@ int biot_create(const biot_params *p, const biot_side sides[4], biot_handle *out
         const size_t esz = Lv.fp64 ? sizeof(double) : sizeof(float);
         TRY_RC(dev_alloc(h, &Lv.g[0], 8 * Lv.np * esz));
         TRY_RC(dev_alloc(h, &Lv.g[1], 8 * Lv.np * esz));
-        if (!Lv.fp64 && (l == h->L - 1 || coarse_lo())) {  // double-float displacement moments
+        if (!Lv.fp64 && (l == h->L - 1 || coarse_lo_mode() != COARSE_LO_OFF)) {  // double-float displacement moments
             TRY_RC(dev_alloc(h, &Lv.glo[0], 2 * Lv.np * esz));
             TRY_RC(dev_alloc(h, &Lv.glo[1], 2 * Lv.np * esz));
         }
@@ -1136,7 +1156,7 @@ int level_variant(const biot_ctx *h, int l, int mode)
     // in a batch the launches of a phase are large: strips except for the
     // smallest levels and FP64 levels
     const bool tile = (long)h->lv[l].nx * h->lv[l].ny <= BATCH_TILE_CELLS || h->lv[l].fp64;
-    return (fine ? 0 : SWEEP_V_COARSE) | (h->lv[l].glo[0] ? SWEEP_V_LO : 0) |
+    return (fine ? 0 : SWEEP_V_COARSE) | (level_lo(h, l, false) ? SWEEP_V_LO : 0) |
            (mode == SWEEP_RESTRICT ? SWEEP_V_RESTRICT : 0) | (h->P.ne_fixed > 0 ? SWEEP_V_NOGHOST : 0) |
            (tile ? SWEEP_V_TILE : 0);
 }
@@ -1345,6 +1365,16 @@ int batch_capture(biot_batch_s *b, int par)
         if (!rc && frec.size() != (size_t)i + 1) rc = fail(BIOT_ERR_CUDA, "batched schedule: flow step not recorded");
         nl += h->launches - l0[i];
         if (!rc && rec[i].size() != b->nops[i]) rc = fail(BIOT_ERR_CUDA, "batched schedule does not match the recorded sweeps");
+    }
+    // every recorded sweep must be of the kind its planned launch instantiates
+    for (size_t k = 0; k < b->launches.size() && !rc; k++) {
+        const BatchLaunch &L = b->launches[k];
+        for (int j = 0; j < L.njobs && !rc; j++) {
+            const BatchSlot &sl = b->slots[L.tkind][L.job_off + j];
+            const SweepJob &r = rec[sl.inst][sl.op];
+            if (r.tkind != L.tkind || r.variant != (L.variant & ~SWEEP_V_TILE))
+                rc = fail(BIOT_ERR_CUDA, "batched schedule: a recorded sweep differs from its planned kind");
+        }
     }
     // flow steps of all instances, then their history copies
     if (!rc && !b->flow_items[0].empty()) {
@@ -1586,7 +1616,7 @@ size_t estimate_bytes(const biot_params *p, const biot_side *sides)
         const bool fp64 = !fp32 || (l == 0 && p->mg_levels > 1) || (p->precision == BIOT_FP32_COARSE64 && l < p->mg_levels - 1);
         const size_t esz = fp64 ? 8 : 4;
         b += 2 * 8 * n * esz;
-        if (!fp64 && (l == p->mg_levels - 1 || coarse_lo())) b += 2 * 2 * n * esz;
+        if (!fp64 && (l == p->mg_levels - 1 || coarse_lo_mode() != COARSE_LO_OFF)) b += 2 * 2 * n * esz;
         if (l < p->mg_levels - 1) b += 8 * n * esz;
         for (int s = 0; s < 4; s++)
             if (sides && sides[s].eta_type == BIOT_DIRICHLET) b += 3 * ((s == BIOT_BOTTOM || s == BIOT_TOP) ? nx : ny) * esz;
