@@ -44,9 +44,13 @@ struct SweepArgs {
     int ghosts;                  // 1: load and store the ghost moments 12, 21, 22 (tolerance mode)
     // the same coefficients, evaluated once on the host in the storage type:
     T k_fs;   // coef_fstar * dD/dm_s = -(alpha^2 r / 2) * 3 / (2 (3 lm + 1))
-    T k_ws;   // 1 - om_s
-    T k_wd;   // 1 - om_d
-    T k_22;   // -1 / (12 lm + 4)   (eq. moments:collision:22)
+    // halves of the even post-collision combinations S*_p of Tab. moments:inverse
+    // as linear forms of the moments (eq. moments:collision:22 for m_22):
+    //   S*_0/2 = k_hs m_s + k_hd m_d,   S*_1/2 = k_hs m_s - k_hd m_d,
+    //   S*_2/2 = k_hd m_11 + k_h22 m_s, S*_3/2 = k_h22 m_s - k_hd m_11
+    T k_hs;   // (1 - om_s) / 4 + 1 / (2 (12 lm + 4))
+    T k_hd;   // (1 - om_d) / 4
+    T k_h22;  // -1 / (4 (12 lm + 4))
     T k_gam;  // gamma
 };
 

@@ -294,9 +294,12 @@ int sweep_typed(biot_ctx *h, int l, int mode, bool zero_init, bool prolong, bool
     a.rows = Lv.rows[mode];
     a.ghosts = h->P.ne_fixed > 0 ? 0 : 1;
     a.k_fs = T(a.coef_fstar * (-1.5 / (3.0 * a.lm + 1.0)));
-    a.k_ws = T(1.0 - a.om_s);
-    a.k_wd = T(1.0 - a.om_d);
-    a.k_22 = T(-1.0 / (12.0 * a.lm + 4.0));
+    {
+        const double k22 = -1.0 / (12.0 * a.lm + 4.0);  // m_22 relaxation (eq. moments:collision:22)
+        a.k_hs = T(0.25 * (1.0 - a.om_s) - 0.5 * k22);
+        a.k_hd = T(0.25 * (1.0 - a.om_d));
+        a.k_h22 = T(0.25 * k22);
+    }
     a.k_gam = T(a.gamma);
 
     if (h->rec) {

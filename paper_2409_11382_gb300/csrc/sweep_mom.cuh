@@ -41,9 +41,13 @@ namespace biot {
 // applies the wall rules, and relaxes or restricts.  The two outer columns on
 // each side are halo: the outermost only supply m_s, the next ones are also
 // collided; the NT-4 inner columns are written.  Strips overlap by 4 columns.
-// The rings are planes of 4-vectors (one 128-bit shared-memory access per
-// group of four values of a cell; consecutive threads read consecutive
-// vectors, so the accesses are free of bank conflicts).
+// The rings are planes (consecutive threads access consecutive elements, so
+// the accesses are free of bank conflicts).  Values read by neighbouring
+// threads have scalar planes: m_s in the raw ring, and in the post-collision
+// ring the small part G_K of every outgoing population and the high parts of
+// the first moments; values read only by the thread of the column are packed
+// into 4-vectors (one 128-bit access each).  A pull thus reads one G_K and the
+// one or two first moments its pair needs.
 // FINE: finest level (explicit force F~, boundary data; double-float first
 // moments when LO).  COARSE: residual right-hand side r, homogeneous walls.
 // ---------------------------------------------------------------------------
@@ -68,88 +72,99 @@ struct alignas(2 * sizeof(T)) V2 {
 };
 template <int KIND, bool LO>
 struct RingLayout {
-    // raw values of a cell: v0..v7 the 8 moments; FINE: v8, v9 F~, v10, v11 the
-    // low parts of m_10, m_01 (LO); COARSE: v8..v12 r_0..r_4, v13, v14 the low
-    // parts (LO).
+    // values fetched per cell (fetch_cell): v0..v7 the 8 moments (the ghost
+    // moments 0 when elided), then F~ (FINE, 2) or r_0..r_4 (COARSE, 5), then
+    // the low parts of m_10, m_01 (LO)
     static constexpr int XV = 8;
-    static constexpr int LOV = kind_fine(KIND) ? 10 : 13;
-    static constexpr int RV = kind_fine(KIND) ? 12 : (LO ? 15 : 13);  // values fetched per cell
-    // In shared memory m_s (v3, read by the neighbours' F_* stencil) has a
-    // plane of its own; the other values of a cell, used only by the thread of
-    // its column, are packed into 4-vectors:
-    //   q0 = (m_10, m_01, m_11, m_d), q1 = (m_12, m_21, m_22, v8),
-    //   q2 = (v9, v10, v11, v12 or 0), q3 = (v13, v14, 0, 0) (COARSE with LO).
-    static constexpr int NQ = (!kind_fine(KIND) && LO) ? 4 : 3;
+    static constexpr int NXV = kind_fine(KIND) ? 2 : 5;
+    static constexpr int LOV = XV + NXV;
+    static constexpr int RV = LOV + (LO ? 2 : 0);
+    // Raw ring: m_s on a scalar plane, q0 = (m_10, m_01, m_11, m_d) on a 4-vector
+    // plane, and the cell's "extra" values e[0..NE) -- the ghost moments (when
+    // kept), F~ or r, the low parts, in this order -- packed into 4-vector
+    // planes, a remainder of two values into a 2-vector plane and of one value
+    // into a scalar plane.
+    static constexpr int EX = kind_ghosts(KIND) ? 3 : 0;  // first F~ / r value
+    static constexpr int EL = EX + NXV;                    // first low part
+    static constexpr int NE = EL + (LO ? 2 : 0);
+    static constexpr int NE4 = (NE % 4 == 3) ? NE / 4 + 1 : NE / 4;
+    static constexpr int NV4 = 1 + NE4;  // 4-vector planes per slot, q0 included
+    static constexpr bool E2 = NE % 4 == 2;
+    static constexpr bool E1 = NE % 4 == 1;
+    // Post-collision ring: scalar planes G_0..G_7 (small parts of the outgoing
+    // populations) and the high parts of the collision-input m_10, m_01.
+    static constexpr int NPOST = 10;
+    template <typename T>
+    static constexpr size_t slot_bytes(int W)
+    {
+        return (size_t)W * (4 * NV4 + (E2 ? 2 : 0) + (E1 ? 1 : 0) + 1 + NPOST) * sizeof(T);
+    }
 };
 
 template <typename T, int KIND, bool LO, int NT>
 constexpr size_t rows_smem_bytes()
 {
-    // raw: m_s plane + NQ vector planes; post: 4 planes S*_p + 1 vector plane
-    // (m_10, m_01, F_x, F_y) + (LO) a 2-vector plane of low parts; 3 slots each
-    return (size_t)3 * NT *
-           (sizeof(T) + RingLayout<KIND, LO>::NQ * sizeof(V4<T>) + 4 * sizeof(T) + sizeof(V4<T>) + (LO ? sizeof(V2<T>) : 0));
+    return 3 * RingLayout<KIND, LO>::template slot_bytes<T>(NT);  // 3 slots
 }
 
 template <typename T>
 struct PVal {
-    T sig, bx, by;  // value = sig + bx * m_10(x) + by * m_01(x)
+    // value = g + h + bx * m_10(x) + by * m_01(x): g stress-sized, h the small
+    // target-relative part (kept apart so that a pair's sum and difference round
+    // the stress-sized parts once)
+    T g, h, bx, by;
 };
 
-// Post-collision data a pull reads from its source cell.
-template <typename T>
-struct PostSrc {
-    T S;           // even part S*_p of the pulled population's pair
-    T mx, my;      // first moments (high parts with LO)
-    T Fx, Fy;      // force of the collision
-    T lx, ly;      // low parts of the first moments (LO), else 0
-};
-
-// Shared-memory rings of W columns and 3 slots.  Scalar planes are read by
-// neighbouring threads (consecutive threads, consecutive words); vector planes
-// by the thread of the column or as a whole 4-vector.
+// Shared-memory rings of W columns (slots: rows of the strip's window, or of
+// the tile).
 template <typename T, int W, int KIND, bool LO>
 struct Rings {
     using L = RingLayout<KIND, LO>;
-    T *rms;        // [3][W]     m_s
-    V4<T> *raw4;   // [3][NQ][W]  q0, q1, q2 (, q3)
-    T *postS;      // [3][4][W]  S*_0..3
-    V4<T> *post4;  // [3][W]     (m_10, m_01, F_x, F_y)
-    V2<T> *post2;  // [3][W]     low parts of m_10, m_01 (LO)
-    __device__ __forceinline__ V4<T> &R4(int s, int q, int c) const { return raw4[(s * L::NQ + q) * W + c]; }
-    // low parts of the first moments of the raw cell (LO)
-    __device__ __forceinline__ V2<T> lo(int s, int c) const
+    V4<T> *q;   // [slot][NV4][W]  q0, packed extra values
+    V2<T> *q2;  // [slot][W]       extra values, 2-vector remainder (E2)
+    T *qs;      // [slot][W]       extra value, scalar remainder (E1)
+    T *rms;     // [slot][W]       m_s
+    T *post;    // [slot][NPOST][W] G_0..G_7, m_10, m_01 (high parts)
+    __device__ __forceinline__ void carve(unsigned char *p, int slots)
     {
-        if (kind_fine(KIND)) {
-            const V4<T> q = R4(s, 2, c);
-            return V2<T>{q.y, q.z};
-        }
-        const V4<T> q = R4(s, 3, c);
-        return V2<T>{q.x, q.y};
+        q = reinterpret_cast<V4<T> *>(p);  // vectors first (alignment)
+        q2 = reinterpret_cast<V2<T> *>(q + slots * L::NV4 * W);
+        qs = reinterpret_cast<T *>(q2 + (L::E2 ? slots * W : 0));
+        rms = qs + (L::E1 ? slots * W : 0);
+        post = rms + slots * W;
     }
+    __device__ __forceinline__ V4<T> &Q(int s, int j, int c) const { return q[(s * L::NV4 + j) * W + c]; }
     __device__ __forceinline__ T &ms(int s, int c) const { return rms[s * W + c]; }
-    __device__ __forceinline__ T &PS(int s, int p, int c) const { return postS[(s * 4 + p) * W + c]; }
-    __device__ __forceinline__ V4<T> &P4(int s, int c) const { return post4[s * W + c]; }
-    __device__ __forceinline__ V2<T> &P2(int s, int c) const { return post2[s * W + c]; }
-    template <int PAIR>
-    __device__ __forceinline__ PostSrc<T> src(int s, int c) const
+    __device__ __forceinline__ T &G(int s, int k, int c) const { return post[(s * L::NPOST + k) * W + c]; }
+    __device__ __forceinline__ T &MX(int s, int c) const { return post[(s * L::NPOST + 8) * W + c]; }
+    __device__ __forceinline__ T &MY(int s, int c) const { return post[(s * L::NPOST + 9) * W + c]; }
+    __device__ __forceinline__ void put_extras(int s, int c, const T (&e)[L::NE]) const
     {
-        PostSrc<T> o;
-        o.S = PS(s, PAIR, c);
-        const V4<T> q = P4(s, c);
-        o.mx = q.x;
-        o.my = q.y;
-        o.Fx = q.z;
-        o.Fy = q.w;
-        if (LO) {
-            const V2<T> l = P2(s, c);
-            o.lx = l.x;
-            o.ly = l.y;
-        } else {
-            o.lx = T(0);
-            o.ly = T(0);
+#pragma unroll
+        for (int j = 0; j < L::NE4; j++) {
+            const int b = 4 * j;
+            Q(s, 1 + j, c) = V4<T>{e[b], e[b + 1], e[b + 2 < L::NE ? b + 2 : b], b + 3 < L::NE ? e[b + 3] : T(0)};
         }
-        return o;
+        if constexpr (L::E2) q2[s * W + c] = V2<T>{e[L::NE - 2], e[L::NE - 1]};
+        if constexpr (L::E1) qs[s * W + c] = e[L::NE - 1];
+    }
+    __device__ __forceinline__ void get_extras(int s, int c, T (&e)[L::NE]) const
+    {
+#pragma unroll
+        for (int j = 0; j < L::NE4; j++) {
+            const V4<T> v = Q(s, 1 + j, c);
+            const int b = 4 * j;
+            e[b] = v.x;
+            e[b + 1] = v.y;
+            if (b + 2 < L::NE) e[b + 2 < L::NE ? b + 2 : b] = v.z;
+            if (b + 3 < L::NE) e[b + 3 < L::NE ? b + 3 : b] = v.w;
+        }
+        if constexpr (L::E2) {
+            const V2<T> v = q2[s * W + c];
+            e[L::NE - 2] = v.x;
+            e[L::NE - 1] = v.y;
+        }
+        if constexpr (L::E1) e[L::NE - 1] = qs[s * W + c];
     }
 };
 
@@ -195,17 +210,14 @@ __device__ __forceinline__ void fetch_cell(const SweepArgs<T, TC> &a, int gx, in
 #pragma unroll
         for (int k = 0; k < 5; k++) v[L::XV + k] = r[k * NP];
     }
-    if (LO) {
+    if constexpr (LO) {
         v[L::LOV] = a.zero_init ? T(0) : a.glo[idx];
         v[L::LOV + 1] = a.zero_init ? T(0) : a.glo[NP + idx];
-    } else if (kind_fine(KIND)) {
-        v[L::LOV] = T(0);
-        v[L::LOV + 1] = T(0);
     }
     if (a.gc) {
         const size_t NPc = NP >> 2;
         const size_t cidx = (size_t)(gy >> 1) * (a.nx >> 1) + (gx >> 1);
-        if (LO) {
+        if constexpr (LO) {
             v[L::LOV] += (T)a.gc[cidx];
             v[L::LOV + 1] += (T)a.gc[NPc + cidx];
         } else {
@@ -220,80 +232,161 @@ __device__ __forceinline__ void fetch_cell(const SweepArgs<T, TC> &a, int gx, in
 template <typename T, int W, int KIND, bool LO, int RV>
 __device__ __forceinline__ void store_cell(const Rings<T, W, KIND, LO> &rg, int s, int c, const T (&v)[RV])
 {
+    using L = RingLayout<KIND, LO>;
     rg.ms(s, c) = v[3];
-    rg.R4(s, 0, c) = V4<T>{v[0], v[1], v[2], v[4]};
-    rg.R4(s, 1, c) = V4<T>{v[5], v[6], v[7], v[8]};
-    rg.R4(s, 2, c) = V4<T>{v[9], v[10], v[11], RV > 12 ? v[12] : T(0)};
-    if (RingLayout<KIND, LO>::NQ > 3) rg.R4(s, 3, c) = V4<T>{v[RV > 14 ? 13 : 0], v[RV > 14 ? 14 : 0], T(0), T(0)};
+    rg.Q(s, 0, c) = V4<T>{v[0], v[1], v[2], v[4]};
+    T e[L::NE];
+#pragma unroll
+    for (int i = 0; i < L::EX; i++) e[i] = v[5 + i];
+#pragma unroll
+    for (int i = 0; i < L::NXV; i++) e[L::EX + i] = v[L::XV + i];
+#pragma unroll
+    for (int i = 0; i < L::NE - L::EL; i++) e[L::EL + i] = v[L::LOV + i];
+    rg.put_extras(s, c, e);
+}
+
+// Product rounded on its own, never fused into a neighbouring add: the pulls
+// of wall cells and of interior cells are separate inlined copies of the same
+// code, and an x-independent problem must give identical columns.
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+
+// a_p . (x, y) / 2 for the odd coefficient vectors a_p of Tab. moments:inverse,
+// zero terms omitted.
+template <typename T, int P>
+__device__ __forceinline__ T half_pa_dot(T x, T y)
+{
+    static_assert(pa_x(0) == 2.0 / 3.0 && pa_y(0) == 0.0 && pa_x(1) == 0.0 && pa_y(1) == 2.0 / 3.0 &&
+                      pa_x(2) == 1.0 / 6.0 && pa_y(2) == 1.0 / 6.0 && pa_x(3) == -1.0 / 6.0 && pa_y(3) == 1.0 / 6.0,
+                  "coefficients a_p");
+    if constexpr (P == 0) return T(1.0 / 3.0) * x;
+    if constexpr (P == 1) return T(1.0 / 3.0) * y;
+    if constexpr (P == 2) return T(1.0 / 12.0) * (x + y);
+    return T(1.0 / 12.0) * (y - x);
 }
 
 // Collision of the cell in raw slot s, column c (Alg. 2, first six lines, in
 // moment space): even moments relaxed (Tab. moments, eq. moments:collision:22),
 // odd part kept as first moments + force F = F~ + (alpha^2 r/2) grad^c D(g).
+// Writes, per outgoing direction K of pair p and sign e, the part of
+//   g*_K = 1/2 (S*_p + e A*_p),  A*_p = a_p . m + b_p . F  (Tab. moments:inverse)
+// that does not contain the high parts of the first moments,
+//   G_K = 1/2 (S*_p + e (a_p . m_lo + b_p . F)),
+// and the high parts m_10, m_01 themselves: a pull adds e/2 a_p . (m_hi(source)
+// - m_hi(target)), a difference of nearby values (exact), so that no
+// displacement-sized value is ever rounded into a population.
 template <typename T, typename TC, int KIND, bool LO, int W>
 __device__ __forceinline__ void collide_cell(const SweepArgs<T, TC> &a, const Rings<T, W, KIND, LO> &rg, int sm, int s,
                                              int sp, int c)
 {
-    const V4<T> q0 = rg.R4(s, 0, c), q1 = rg.R4(s, 1, c), q2 = rg.R4(s, 2, c);
+    using L = RingLayout<KIND, LO>;
+    const V4<T> q0 = rg.Q(s, 0, c);
+    T e[L::NE];
+    rg.get_extras(s, c, e);
     T m0 = q0.x, m1 = q0.y, m2 = q0.z, m3 = rg.ms(s, c), m4 = q0.w;
     const T dE = rg.ms(s, c + 1), dW = rg.ms(s, c - 1), dN = rg.ms(sp, c), dS = rg.ms(sm, c);
     const T dNE = rg.ms(sp, c + 1), dNW = rg.ms(sp, c - 1), dSE = rg.ms(sm, c + 1), dSW = rg.ms(sm, c - 1);
     const T cf = a.k_fs;  // alpha^2 r/2 * dD/dm_s
     T Fx = cf * ((dE - dW) * T(1.0 / 3.0) + ((dNE + dSE) - (dNW + dSW)) * T(1.0 / 12.0));
     T Fy = cf * ((dN - dS) * T(1.0 / 3.0) + ((dNE + dNW) - (dSE + dSW)) * T(1.0 / 12.0));
-    if (kind_fine(KIND)) {
-        Fx += q1.w;  // F~
-        Fy += q2.x;
-    } else {           // minus the residual right-hand side r_0..r_4
-        if (!LO) {
-            m0 -= q1.w;
-            m1 -= q2.x;
-        }  // (with LO, r_0 and r_1 come off the low parts below)
-        m2 -= q2.y;
-        m3 -= q2.z;
-        m4 -= q2.w;
-    }
-    const T ms = a.k_ws * m3, md = a.k_wd * m4, m11 = a.k_wd * m2, m22 = a.k_22 * m3;
-    rg.PS(s, 0, c) = T(0.5) * (ms + md) - m22;
-    rg.PS(s, 1, c) = T(0.5) * (ms - md) - m22;
-    rg.PS(s, 2, c) = T(0.5) * (m11 + m22);
-    rg.PS(s, 3, c) = T(0.5) * (m22 - m11);
-    rg.P4(s, c) = V4<T>{m0, m1, Fx, Fy};
-    if (LO) {
-        if (kind_fine(KIND)) {
-            rg.P2(s, c) = V2<T>{q2.y, q2.z};
-        } else {
-            const V4<T> q3 = rg.R4(s, 3, c);
-            rg.P2(s, c) = V2<T>{q3.x - q1.w, q3.y - q2.x};
+    T lx = T(0), ly = T(0);  // low parts of the collision-input first moments (LO)
+    if constexpr (kind_fine(KIND)) {
+        Fx += e[L::EX];  // F~
+        Fy += e[L::EX + 1];
+        if constexpr (LO) {
+            lx = e[L::EL];
+            ly = e[L::EL + 1];
         }
+    } else {  // minus the residual right-hand side r_0..r_4
+        if constexpr (LO) {  // r_0, r_1 come off the low parts
+            lx = e[L::EL] - e[L::EX];
+            ly = e[L::EL + 1] - e[L::EX + 1];
+        } else {
+            m0 -= e[L::EX];
+            m1 -= e[L::EX + 1];
+        }
+        m2 -= e[L::EX + 2];
+        m3 -= e[L::EX + 3];
+        m4 -= e[L::EX + 4];
     }
+    // halves of the even combinations S*_p, one multiply and one fused multiply-add each
+    const T hd = a.k_hd * m4, h22 = a.k_h22 * m3;
+    const T hS0 = a.k_hs * m3 + hd, hS1 = a.k_hs * m3 - hd;
+    const T hS2 = a.k_hd * m2 + h22, hS3 = h22 - a.k_hd * m2;
+    // G_K = S*_p/2 + e (a_p . m_lo + b_p . F)/2, b_p = (5/6, 0), (0, 5/6), (1/12, 1/12), (-1/12, 1/12)
+    static_assert(pb_x(0) == 5.0 / 6.0 && pb_y(0) == 0.0 && pb_x(1) == 0.0 && pb_y(1) == 5.0 / 6.0 &&
+                      pb_x(2) == 1.0 / 12.0 && pb_y(2) == 1.0 / 12.0 && pb_x(3) == -1.0 / 12.0 && pb_y(3) == 1.0 / 12.0,
+                  "coefficients b_p");
+    static_assert(pair_first(0) == 0 && pair_second(0) == 2 && pair_first(1) == 1 && pair_second(1) == 3 &&
+                      pair_first(2) == 4 && pair_second(2) == 6 && pair_first(3) == 5 && pair_second(3) == 7,
+                  "pairs");
+    const T Fp = Fx + Fy, Fm = Fy - Fx;
+    T G0, G1, G2, G3, G4, G5, G6, G7;
+    if constexpr (LO) {  // odd parts without the high moments first (small), then one add each
+        const T A0 = T(5.0 / 12.0) * Fx + half_pa_dot<T, 0>(lx, ly), A1 = T(5.0 / 12.0) * Fy + half_pa_dot<T, 1>(lx, ly);
+        const T A2 = T(1.0 / 24.0) * Fp + half_pa_dot<T, 2>(lx, ly), A3 = T(1.0 / 24.0) * Fm + half_pa_dot<T, 3>(lx, ly);
+        G0 = hS0 + A0;
+        G2 = hS0 - A0;
+        G1 = hS1 + A1;
+        G3 = hS1 - A1;
+        G4 = hS2 + A2;
+        G6 = hS2 - A2;
+        G5 = hS3 + A3;
+        G7 = hS3 - A3;
+    } else {  // one fused multiply-add each
+        G0 = hS0 + T(5.0 / 12.0) * Fx;
+        G2 = hS0 - T(5.0 / 12.0) * Fx;
+        G1 = hS1 + T(5.0 / 12.0) * Fy;
+        G3 = hS1 - T(5.0 / 12.0) * Fy;
+        G4 = hS2 + T(1.0 / 24.0) * Fp;
+        G6 = hS2 - T(1.0 / 24.0) * Fp;
+        G5 = hS3 + T(1.0 / 24.0) * Fm;
+        G7 = hS3 - T(1.0 / 24.0) * Fm;
+    }
+    rg.G(s, 0, c) = G0;
+    rg.G(s, 1, c) = G1;
+    rg.G(s, 2, c) = G2;
+    rg.G(s, 3, c) = G3;
+    rg.G(s, 4, c) = G4;
+    rg.G(s, 5, c) = G5;
+    rg.G(s, 6, c) = G6;
+    rg.G(s, 7, c) = G7;
+    rg.MX(s, c) = m0;
+    rg.MY(s, c) = m1;
 }
 
-// Post-collision population K of a source cell, split relative to the target's
-// collision-input first moments (tx, ty high, tlx, tly low parts):
-//   g*_K = 1/2 (S*_p + e A*_p),  A*_p = a_p . m + b_p . F  (Tab. moments:inverse)
-template <typename T, bool LO, int K>
-__device__ __forceinline__ PVal<T> post_pop(const PostSrc<T> &q, T tx, T ty, T tlx, T tly)
-{
-    constexpr int p = pair_of(K);
-    constexpr T e = T(sign_of(K));
-    T dmx = q.mx - tx, dmy = q.my - ty;
-    if (LO) {
-        dmx += q.lx - tlx;
-        dmy += q.ly - tly;
-    }
-    const T odd = (T(pa_x(p)) * dmx + T(pa_y(p)) * dmy) + (T(pb_x(p)) * q.Fx + T(pb_y(p)) * q.Fy);
-    PVal<T> v;
-    v.sig = T(0.5) * (q.S + e * odd);
-    v.bx = e * T(0.5 * pa_x(p));
-    v.by = e * T(0.5 * pa_y(p));
-    return v;
-}
-
+// Post-collision population K of the source cell in slot s, column c, split
+// relative to the target's collision-input first moments (tx, ty high, tlx,
+// tly low parts): sig = G_K + e/2 a_p . ((m_hi - t_hi) - t_lo).
 template <typename T, bool LO, int W, int KIND, int K>
 __device__ __forceinline__ PVal<T> post_at(const Rings<T, W, KIND, LO> &rg, int s, int c, T tx, T ty, T tlx, T tly)
 {
-    return post_pop<T, LO, K>(rg.template src<pair_of(K)>(s, c), tx, ty, tlx, tly);
+    constexpr int p = pair_of(K);
+    constexpr bool POS = sign_of(K) > 0;
+    T dx = T(0), dy = T(0);
+    if constexpr (pa_x(p) != 0.0) {
+        dx = rg.MX(s, c) - tx;
+        if constexpr (LO) dx -= tlx;
+    }
+    if constexpr (pa_y(p) != 0.0) {
+        dy = rg.MY(s, c) - ty;
+        if constexpr (LO) dy -= tly;
+    }
+    const T g = rg.G(s, K, c);
+    T h;
+    if constexpr (p == 0) h = mul_rn(T(1.0 / 3.0), dx);
+    else if constexpr (p == 1) h = mul_rn(T(1.0 / 3.0), dy);
+    else if constexpr (p == 2) h = mul_rn(T(1.0 / 12.0), dx + dy);
+    else h = mul_rn(T(1.0 / 12.0), dy - dx);
+    static_assert(pa_x(0) == 2.0 / 3.0 && pa_y(1) == 2.0 / 3.0 && pa_x(2) == 1.0 / 6.0 && pa_y(2) == 1.0 / 6.0 &&
+                      pa_x(3) == -1.0 / 6.0 && pa_y(3) == 1.0 / 6.0,
+                  "h = a_p . (dx, dy) / 2");
+    PVal<T> v;
+    v.g = g;
+    v.h = POS ? h : -h;
+    v.bx = T(sign_of(K) * 0.5 * pa_x(p));
+    v.by = T(sign_of(K) * 0.5 * pa_y(p));
+    return v;
 }
 
 // Population of direction K arriving at cell (x, y) (ring column c0); sl[0..2]
@@ -330,21 +423,23 @@ __device__ __forceinline__ PVal<T> pull(const SweepArgs<T, TC> &a, const Rings<T
     const int n = horiz ? a.nx : a.ny;
     PVal<T> v;
     if (type == BC_NEUMANN) {  // eq. BC:traction
-        v.sig = -o.sig;
+        v.g = -o.g;
+        v.h = -o.h;
         v.bx = -o.bx;
         v.by = -o.by;
-        if (kind_fine(KIND) && a.prof[side]) v.sig += T(a.c0h * traction_term(a.prof[side], side, n, x, y, cx, cy));
+        if (kind_fine(KIND) && a.prof[side]) v.g += T(a.c0h * traction_term(a.prof[side], side, n, x, y, cx, cy));
         return v;
     }
     // BC_DIRICHLET: eq. BC:elasticity, history = previous call's outgoing population
     if (a.hist_valid) {
-        v.sig = a.H[side][3 * (horiz ? x : y) + hslot(side, kout)];
+        v.g = a.H[side][3 * (horiz ? x : y) + hslot(side, kout)];
+        v.h = T(0);
         v.bx = T(0);
         v.by = T(0);
     } else {
         v = o;
     }
-    if (kind_fine(KIND) && a.prof[side]) v.sig += T(dirichlet_term(a.prof[side], side, n, x, y, cx, cy));
+    if (kind_fine(KIND) && a.prof[side]) v.g += T(dirichlet_term(a.prof[side], side, n, x, y, cx, cy));
     return v;
 }
 
@@ -365,8 +460,8 @@ __device__ __forceinline__ PairOut<T> pull_pair(const SweepArgs<T, TC> &a, const
     const PVal<T> u = pull<T, TC, KIND, LO, W, pair_first(P), WALL>(a, rg, x, y, sl, c0, tx, ty, tlx, tly, perx, pery);
     const PVal<T> v = pull<T, TC, KIND, LO, W, pair_second(P), WALL>(a, rg, x, y, sl, c0, tx, ty, tlx, tly, perx, pery);
     PairOut<T> o;
-    o.Ss = u.sig + v.sig;
-    o.As = u.sig - v.sig;
+    o.Ss = (u.g + v.g) + (u.h + v.h);
+    o.As = (u.g - v.g) + (u.h - v.h);
     o.bsx = u.bx + v.bx;
     o.bsy = u.by + v.by;
     o.dbx = (u.bx - v.bx) - T(pa_x(P));
@@ -379,25 +474,70 @@ __device__ __forceinline__ void store_history(const SweepArgs<T, TC> &a, const R
                                               int s0, int c0, T tx, T ty, T tlx, T tly)
 {
     const PVal<T> o = post_at<T, LO, W, KIND, K>(rg, s0, c0, tx, ty, tlx, tly);
-    a.H[side][3 * pos + hslot(side, K)] = o.sig + (o.bx * (tx + tlx) + o.by * (ty + tly));
+    a.H[side][3 * pos + hslot(side, K)] = (o.g + o.h) + (o.bx * (tx + tlx) + o.by * (ty + tly));
+}
+
+// The streamed cell's own values, from its raw ring slot: the iterate's moments
+// g, the low parts of m_10, m_01 (LO), and the collision-input first moments as
+// the collision formed them (tx, ty high, tlx, tly low parts).
+template <typename T>
+struct OwnCell {
+    T g[8];
+    T lo[2];
+    T tx, ty, tlx, tly;
+};
+
+template <typename T, int W, int KIND, bool LO>
+__device__ __forceinline__ OwnCell<T> own_cell(const Rings<T, W, KIND, LO> &rg, int s, int c)
+{
+    using L = RingLayout<KIND, LO>;
+    const V4<T> q0 = rg.Q(s, 0, c);
+    T e[L::NE];
+    rg.get_extras(s, c, e);
+    OwnCell<T> o;
+    o.g[0] = q0.x;
+    o.g[1] = q0.y;
+    o.g[2] = q0.z;
+    o.g[3] = rg.ms(s, c);
+    o.g[4] = q0.w;
+#pragma unroll
+    for (int i = 0; i < 3; i++) o.g[5 + i] = T(0);
+    if constexpr (kind_ghosts(KIND)) {
+        o.g[5] = e[0];
+        o.g[6] = e[1];
+        o.g[7] = e[2];
+    }
+    o.lo[0] = o.lo[1] = T(0);
+    if constexpr (LO) {
+        o.lo[0] = e[L::EL];
+        o.lo[1] = e[L::EL + 1];
+    }
+    o.tx = o.g[0];
+    o.ty = o.g[1];
+    o.tlx = o.lo[0];
+    o.tly = o.lo[1];
+    if constexpr (!kind_fine(KIND)) {  // the same operations as collide_cell
+        if constexpr (LO) {
+            o.tlx = o.lo[0] - e[L::EX];
+            o.tly = o.lo[1] - e[L::EX + 1];
+        } else {
+            o.tx = o.g[0] - e[L::EX];
+            o.ty = o.g[1] - e[L::EX + 1];
+        }
+    }
+    return o;
 }
 
 // Residual d = m - m** of the cell (x, y) (small parts only, see the file
-// comment); gcur: the iterate's moments.
+// comment); own: the cell's own values.
 template <typename T, typename TC, int KIND, bool LO, int W, bool WALL>
 __device__ __forceinline__ void residual_cell(const SweepArgs<T, TC> &a, const Rings<T, W, KIND, LO> &rg, int x, int y,
-                                              const int (&sl)[3], int c0, bool perx, bool pery, const T (&gcur)[8],
+                                              const int (&sl)[3], int c0, bool perx, bool pery, const OwnCell<T> &own,
                                               T (&d)[8])
 {
     const int s0 = sl[1];
-    const V4<T> own = rg.P4(s0, c0);
-    const T tx = own.x, ty = own.y;
-    T tlx = T(0), tly = T(0);
-    if (LO) {
-        const V2<T> l = rg.P2(s0, c0);
-        tlx = l.x;
-        tly = l.y;
-    }
+    const T(&gcur)[8] = own.g;
+    const T tx = own.tx, ty = own.ty, tlx = own.tlx, tly = own.tly;
 #define BIOT_PAIR(P) pull_pair<T, TC, KIND, LO, W, P, WALL>(a, rg, x, y, sl, c0, tx, ty, tlx, tly, perx, pery)
     const PairOut<T> P0 = BIOT_PAIR(0), P1 = BIOT_PAIR(1), P2 = BIOT_PAIR(2), P3 = BIOT_PAIR(3);
 #undef BIOT_PAIR
@@ -407,10 +547,9 @@ __device__ __forceinline__ void residual_cell(const SweepArgs<T, TC> &a, const R
     // residual rhs r_0, r_1 on coarse levels (0 on the finest): the iterate minus
     // the collision input, high and low parts differenced separately
     T r0 = gcur[0] - tx, r1 = gcur[1] - ty;
-    if (LO && !kind_fine(KIND)) {
-        const V2<T> gl = rg.lo(s0, c0);
-        r0 += gl.x - tlx;
-        r1 += gl.y - tly;
+    if constexpr (LO && !kind_fine(KIND)) {
+        r0 += own.lo[0] - tlx;
+        r1 += own.lo[1] - tly;
     }
     d[0] = r0 - ((P0.As + P2.As) - P3.As);
     d[1] = r1 - ((P1.As + P2.As) + P3.As);
@@ -450,11 +589,7 @@ __device__ __forceinline__ void sweep_strip(const SweepArgs<T, TC> &a, int bx, i
     using L = RingLayout<KIND, LO>;
     constexpr int W = NT, RV = L::RV;
     Rings<T, W, KIND, LO> rg;
-    rg.raw4 = reinterpret_cast<V4<T> *>(smem_raw);   // vectors first (alignment)
-    rg.post4 = rg.raw4 + 3 * L::NQ * W;
-    rg.post2 = reinterpret_cast<V2<T> *>(rg.post4 + 3 * W);
-    rg.rms = reinterpret_cast<T *>(rg.post2 + (LO ? 3 * W : 0));
-    rg.postS = rg.rms + 3 * W;
+    rg.carve(smem_raw, 3);
 
     const int nx = a.nx, ny = a.ny;
     const size_t NP = (size_t)nx * ny;
@@ -519,24 +654,22 @@ __device__ __forceinline__ void sweep_strip(const SweepArgs<T, TC> &a, int bx, i
 #pragma unroll
         for (int k = 0; k < 8; k++) d[k] = T(0);
         if (writes) {
-            const V4<T> g0 = rg.R4(sb, 0, t), g1 = rg.R4(sb, 1, t);
-            const T gcur[8] = {g0.x, g0.y, g0.z, rg.ms(sb, t), g0.w, g1.x, g1.y, g1.z};
+            const OwnCell<T> own = own_cell<T, W, KIND, LO>(rg, sb, t);
+            const T(&gcur)[8] = own.g;
             const bool wall = wall_col || (!pery && (y == 0 || y == ny - 1));
-            if (wall) residual_cell<T, TC, KIND, LO, W, true>(a, rg, x, y, sl, t, perx, pery, gcur, d);
-            else residual_cell<T, TC, KIND, LO, W, false>(a, rg, x, y, sl, t, perx, pery, gcur, d);
+            if (wall) residual_cell<T, TC, KIND, LO, W, true>(a, rg, x, y, sl, t, perx, pery, own, d);
+            else residual_cell<T, TC, KIND, LO, W, false>(a, rg, x, y, sl, t, perx, pery, own, d);
             if (!RESTRICT) {
                 const size_t idx = (size_t)y * nx + x;
                 T *go = a.gout + idx;
 #pragma unroll
                 for (int k = 2; k < (kind_ghosts(KIND) ? 8 : 5); k++) go[k * NP] = gcur[k] - gam * d[k];
                 // first moments: (hi + lo) - gamma d, renormalised into hi + lo with LO
-                if (LO) {
-                    const V2<T> gl = rg.lo(sb, t);
-                    const T lo[2] = {gl.x, gl.y};
+                if constexpr (LO) {
 #pragma unroll
                     for (int k = 0; k < 2; k++) {
                         T hi, lw;
-                        two_sum(gcur[k], lo[k] - gam * d[k], hi, lw);
+                        two_sum(gcur[k], own.lo[k] - gam * d[k], hi, lw);
                         go[k * NP] = hi;
                         a.glo_out[k * NP + idx] = lw;
                     }
@@ -644,9 +777,7 @@ template <typename T, int TX, int TY, int KIND, bool LO>
 constexpr size_t tile_smem_bytes()
 {
     using S = TileShape<TX, TY>;
-    return (size_t)S::R * S::W *
-               (sizeof(T) + RingLayout<KIND, LO>::NQ * sizeof(V4<T>) + 4 * sizeof(T) + sizeof(V4<T>) + (LO ? sizeof(V2<T>) : 0)) +
-           (size_t)8 * TX * TY * sizeof(T);
+    return (size_t)S::R * RingLayout<KIND, LO>::template slot_bytes<T>(S::W) + (size_t)8 * TX * TY * sizeof(T);
 }
 
 template <typename T, typename TC, int TX, int TY, int KIND, bool LO, bool RESTRICT>
@@ -657,12 +788,8 @@ __device__ __forceinline__ void tile_body(const SweepArgs<T, TC> &a, int bx, int
     using S = TileShape<TX, TY>;
     constexpr int W = S::W, R = S::R, RV = L::RV, NT = S::NT;
     Rings<T, W, KIND, LO> rg;  // slot = tile row
-    rg.raw4 = reinterpret_cast<V4<T> *>(smem_raw);
-    rg.post4 = rg.raw4 + R * L::NQ * W;
-    rg.post2 = reinterpret_cast<V2<T> *>(rg.post4 + R * W);
-    rg.rms = reinterpret_cast<T *>(rg.post2 + (LO ? R * W : 0));
-    rg.postS = rg.rms + R * W;
-    T *dres = rg.postS + R * 4 * W;  // [8][TY][TX] residuals (restriction)
+    rg.carve(smem_raw, R);
+    T *dres = reinterpret_cast<T *>(smem_raw + R * L::template slot_bytes<T>(W));  // [8][TY][TX] residuals (restriction)
 
     const int nx = a.nx, ny = a.ny;
     const size_t NP = (size_t)nx * ny;
@@ -693,24 +820,22 @@ __device__ __forceinline__ void tile_body(const SweepArgs<T, TC> &a, int bx, int
     for (int k = 0; k < 8; k++) d[k] = T(0);
     if (writes) {
         const int sl[3] = {rrow - 1, rrow, rrow + 1};
-        const V4<T> g0 = rg.R4(rrow, 0, c), g1 = rg.R4(rrow, 1, c);
-        const T gcur[8] = {g0.x, g0.y, g0.z, rg.ms(rrow, c), g0.w, g1.x, g1.y, g1.z};
+        const OwnCell<T> own = own_cell<T, W, KIND, LO>(rg, rrow, c);
+        const T(&gcur)[8] = own.g;
         const bool wall = (!perx && (x == 0 || x == nx - 1)) || (!pery && (y == 0 || y == ny - 1));
-        if (wall) residual_cell<T, TC, KIND, LO, W, true>(a, rg, x, y, sl, c, perx, pery, gcur, d);
-        else residual_cell<T, TC, KIND, LO, W, false>(a, rg, x, y, sl, c, perx, pery, gcur, d);
+        if (wall) residual_cell<T, TC, KIND, LO, W, true>(a, rg, x, y, sl, c, perx, pery, own, d);
+        else residual_cell<T, TC, KIND, LO, W, false>(a, rg, x, y, sl, c, perx, pery, own, d);
         if (!RESTRICT) {
             const size_t idx = (size_t)y * nx + x;
             T *go = a.gout + idx;
             const T gam = a.k_gam;
 #pragma unroll
             for (int k = 2; k < (kind_ghosts(KIND) ? 8 : 5); k++) go[k * NP] = gcur[k] - gam * d[k];
-            if (LO) {
-                const V2<T> gl = rg.lo(rrow, c);
-                const T lo[2] = {gl.x, gl.y};
+            if constexpr (LO) {
 #pragma unroll
                 for (int k = 0; k < 2; k++) {
                     T hi, lw;
-                    two_sum(gcur[k], lo[k] - gam * d[k], hi, lw);
+                    two_sum(gcur[k], own.lo[k] - gam * d[k], hi, lw);
                     go[k * NP] = hi;
                     a.glo_out[k * NP + idx] = lw;
                 }
