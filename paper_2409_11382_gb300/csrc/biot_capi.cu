@@ -1120,7 +1120,18 @@ extern "C" int biot_read_u_noalloc(biot_handle h, double *eta, double *t_out)
 // ============================================================================
 namespace {
 
-constexpr long BATCH_TILE_CELLS = 64L * 64L;
+// In a batch, levels of at most this many cells run as tiles (default 64^2;
+// the environment variable BIOT_BATCH_TILE_MAX_CELLS overrides it).
+long batch_tile_max_cells()
+{
+    static long v = -1;
+    if (v < 0) {
+        const char *e = getenv("BIOT_BATCH_TILE_MAX_CELLS");
+        v = e ? atol(e) : 64L * 64L;
+        if (v < 0) v = 0;
+    }
+    return v;
+}
 
 // One sweep of the static schedule of an instance.
 struct PlanOp {
@@ -1158,7 +1169,7 @@ int level_variant(const biot_ctx *h, int l, int mode)
     const bool fine = l == h->L - 1;
     // in a batch the launches of a phase are large: strips except for the
     // smallest levels and FP64 levels
-    const bool tile = (long)h->lv[l].nx * h->lv[l].ny <= BATCH_TILE_CELLS || h->lv[l].fp64;
+    const bool tile = (long)h->lv[l].nx * h->lv[l].ny <= batch_tile_max_cells() || h->lv[l].fp64;
     return (fine ? 0 : SWEEP_V_COARSE) | (level_lo(h, l, false) ? SWEEP_V_LO : 0) |
            (mode == SWEEP_RESTRICT ? SWEEP_V_RESTRICT : 0) | (h->P.ne_fixed > 0 ? SWEEP_V_NOGHOST : 0) |
            (tile ? SWEEP_V_TILE : 0);

@@ -746,8 +746,11 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 6 : 1) k_sweep_mom(const 
 // Batched form: CTA b processes work item items[b], a strip of the sweep
 // described by jobs[items[b].job] (the jobs of one launch may belong to
 // different instances and different multigrid levels of one storage kind).
+// (7 resident CTAs per SM with FP32 storage, as the single-instance kernel reaches
+// on its own: the job arguments live in shared memory here, and without the bound
+// the compiler keeps more of them in registers at the cost of one CTA per SM)
 template <typename T, typename TC, int NT, int KIND, bool LO, bool RESTRICT>
-__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 6 : 1)
+__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 7 : 1)
     k_sweep_batch(const SweepArgs<T, TC> *__restrict__ jobs, const SweepItem *__restrict__ items)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
