@@ -173,3 +173,32 @@ def served_requests(count: int = 200, seed: int = 11382, mean_in_flight: float =
                     levels=int(np.log2(n)) - 2, ne_fixed=3, precision=FP32)
         out.append((t, p, top_load_sides(n, uniform_load(n)), T))
     return out
+
+
+def loading_2d(n: int = 128, precision=FP64, ne_fixed=3, K=4):
+    """The dimensional two-dimensional loading problem of §4.3: domain (0,100)^2,
+    Young's modulus E = 1e5 and Poisson ratio nu = 0.9 in plane stress, so
+    lambda = E nu / (1 - nu^2) = 9e6/19 and mu = E / (2 (1 + nu)) = 5e5/19;
+    c0 = 1e-6, kappa = 1e-9, alpha = 1, centered coupling, no body force or
+    source, zero initial data.  Top: p = 0 and traction
+    (0, -1e4 (1 - cos((x + 25) pi / 50))); bottom: fixed displacement, no flow;
+    left and right periodic.  Final time 2e6 in N_T = n^2 steps (the paper's
+    n = 128, N_T = 16384), MG(3,4) on log2(n) levels as in the paper's own
+    experiments.  Returns (params, sides, steps)."""
+    lx = 100.0
+    p = _params(n, lam=9e6 / 19.0, mu=5e5 / 19.0, alpha=1.0, c0=1e-6, kappa=1e-9,
+                dt=2e6 / (n * n), levels=int(np.log2(n)), K=K, ne_fixed=ne_fixed,
+                precision=precision, lx=lx)
+    x = np.arange(2 * n + 1) * (lx / n) / 2.0
+    load = 1e4 * (1.0 - np.cos((x + 25.0) * np.pi / 50.0))
+    return p, top_load_sides(n, load, PERIODIC), n * n
+
+
+def alg1(params: dict, ne: int) -> dict:
+    """Alg. 1 -- pseudo-time stepping without multigrid -- as a parameter set:
+    one level, no under-relaxation (gamma = 1, so each sweep is one
+    ELASTIC_STEP), ne pseudo-time steps per time step (one cycle of ne/2 + ne/2
+    sweeps; ne even)."""
+    if ne < 2 or ne % 2:
+        raise ValueError("ne must be even and >= 2")
+    return dict(params, levels=1, gamma=1.0, K=ne // 2, ne_fixed=1)

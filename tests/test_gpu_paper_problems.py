@@ -6,7 +6,12 @@
   diverges at alpha = 0.6, the implicit one (r = 1) at alpha = 0.8, the
   centered one (r = 1/2) converges at alpha = 1;
 * Terzaghi's problem converges at first order to its series solution
-  (dt = dx^2/4, MG(3,4), periodic sides).
+  (dt = dx^2/4, MG(3,4), periodic sides);
+* Alg. 1 (pseudo-time stepping without multigrid, N_E = 1.5 N_x) matches the
+  oracle and converges at almost second order (§4.1);
+* the dimensional two-dimensional loading problem (§4.3) matches the oracle
+  over its whole time span at 32^2 cells and, at the paper's size (128^2
+  cells, 16384 steps), behaves as the paper describes.
 The exact solutions are the paper's; the time-dependent sources are uploaded
 with biot_set_sources every step, as the oracle's tests do."""
 import numpy as np
@@ -16,6 +21,7 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 from paper_2409_11382_gb300 import biot, workloads as W  # noqa: E402
+from paper_checks import check_loading_2d_statements, loading_2d_snapshots  # noqa: E402
 
 PI = np.pi
 
@@ -29,8 +35,10 @@ def _device():
     torch.cuda.set_device(0)
 
 
-def manufactured_errors(n, alpha, r, ne=3, K=2, tf=1.0):
+def manufactured_errors(n, alpha, r, ne=3, K=2, tf=1.0, alg1_ne=None):
     p, sides = W.manufactured_params(n, alpha, r, ne_fixed=ne, K=K)
+    if alg1_ne is not None:
+        p = W.alg1(p, alg1_ne)
     lam, mu, kap = p["lam"], p["mu"], p["kappa"]
     x = (np.arange(n) + 0.5) / n
     X1, X2 = np.meshgrid(x, x)
@@ -116,3 +124,61 @@ def test_terzaghi_first_order_on_gpu():
     e = np.array([terzaghi_error(n) for n in (16, 32, 64)])
     assert e[-1] < 0.02
     assert np.all((e[:-1] / e[1:] > 1.7) & (e[:-1] / e[1:] < 3.0))
+
+
+# ---------------------------------------------------------------------------
+# Alg. 1 without multigrid (§4.1)
+# ---------------------------------------------------------------------------
+
+def rel(a, b):
+    return float(np.abs(a - b).max() / np.abs(b).max())
+
+
+@pytest.mark.parametrize("precision, tol", [(W.FP64, 1e-12), (W.FP32, 1e-5)])
+def test_alg1_matches_oracle(precision, tol):
+    """Alg. 1 with N_E = 1.5 N_x = 48 pseudo steps on the 33x33 Terzaghi case
+    (one level, gamma = 1): the GPU path against the FP64 oracle after 10 steps."""
+    from oracle import oracle as O
+    p, sides, _ = W.terzaghi_33(precision=precision)
+    p = W.alg1(p, 48)
+    with biot.Solver(p, sides) as g:
+        g.step(10)
+        eta, _ = g.read_u()
+        pp, _ = g.read_p()
+    ref = O.Oracle(W.alg1(W.terzaghi_33()[0], 48), sides)
+    ref.step(10)
+    eta_o, _ = ref.read_u()
+    p_o, _ = ref.read_p()
+    ref.close()
+    assert rel(eta, eta_o) < tol and rel(pp, p_o) < tol
+
+
+def test_alg1_almost_second_order_on_gpu():
+    errs = [manufactured_errors(n, 0.5, 0.5, tf=0.25, alg1_ne=int(1.5 * n)) for n in (16, 32, 64)]
+    ep = np.array([e[0] for e in errs])
+    ee = np.array([e[1] for e in errs])
+    assert np.all(ep[:-1] / ep[1:] > 3.0) and np.all(ee[:-1] / ee[1:] > 3.0)
+
+
+# ---------------------------------------------------------------------------
+# Two-dimensional loading problem (§4.3)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("precision, tol", [(W.FP64, 1e-12), (W.FP32, 1e-5)])
+def test_loading_2d_matches_oracle(precision, tol):
+    """32^2 cells, t_f = 2e6 in 1024 steps (the lattice permeability of the
+    paper's 128^2 run): eta and p at t = 2e4, 2e5, 2e6 against the oracle."""
+    from oracle import oracle as O
+    n = 32
+    got = loading_2d_snapshots(lambda p, s: biot.Solver(p, s), n, precision)
+    ref = loading_2d_snapshots(O.Oracle, n)
+    for (t, e, p), (to, eo, po) in zip(got, ref):
+        assert t == pytest.approx(to)
+        assert rel(e, eo) < tol and rel(p, po) < tol
+
+
+def test_loading_2d_paper_size_statements():
+    """The paper's run: 128^2 cells, 16384 steps to t_f = 2e6, MG(3,4), on the
+    FP32 path; the solution behaves as §4.3 describes."""
+    n = 128
+    check_loading_2d_statements(loading_2d_snapshots(lambda p, s: biot.Solver(p, s), n, W.FP32), n)

@@ -8,7 +8,12 @@
   diverges at alpha = 0.6, implicit (r = 1) at alpha = 0.8, centered (r = 1/2)
   converges at alpha = 1;
 * roller (mirror) side walls give the periodic result for a problem that does
-  not depend on x (reading R12).
+  not depend on x (reading R12);
+* Alg. 1 (pseudo-time stepping without multigrid) with N_E = 1.5 N_x pseudo
+  steps converges at almost second order on the manufactured problem (§4.1),
+  and far too few pseudo steps leave the elasticity error dominant;
+* the dimensional two-dimensional loading problem (§4.3): parameters as
+  printed, and the behaviour the paper describes for its solution.
 """
 import json
 import os
@@ -18,6 +23,7 @@ import pytest
 
 from oracle import oracle as O
 from paper_2409_11382_gb300 import workloads as W
+from paper_checks import check_loading_2d_statements, loading_2d_snapshots
 
 GOLD = os.path.join(os.path.dirname(__file__), "golden")
 PI = np.pi
@@ -79,8 +85,10 @@ def test_terzaghi_first_order():
     assert np.all((eS[:-1] / eS[1:] > 1.6) & (eS[:-1] / eS[1:] < 3.0))
 
 
-def manufactured_errors(n, alpha, r, ne=3, K=2, tf=1.0):
+def manufactured_errors(n, alpha, r, ne=3, K=2, tf=1.0, alg1_ne=None):
     p, sides = W.manufactured_params(n, alpha, r, ne_fixed=ne, K=K)
+    if alg1_ne is not None:
+        p = W.alg1(p, alg1_ne)
     lam, mu, kap = p["lam"], p["mu"], p["kappa"]
     o = O.Oracle(p, sides)
     x = (np.arange(n) + 0.5) / n
@@ -150,3 +158,48 @@ def test_roller_sides_equal_periodic_sides_for_x_uniform_problem():
         out.append((eta, pp, o.read_stress()))
     for a, b in zip(out[0], out[1]):
         np.testing.assert_allclose(a, b, rtol=0, atol=1e-13 * max(1.0, np.abs(b).max()))
+
+
+def test_alg1_almost_second_order_and_pseudo_step_starvation():
+    """§4.1, Alg. 1 without multigrid: N_E = 1.5 N_x pseudo steps give almost
+    second-order convergence (alpha = 0.5, centered coupling); with N_E = 2 at
+    N_x = 32 (far below the 0.015 N_x^2 transition) the unconverged elasticity
+    dominates the error."""
+    g = json.load(open(os.path.join(GOLD, "paper_parameters.json")))["alg1_no_multigrid"]
+    errs = [manufactured_errors(n, 0.5, 0.5, tf=0.25, alg1_ne=int(g["NE_over_Nx"] * n)) for n in (8, 16, 32)]
+    ep = np.array([e[0] for e in errs])
+    ee = np.array([e[1] for e in errs])
+    assert np.all(ep[:-1] / ep[1:] > 3.0) and np.all(ee[:-1] / ee[1:] > 3.0)
+    starved = manufactured_errors(32, 0.5, 0.5, tf=0.25, alg1_ne=2)
+    assert starved[1] > 4 * ee[-1]
+
+
+def test_alg1_is_the_smoother_at_gamma_one_on_one_level():
+    """Alg. 1 as a parameter set: one level, gamma = 1, N_E sweeps in one cycle."""
+    p, _ = W.manufactured_params(16, 0.5, 0.5)
+    q = W.alg1(p, 24)
+    assert (q["levels"], q["gamma"], q["K"], q["ne_fixed"]) == (1, 1.0, 12, 1)
+    with pytest.raises(ValueError):
+        W.alg1(p, 23)
+
+
+def test_loading_2d_parameters_as_printed():
+    g = json.load(open(os.path.join(GOLD, "paper_parameters.json")))["loading_2d"]
+    p, sides, steps = W.loading_2d(g["Nx"])
+    E, nu = g["E"], g["nu"]
+    assert np.isclose(p["lam"], E * nu / (1 - nu ** 2)) and np.isclose(p["lam"], 9e6 / 19)
+    assert np.isclose(p["mu"], E / (2 * (1 + nu))) and np.isclose(p["mu"], 5e5 / 19)
+    assert (p["c0"], p["kappa"], p["alpha"], p["r"]) == (g["c0"], g["kappa"], g["alpha"], g["r"])
+    assert p["lx"] == g["domain"][1] and steps == g["NT"] and np.isclose(p["dt"] * steps, g["tf"])
+    assert (p["ne_fixed"], p["K"]) == (3, 4)
+    top = sides[W.TOP]["eta_profile"]
+    x = np.arange(2 * g["Nx"] + 1) * (p["lx"] / g["Nx"]) / 2
+    assert np.allclose(top[0], 0.0)
+    assert np.isclose(top[1][np.argmin(abs(x - 25))], -2 * g["load_amplitude"])  # largest load at x1 = 25
+    assert np.isclose(top[1][np.argmin(abs(x - 75))], 0.0, atol=1e-9)            # no load at x1 = 75
+    assert sides[W.LEFT]["eta_type"] == W.PERIODIC and sides[W.BOTTOM]["eta_type"] == W.DIRICHLET
+
+
+def test_loading_2d_statements_oracle():
+    n = 32
+    check_loading_2d_statements(loading_2d_snapshots(O.Oracle, n), n)
