@@ -9,6 +9,7 @@ input (the problem is fully defined by its parameters); all state stays
 resident in HBM and is larger than L2.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+    python bench.py --precision fp64     # the plain FP64 path on the same problem
 
 Under torchrun every rank runs its own independent instance (instances do not
 exchange data, so the run is weak-scaled replicas); rank 0 prints one JSON line.
@@ -34,6 +35,7 @@ sys.path.insert(0, ROOT)
 METRIC = "MLUPS & time per Biot step at stated error vs FP64 oracle"
 WORKLOAD = "terzaghi_4097x4097_fp32"
 PROFILE = os.path.join(ROOT, "profiles", "sweep_fp32_terzaghi_4097.md")
+PROFILE64 = os.path.join(ROOT, "profiles", "sweep_fp64_terzaghi_4097.md")
 KERNEL_SRC = os.path.join(ROOT, "paper_2409_11382_gb300", "csrc", "sweep_mom.cuh")
 
 
@@ -56,17 +58,42 @@ def kernel_sha():
     return hashlib.sha256(open(KERNEL_SRC, "rb").read()).hexdigest()[:16]
 
 
-def profiled_traffic_per_cell():
-    """DRAM bytes per cell of one finest-level sweep from the committed ncu summary,
-    or None if the kernel source changed since the counters were taken."""
-    if not os.path.exists(PROFILE):
+def profiled_per_cell(key, path=PROFILE):
+    """A per-cell figure of one finest-level sweep (``key: value``) from a
+    committed ncu summary, or None if the kernel source changed since the
+    counters were taken."""
+    if not os.path.exists(path):
         return None
-    text = open(PROFILE).read()
-    m = re.search(r"traffic_bytes_per_cell:\s*([0-9.]+)", text)
+    text = open(path).read()
+    m = re.search(key + r":\s*([0-9.]+)", text)
     s = re.search(r"kernel_source_sha:\s*([0-9a-f]+)", text)
     if not m or not s or s.group(1) != kernel_sha():
         return None
     return float(m.group(1))
+
+
+def profiled_traffic_per_cell(path=PROFILE):
+    return profiled_per_cell("traffic_bytes_per_cell", path)
+
+
+def measured_fp64_peak(torch):
+    """FP64 arithmetic peak of this GPU, measured: the best of 3 timed FP64 GEMMs
+    of 4096^3 (cuBLAS through torch), in FLOP/s."""
+    n = 4096
+    a = torch.randn(n, n, dtype=torch.float64, device="cuda")
+    b = torch.randn(n, n, dtype=torch.float64, device="cuda")
+    torch.matmul(a, b)
+    best = None
+    for _ in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        torch.matmul(a, b)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        best = ms if best is None else min(best, ms)
+    del a, b
+    return 2.0 * n ** 3 / (best / 1e3)
 
 
 class ClockSampler:
@@ -135,11 +162,11 @@ def oracle_sample_step(keep=None):
     return dt, 512 * params["ny"]
 
 
-def accuracy_vs_oracle(oracle_fields, n):
+def accuracy_vs_oracle(oracle_fields, n, precision=None):
     """L-infinity and L2 relative errors of eta and p of the GPU path after one step
     of the benchmark problem against the oracle's strip (x-independent problem)."""
     from paper_2409_11382_gb300 import biot, workloads as W
-    params, sides, _ = W.terzaghi_4097(n=n)
+    params, sides, _ = W.terzaghi_4097(n=n, precision=W.FP32 if precision is None else precision)
     with biot.Solver(params, sides) as s:
         s.step(1)
         eta, _ = s.read_u()
@@ -223,12 +250,14 @@ def run_ours(args):
         B.build()
     if world > 1:
         torch.distributed.barrier()
-    params, sides, _ = W.terzaghi_4097(n=args.n)
+    fp64 = args.precision == "fp64"
+    params, sides, _ = W.terzaghi_4097(n=args.n, precision=W.FP64 if fp64 else W.FP32)
     nx, ny = params["nx"], params["ny"]
     cells = nx * ny
     stream = torch.cuda.current_stream()
     solver = biot.Solver(params, sides, stream=stream.cuda_stream)
-    tuned = solver.autotune() if not args.no_tune else None  # launch shapes (results unchanged)
+    # launch shapes (results unchanged); the FP64 path keeps the default shapes
+    tuned = solver.autotune() if not (args.no_tune or fp64) else None
 
     for _ in range(args.warmup):
         solver.step(1)
@@ -296,31 +325,50 @@ def run_ours(args):
     if not args.no_cpu_baseline and args.n == 4096:
         fields = {}
         cpu_base = cpu_baseline_entry(fields)
-        accuracy = accuracy_vs_oracle(fields, args.n)
-    # finest-level smoothing sweep, FP32, fixed V-cycle count: the 5 moments that carry
-    # state (the ghost moments 12, 21, 22 are elided) + 2 low parts in and out, F~ in;
-    # the prolongated correction (5 coarse moments per 4 cells) once per 2K sweeps
+        accuracy = accuracy_vs_oracle(fields, args.n, W.FP64 if fp64 else W.FP32)
+    # finest-level smoothing sweep, fixed V-cycle count: the 5 moments that carry
+    # state (the ghost moments 12, 21, 22 are elided) in and out, F~ in, with FP32
+    # storage also the 2 low parts of the first moments in and out; the
+    # prolongated correction (5 coarse moments per 4 cells) once per 2K sweeps
     nm = 5 if params["ne_fixed"] > 0 else 8
-    bytes_per_cell = ((nm + 2) * 2 + 2) * 4.0 + nm * 4.0 / 4.0 / (2 * params["K"])
+    esz = 8.0 if fp64 else 4.0
+    nlo = 0 if fp64 else 2
+    bytes_per_cell = ((nm + nlo) * 2 + 2) * esz + nm * esz / 4.0 / (2 * params["K"])
     avg_sweep_ms = sweep_ms / max(sweep_n, 1)
     achieved = bytes_per_cell * cells / (avg_sweep_ms / 1e3) / 1e9
-    traffic_pc = profiled_traffic_per_cell()
+    traffic_pc = profiled_traffic_per_cell(PROFILE64 if fp64 else PROFILE)
+    hbm_roof = {"kernel": f"k_sweep_mom<{'double,double' if fp64 else 'float,float'}> finest level, smoothing",
+                "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "peak_kind": f"{peak_kind} copy bandwidth (burst)",
+                "bytes_per_cell": bytes_per_cell, "launches": sweep_n, "avg_launch_ms": avg_sweep_ms,
+                "traffic": None if traffic_pc is None else traffic_pc * cells}
+    roofline, roofline_other = hbm_roof, None
+    if fp64:
+        # FP64 arithmetic: FP64 instructions per cell from the committed ncu counters
+        # against the measured FP64 rate (FP64 GEMM FLOP/s / 2 = FP64 instructions/s,
+        # one FMA being two FLOP); this path is built without fused multiply-adds
+        inst_pc = profiled_per_cell("fp64_inst_per_cell", PROFILE64)
+        peak64 = measured_fp64_peak(torch) / 2.0 / 1e9
+        ach64 = None if inst_pc is None else inst_pc * cells / (avg_sweep_ms / 1e3) / 1e9
+        roofline = {"kernel": hbm_roof["kernel"], "bound": "fp64", "achieved": ach64, "peak": peak64,
+                    "unit": "G FP64-inst/s", "frac": None if ach64 is None else ach64 / peak64,
+                    "peak_kind": "measured FP64 GEMM rate (cuBLAS, 4096^3) / 2 FLOP per FMA",
+                    "fp64_inst_per_cell": inst_pc, "launches": sweep_n, "avg_launch_ms": avg_sweep_ms,
+                    "traffic": hbm_roof["traffic"]}
+        roofline_other = hbm_roof
     line = {
         "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD if args.n == 4096 else f"terzaghi_{args.n + 1}x{args.n + 1}_fp32",
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if fp64 else "f32", "data": "synthetic",
+        "config": {"workload": f"terzaghi_{args.n + 1}x{args.n + 1}_{args.precision}",
                    "cells": f"{nx}x{ny}", "levels": params["levels"],
                    "ne_fixed": params["ne_fixed"], "K": params["K"], "gamma": params["gamma"],
-                   "precision": "fp32 populations; fp64 residual norms, coarsest level, coupling",
-                   "l2": "state (3.4 GB) larger than L2; no flush needed",
+                   "precision": "fp64 storage and arithmetic" if fp64 else
+                                "fp32 populations; fp64 residual norms, coarsest level, coupling",
+                   "l2": f"state ({st['device_bytes'] / 1e9:.1f} GB) larger than L2; no flush needed",
                    "parallelism": f"replicas{world}",
                    "autotuned_strip_rows": tuned},
-        "roofline": {"kernel": "k_sweep_mom<float,float> finest level, smoothing", "bound": "hbm",
-                     "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "peak_kind": f"{peak_kind} copy bandwidth (burst)",
-                     "bytes_per_cell": bytes_per_cell, "launches": sweep_n, "avg_launch_ms": avg_sweep_ms,
-                     "traffic": None if traffic_pc is None else traffic_pc * cells},
+        "roofline": roofline,
         "cpu_baseline": cpu_base,
         "accuracy": accuracy,
         "e2e": {"value": cells * e2e_steps / e2e_s / 1e6, "unit": "MLUPS", "h2d_bytes_per_step": h2d,
@@ -330,6 +378,8 @@ def run_ours(args):
         "solver": {"last_ne": st["last_ne"], "last_res": st["last_res"], "diverged": st["diverged"],
                    "device_bytes": st["device_bytes"]},
     }
+    if roofline_other is not None:
+        line["roofline_hbm"] = roofline_other
     print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
@@ -525,6 +575,8 @@ def main():
     ap.add_argument("--no-tune", action="store_true", help="skip biot_autotune (default launch shapes)")
     ap.add_argument("--n", type=int, default=4096, help="cells per side (4096 = the benchmark workload)")
     ap.add_argument("--workload", choices=["single", "batched", "served"], default="single")
+    ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32",
+                    help="single: the FP32 path (default) or the plain FP64 path")
     ap.add_argument("--instances", type=int, default=64, help="batched: number of instances")
     ap.add_argument("--requests", type=int, default=48, help="served: number of requests")
     ap.add_argument("--mean-service", type=float, default=0.05, help="served: assumed mean service time (s)")
