@@ -76,6 +76,46 @@ def profiled_traffic_per_cell(path=PROFILE):
     return profiled_per_cell("traffic_bytes_per_cell", path)
 
 
+def step_model(params, n, fp64):
+    """Sweeps and algorithmic bytes of one physical step with fixed V-cycle counts
+    (N_E V-cycles of 2K smoothing sweeps and one residual + restriction sweep per
+    level, 2K sweeps on the coarsest level, then the fused flow step).  Per cell
+    and sweep:
+      finest smoothing: 5 moments in and out, F~ in, with FP32 storage the 2 low
+        parts in and out, plus the prolongated correction (5 coarse moments per 4
+        cells) once per 2K sweeps;
+      finest residual + restriction: the same inputs, 5 coarse moments per 4 cells out;
+      coarse smoothing: 5 moments and 5 of r in, 5 moments out (+ prolongation);
+      coarse residual + restriction: 10 in, 5 coarse out per 4 cells;
+      coarsest level (FP64): as coarse smoothing;
+      flow step: 9 f in and out, m_s in, two FP64 history planes in, D(t) and F~
+        out, and the copy of D(t) into the history.
+    Returns (cell-sweeps per step, bytes per step)."""
+    L, K, ne = params["levels"], params["K"], params["ne_fixed"]
+    esz = 8 if fp64 else 4
+    cell_sweeps = 0.0
+    nbytes = 0.0
+    for l in range(L - 1, -1, -1):  # finest first
+        side = n >> (L - 1 - l)
+        c = float(side * side)
+        e = 8 if (l == 0 and L > 1) or fp64 else esz
+        ec = 8 if (l == 1 and L > 1) or fp64 else esz  # storage of the next coarser level
+        fine = l == L - 1
+        nlo = 2 if (fine and not fp64) else 0
+        xin = 2 if fine else 5  # F~ or r
+        prol = 5 * ec / 4.0 / (2 * K) if l > 0 else 0.0  # correction from level l - 1
+        smooth = ((5 + nlo) * 2 + xin) * e + prol
+        cell_sweeps += ne * 2 * K * c
+        nbytes += ne * 2 * K * c * smooth
+        if l > 0:
+            cell_sweeps += ne * c
+            nbytes += ne * c * ((5 + nlo + xin) * e + 5 * ec / 4.0)
+    fine_cells = float(n * n)
+    fe = 8 if fp64 else 4
+    nbytes += fine_cells * (9 * fe * 2 + fe + 16 + 8 + 2 * fe + 16)
+    return cell_sweeps, nbytes
+
+
 def measured_fp64_peak(torch):
     """FP64 arithmetic peak of this GPU, measured: the best of 3 timed FP64 GEMMs
     of 4096^3 (cuBLAS through torch), in FLOP/s."""
@@ -380,6 +420,15 @@ def run_ours(args):
     }
     if roofline_other is not None:
         line["roofline_hbm"] = roofline_other
+    if params["ne_fixed"] > 0:
+        sweeps, nb = step_model(params, args.n, fp64)
+        t_step = ms / args.steps / 1e3
+        line["step"] = {"mlups_sweep": world * sweeps / t_step / 1e6,
+                        "algorithmic_bytes_per_step": nb, "achieved_gbs": nb / t_step / 1e9,
+                        "frac": nb / t_step / 1e9 / peak,
+                        "peak_kind": f"{peak_kind} copy bandwidth",
+                        "population_model_frac": (params["ne_fixed"] * 900.0 + 140.0) * cells / t_step / 1e9 / peak,
+                        "population_model": "N_E * 0.90 KB + 0.14 KB per fine cell (8 FP32 populations per cell-sweep)"}
     print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
