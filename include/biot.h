@@ -55,11 +55,13 @@ extern "C" {
 /* ---- storage precision of the populations --------------------------------- */
 #define BIOT_FP64 0  /* all populations and arithmetic in FP64 (parity path) */
 #define BIOT_FP32 1  /* FP32 elastic state and collisions, the displacement moments of
-                        the finest level kept as double-float (two FP32 planes), and
-                        of the coarse FP32 levels in the solve at t = 0 (which starts
-                        from a zero iterate); FP64 for residual norms, the coarsest
-                        multigrid level and the divergence / pressure accumulations
-                        of the coupling */
+                        the finest level kept as double-float (two FP32 planes); FP64
+                        for residual norms, the coarsest multigrid level and the
+                        divergence / pressure accumulations of the coupling.  The
+                        solve at t = 0, which starts from a zero iterate, runs on a
+                        temporary FP64 copy of the problem for grids of at least
+                        2048^2 cells (its state then rounded into FP32 storage), and
+                        with double-float coarse levels on smaller grids */
 #define BIOT_FP32_COARSE64 2  /* BIOT_FP32 on the finest level (elastic state and flow
                                  populations), FP64 on every coarser multigrid level:
                                  the coarse-grid corrections are not rounded to FP32 */

@@ -212,6 +212,17 @@ struct CopyJob {
     size_t n;
 };
 cudaError_t launch_copy_batch(const CopyJob *jobs, const SweepItem *items, int n, cudaStream_t s);
+
+// The finest-level state of an FP64 instance narrowed into an FP32 instance:
+// the 8 moment planes rounded to FP32, the first moments m_10, m_01 as
+// double-float (high part + low part of the remainder), the 9 flow population
+// planes and the 2 planes of F~ rounded to FP32.
+struct NarrowArgs {
+    size_t np;
+    const double *g64, *f64, *ft64;
+    float *g32, *glo32, *f32, *ft32;
+};
+cudaError_t launch_narrow_state(const NarrowArgs &a, cudaStream_t s);
 template <typename T> cudaError_t launch_init(const InitArgs<T> &a, cudaStream_t s);
 
 }  // namespace biot

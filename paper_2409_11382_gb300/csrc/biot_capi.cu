@@ -135,6 +135,7 @@ struct biot_ctx {
     long nstep = 0;
     bool solved = false, initialized = false, pending_res = false;
     bool cold_solve = false;  // the current elastic solve starts from a zero iterate (t = 0)
+    bool cold64 = false;      // FP32 instance: run the solve at t = 0 on an FP64 shadow (cold_start_fp64)
     bool se_stale = true;   // SE must be recomputed from D1, D2 before k_force
     bool ft_fresh = false;  // the last flow step computed F~ of the next elastic solve
     // statistics
@@ -248,6 +249,27 @@ int set_profiles(biot_ctx *h, int side, const double *eta, const double *p)
 }
 
 // ---- kernel sequencing --------------------------------------------------------
+
+// Large FP32 instances run their solve at t = 0 -- three V-cycles from a zero
+// iterate, where every correction is displacement-sized -- on a temporary FP64
+// copy of the problem and take over its state rounded to FP32 (the first moments
+// as double-float).  The time steps themselves stay on the FP32 path.  The FP32
+// rounding a cold start leaves behind grows with the grid: at 4096^2 it is the
+// largest part of the pressure error after the first steps (1.1e-5 against 4e-6
+// with the FP64 cold start), on grids up to 1024^2 it stays far below the 1e-5
+// target.  So the FP64 cold start applies from BIOT_COLD_FP64_MIN_CELLS cells
+// (default 2048^2; 0 = always, a negative value = never).  Smaller grids, and
+// large ones without room for the FP64 copy, solve with double-float coarse
+// levels instead (coarse_lo_mode).
+bool cold_fp64_for(long long cells)
+{
+    static long long v = -2;
+    if (v == -2) {
+        const char *e = getenv("BIOT_COLD_FP64_MIN_CELLS");
+        v = e ? atoll(e) : 2048LL * 2048LL;
+    }
+    return v >= 0 && cells >= v;
+}
 
 // Whether the sweeps of level l use the double-float first moments: always on
 // the finest FP32 level, on the coarse FP32 levels as coarse_lo_mode() says.
@@ -436,10 +458,112 @@ int read_residual(biot_ctx *h)
 
 // Elasticity update of Alg. 5 at the current time.
 int elastic_solve_device_loop(biot_ctx *h);
+int elastic_solve(biot_ctx *h);
+int ensure_initialized(biot_ctx *h);
+int finish_pending(biot_ctx *h);
+void release(biot_ctx *h);
+size_t estimate_bytes(const biot_params *p, const biot_side *sides);
+
+constexpr int COLD_FALLBACK = 1;  // no room for the FP64 copy: solve on the FP32 path
+
+// The solve at t = 0 of an FP32 instance on an FP64 copy of its problem (same
+// parameters, boundary data and sources), then the copy's finest state narrowed
+// into this instance.  Returns the solve's status, or COLD_FALLBACK when the copy
+// cannot be allocated.
+int cold_start_fp64(biot_ctx *h)
+{
+    biot_params p64 = h->P;
+    p64.precision = BIOT_FP64;
+    biot_side sides[4];
+    for (int s = 0; s < 4; s++) sides[s] = biot_side{h->bc_eta[s], h->bc_p[s], nullptr, nullptr};
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+        cudaGetLastError();
+        return COLD_FALLBACK;
+    }
+    if (estimate_bytes(&p64, sides) + (64u << 20) > free_b) return COLD_FALLBACK;
+    biot_handle s = nullptr;
+    int rc = biot_create(&p64, sides, &s);
+    if (rc) return rc == BIOT_ERR_OOM ? COLD_FALLBACK : rc;
+    // the copy works on this instance's stream, after its own set-up
+    if (cudaStreamSynchronize(s->own_stream) != cudaSuccess) rc = fail(BIOT_ERR_CUDA, "FP64 copy set-up failed");
+    s->stream = h->stream;
+    const size_t np = (size_t)h->P.nx * h->P.ny;
+    for (int side = 0; side < 4 && !rc; side++) {
+        const size_t m = 2 * (size_t)side_cells(h, side) + 1;
+        if (h->eta_prof[side] && !(rc = dev_alloc(s, (void **)&s->eta_prof[side], 2 * m * sizeof(double))))
+            if (cudaMemcpyAsync(s->eta_prof[side], h->eta_prof[side], 2 * m * sizeof(double), cudaMemcpyDeviceToDevice, h->stream) != cudaSuccess)
+                rc = fail(BIOT_ERR_CUDA, "boundary data copy failed");
+        if (!rc && h->p_prof[side] && !(rc = dev_alloc(s, (void **)&s->p_prof[side], m * sizeof(double))))
+            if (cudaMemcpyAsync(s->p_prof[side], h->p_prof[side], m * sizeof(double), cudaMemcpyDeviceToDevice, h->stream) != cudaSuccess)
+                rc = fail(BIOT_ERR_CUDA, "boundary data copy failed");
+    }
+    if (!rc && h->has_src && !(rc = dev_alloc(s, (void **)&s->src, np * sizeof(double)))) {
+        if (cudaMemcpyAsync(s->src, h->src, np * sizeof(double), cudaMemcpyDeviceToDevice, h->stream) != cudaSuccess)
+            rc = fail(BIOT_ERR_CUDA, "source copy failed");
+        s->has_src = true;
+    }
+    if (!rc && h->has_fbody && !(rc = dev_alloc(s, (void **)&s->fbody, 2 * np * sizeof(double)))) {
+        if (cudaMemcpyAsync(s->fbody, h->fbody, 2 * np * sizeof(double), cudaMemcpyDeviceToDevice, h->stream) != cudaSuccess)
+            rc = fail(BIOT_ERR_CUDA, "body force copy failed");
+        s->has_fbody = true;
+    }
+    int status = BIOT_OK;
+    if (!rc) rc = ensure_initialized(s);
+    if (!rc) {
+        rc = elastic_solve(s);
+        if (rc == BIOT_ERR_NOT_CONVERGED) {
+            status = rc;
+            rc = BIOT_OK;
+        }
+    }
+    if (!rc) rc = finish_pending(s);
+    if (!rc) {
+        const Level &Ls = s->lv[s->L - 1];
+        Level &Lh = h->lv[h->L - 1];
+        NarrowArgs a{};
+        a.np = np;
+        a.g64 = static_cast<const double *>(Ls.g[Ls.cur]);
+        a.f64 = static_cast<const double *>(s->f[s->fcur]);
+        a.ft64 = static_cast<const double *>(s->Ft);
+        a.g32 = static_cast<float *>(Lh.g[Lh.cur]);
+        a.glo32 = static_cast<float *>(Lh.glo[Lh.cur]);
+        a.f32 = static_cast<float *>(h->f[h->fcur]);
+        a.ft32 = static_cast<float *>(h->Ft);
+        if (!a.glo32) rc = fail(BIOT_ERR_CUDA, "FP32 instance without double-float first moments");
+        else if (launch_narrow_state(a, h->stream) != cudaSuccess) rc = fail(BIOT_ERR_CUDA, "state hand-over launch failed");
+        else if (cudaStreamSynchronize(h->stream) != cudaSuccess) rc = fail(BIOT_ERR_CUDA, "state hand-over failed");
+    }
+    if (!rc) {
+        h->launches += s->launches + 1;
+        h->total_cycles += s->total_cycles;
+        h->notconv_steps += s->notconv_steps;
+        h->last_ne = s->last_ne;
+        h->last_res = s->last_res;
+        h->initialized = true;
+        h->solved = true;
+        h->pending_res = false;
+        h->ft_fresh = false;
+        h->se_stale = true;
+        h->lv[h->L - 1].hist_valid = 0;
+    }
+    cudaStreamSynchronize(h->stream);
+    s->stream = s->own_stream;
+    release(s);
+    return rc ? rc : status;
+}
 
 int elastic_solve(biot_ctx *h)
 {
     int rc;
+    if (h->cold64 && h->nstep == 0 && !h->solved && !h->rec) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        CUDA_TRY(cudaStreamIsCapturing(h->stream, &cs));
+        if (cs == cudaStreamCaptureStatusNone) {
+            rc = cold_start_fp64(h);
+            if (rc != COLD_FALLBACK) return rc;
+        }
+    }
     rc = h->fp32 ? force_typed<float>(h) : force_typed<double>(h);
     if (rc) return rc;
     h->lv[h->L - 1].hist_valid = 0;
@@ -819,6 +943,7 @@ int biot_create(const biot_params *p, const biot_side sides[4], biot_handle *out
     h->P = *p;
     h->L = p->mg_levels;
     h->fp32 = p->precision != BIOT_FP64;  // finest level and flow populations in FP32
+    h->cold64 = h->fp32 && cold_fp64_for((long long)p->nx * p->ny);
     h->h = p->lx / p->nx;
     h->lam = p->c0 * p->lambda;
     h->mu = p->c0 * p->mu;
@@ -1654,6 +1779,8 @@ struct Request {
     std::vector<double> prof[4][2];  // owned copies of the boundary data
     long target = 0;                 // physical steps to take
     size_t bytes = 0;
+    size_t shadow = 0;   // transient FP64 copy of the solve at t = 0 (cold_start_fp64)
+    bool cold64 = false;
     int state = REQ_QUEUED, status = BIOT_OK;
     std::string error;
     double t_submit = 0, t_start = 0, t_done = 0;
@@ -1722,8 +1849,8 @@ void server_loop(biot_server_s *S)
             if (S->stop) break;
             while (!S->queue.empty() && (int)(S->resident.size() + admit.size()) < S->max_resident) {
                 Request &r = S->req[S->queue.front()];
-                if (S->used + r.bytes > S->budget) break;
-                S->used += r.bytes;
+                if (S->used + r.bytes + r.shadow > S->budget) break;
+                S->used += r.bytes + r.shadow;
                 S->peak_used = S->used > S->peak_used ? S->used : S->peak_used;
                 r.state = REQ_RUNNING;
                 r.t_start = S->now();
@@ -1734,10 +1861,18 @@ void server_loop(biot_server_s *S)
         for (Request *r : admit) {
             biot_handle h = nullptr;
             int rc = biot_create(&r->P, r->sides, &h);
-            if (!rc) rc = ensure_initialized(h);
+            if (!rc) {
+                h->cold64 = r->cold64;
+                rc = ensure_initialized(h);
+            }
             if (!rc) {
                 rc = elastic_solve(h);  // the solve at t = 0 (launch-only with fixed V-cycles)
                 if (rc == BIOT_ERR_NOT_CONVERGED) rc = BIOT_OK;
+            }
+            {
+                std::lock_guard<std::mutex> lock(S->mu);  // the FP64 copy is gone
+                S->used -= r->shadow;
+                r->shadow = 0;
             }
             r->h = h;
             if (rc) {
@@ -1843,6 +1978,12 @@ int biot_server_submit(biot_server S, const biot_params *p, const biot_side side
     r.P = *p;
     r.target = (long)std::floor(T / p->dt + 0.5);
     r.bytes = estimate_bytes(p, sides);
+    if (p->precision != BIOT_FP64 && cold_fp64_for((long long)p->nx * p->ny)) {
+        biot_params p64 = *p;
+        p64.precision = BIOT_FP64;
+        r.shadow = estimate_bytes(&p64, sides);
+        r.cold64 = true;
+    }
     for (int s = 0; s < 4; s++) {
         r.sides[s] = sides[s];
         const size_t m = 2 * (size_t)((s == BIOT_BOTTOM || s == BIOT_TOP) ? p->nx : p->ny) + 1;
@@ -1857,6 +1998,10 @@ int biot_server_submit(biot_server S, const biot_params *p, const biot_side side
     }
     std::lock_guard<std::mutex> lock(S->mu);
     if (r.bytes > S->budget) return fail(BIOT_ERR_OOM, "the request alone needs more device memory than the server's budget");
+    if (r.bytes + r.shadow > S->budget) {  // no room for the FP64 copy: FP32 cold start
+        r.shadow = 0;
+        r.cold64 = false;
+    }
     r.id = S->next_id++;
     r.t_submit = S->now();
     *id = r.id;

@@ -48,6 +48,32 @@ __global__ void __launch_bounds__(256) k_copy_batch(const biot::CopyJob *__restr
     for (size_t i = base + threadIdx.x; i < base + 1024 && i < j.n; i += 256) j.dst[i] = j.src[i];
 }
 
+// State hand-over from an FP64 instance to an FP32 one (see NarrowArgs).
+__global__ void __launch_bounds__(256) k_narrow_state(const biot::NarrowArgs a)
+{
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.np; i += (size_t)gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int k = 0; k < 8; k++) {
+            const double v = a.g64[k * a.np + i];
+            const float hi = (float)v;
+            a.g32[k * a.np + i] = hi;
+            if (k < 2) a.glo32[k * a.np + i] = (float)(v - (double)hi);
+        }
+#pragma unroll
+        for (int k = 0; k < 9; k++) a.f32[k * a.np + i] = (float)a.f64[k * a.np + i];
+#pragma unroll
+        for (int k = 0; k < 2; k++) a.ft32[k * a.np + i] = (float)a.ft64[k * a.np + i];
+    }
+}
+
+cudaError_t biot::launch_narrow_state(const biot::NarrowArgs &a, cudaStream_t s)
+{
+    if (a.np == 0) return cudaSuccess;
+    const unsigned blocks = (unsigned)((a.np + 255) / 256 < 65536 ? (a.np + 255) / 256 : 65536);
+    k_narrow_state<<<blocks, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
 cudaError_t biot::launch_copy_batch(const biot::CopyJob *jobs, const biot::SweepItem *items, int n, cudaStream_t s)
 {
     if (n <= 0) return cudaSuccess;
