@@ -159,10 +159,24 @@ struct StopArgs {
 cudaError_t launch_stop_test(const StopArgs &a, cudaStream_t s);
 
 template <typename T, typename TC> cudaError_t launch_sweep_mom(const SweepArgs<T, TC> &a, cudaStream_t s);
-// Batched sweep: one launch of n work items of storage kind `variant`
-// (SWEEP_V_* flags); jobs and items are device arrays.
+// The jobs of one batched sweep launch, passed as a kernel parameter -- so that,
+// as in a single-instance launch, the arguments sit in constant memory rather
+// than in shared memory and registers.  Job j owns the work items
+// start[j] .. start[j+1]-1, laid out row by row with sx[j] strips (or tiles) per
+// row; ty[j] is its strip height (strip form).
+constexpr int BATCH_MAX_JOBS = 96;
 template <typename T, typename TC>
-cudaError_t launch_sweep_batch(int variant, const SweepArgs<T, TC> *jobs, const SweepItem *items, int n, cudaStream_t s);
+struct BatchParams {
+    int njobs;
+    int start[BATCH_MAX_JOBS + 1];
+    int sx[BATCH_MAX_JOBS];
+    int ty[BATCH_MAX_JOBS];
+    SweepArgs<T, TC> job[BATCH_MAX_JOBS];
+};
+// Batched sweep: one launch of P.start[P.njobs] work items of storage kind
+// `variant` (SWEEP_V_* flags).
+template <typename T, typename TC>
+cudaError_t launch_sweep_batch(int variant, const BatchParams<T, TC> &P, cudaStream_t s);
 // Resident CTAs of a sweep launch of this kind on the current device, and the
 // strip geometry of the sweep kernels (columns per strip).
 template <typename T, typename TC> int sweep_slots(int variant);

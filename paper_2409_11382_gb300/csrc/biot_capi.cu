@@ -8,6 +8,7 @@
 // copies, and evaluates the per-instance coefficients once on the host.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -17,6 +18,7 @@
 #include <condition_variable>
 #include <deque>
 #include <map>
+#include <memory>
 #include <mutex>
 #include <thread>
 #include <new>
@@ -1328,8 +1330,6 @@ struct biot_batch_s {
     std::vector<BatchSlot> slots[3];              // per tkind, parallel to the job tables
     std::vector<SweepItem> items;
     std::vector<size_t> nops;                     // recorded sweeps per instance and step
-    void *jobs_dev[2][3] = {};                    // per graph parity, per tkind
-    SweepItem *items_dev = nullptr;
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     std::vector<long> epoch[2];                   // instance epochs the graphs were captured at
     // batched flow steps: per storage type (0 FP32, 1 FP64) the instances and their
@@ -1344,11 +1344,6 @@ struct biot_batch_s {
 };
 
 namespace {
-
-size_t tkind_size(int tk)
-{
-    return tk == 0 ? sizeof(SweepArgs<double, double>) : tk == 1 ? sizeof(SweepArgs<float, double>) : sizeof(SweepArgs<float, float>);
-}
 
 int batch_alloc(biot_batch_s *b, void **p, size_t bytes)
 {
@@ -1456,30 +1451,40 @@ int batch_plan(biot_batch_s *b)
     }
     if ((rc = batch_alloc(b, (void **)&b->copy_items_dev, b->copy_items.size() * sizeof(SweepItem)))) return rc;
     CUDA_TRY(cudaMemcpy(b->copy_items_dev, b->copy_items.data(), b->copy_items.size() * sizeof(SweepItem), cudaMemcpyHostToDevice));
-    for (int par = 0; par < 2; par++)
-        for (int tk = 0; tk < 3; tk++)
-            if ((rc = batch_alloc(b, &b->jobs_dev[par][tk], b->slots[tk].size() * tkind_size(tk)))) return rc;
-    if ((rc = batch_alloc(b, (void **)&b->items_dev, b->items.size() * sizeof(SweepItem)))) return rc;
-    CUDA_TRY(cudaMemcpy(b->items_dev, b->items.data(), b->items.size() * sizeof(SweepItem), cudaMemcpyHostToDevice));
     return BIOT_OK;
 }
 
+// One planned launch of the batch as launches of at most BATCH_MAX_JOBS jobs,
+// each with its parameter block: the recorded arguments of its sweeps and the
+// geometry of their work items (job-major, row by row, as batch_plan lays them out).
 template <typename T, typename TC>
-cudaError_t batch_launch_typed(biot_batch_s *b, int par, const BatchLaunch &L)
+cudaError_t batch_launch_typed(biot_batch_s *b, const BatchLaunch &L, std::vector<std::vector<SweepJob>> &rec)
 {
-    const SweepArgs<T, TC> *jobs = static_cast<const SweepArgs<T, TC> *>(b->jobs_dev[par][L.tkind]) + L.job_off;
-    return launch_sweep_batch<T, TC>(L.variant, jobs, b->items_dev + L.item_off, L.nitems, b->stream);
-}
-
-template <typename T, typename TC>
-void batch_fill_typed(biot_batch_s *b, int tk, std::vector<std::vector<SweepJob>> &rec, std::vector<unsigned char> &host)
-{
-    host.resize(b->slots[tk].size() * sizeof(SweepArgs<T, TC>));
-    SweepArgs<T, TC> *out = reinterpret_cast<SweepArgs<T, TC> *>(host.data());
-    for (size_t j = 0; j < b->slots[tk].size(); j++) {
-        const BatchSlot &s = b->slots[tk][j];
-        out[j] = job_args<T, TC>(rec[s.inst][s.op]);
+    std::unique_ptr<BatchParams<T, TC>> P(new (std::nothrow) BatchParams<T, TC>());
+    if (!P) return cudaErrorMemoryAllocation;
+    size_t it = L.item_off;
+    const size_t it_end = L.item_off + L.nitems;
+    for (int g0 = 0; g0 < L.njobs; g0 += BATCH_MAX_JOBS) {
+        const int nj = std::min(BATCH_MAX_JOBS, L.njobs - g0);
+        P->njobs = nj;
+        int count = 0;
+        for (int k = 0; k < nj; k++) {
+            const BatchSlot &sl = b->slots[L.tkind][L.job_off + g0 + k];
+            P->job[k] = job_args<T, TC>(rec[sl.inst][sl.op]);
+            P->start[k] = count;
+            P->sx[k] = 1;
+            P->ty[k] = 0;
+            for (; it < it_end && b->items[it].job == g0 + k; it++, count++) {
+                const SweepItem &w = b->items[it];
+                P->sx[k] = std::max(P->sx[k], w.bx + 1);
+                P->ty[k] = w.ty;
+            }
+        }
+        P->start[nj] = count;
+        cudaError_t e = launch_sweep_batch<T, TC>(L.variant, *P, b->stream);
+        if (e != cudaSuccess) return e;
     }
+    return it == it_end ? cudaSuccess : cudaErrorInvalidValue;
 }
 
 // Capture one time step of every instance (parity par of the flow buffers).
@@ -1535,9 +1540,9 @@ int batch_capture(biot_batch_s *b, int par)
     }
     for (size_t k = 0; k < b->launches.size() && !rc; k++) {
         const BatchLaunch &L = b->launches[k];
-        cudaError_t e = L.tkind == 0 ? batch_launch_typed<double, double>(b, par, L)
-                      : L.tkind == 1 ? batch_launch_typed<float, double>(b, par, L)
-                                     : batch_launch_typed<float, float>(b, par, L);
+        cudaError_t e = L.tkind == 0 ? batch_launch_typed<double, double>(b, L, rec)
+                      : L.tkind == 1 ? batch_launch_typed<float, double>(b, L, rec)
+                                     : batch_launch_typed<float, float>(b, L, rec);
         if (e != cudaSuccess) rc = fail(BIOT_ERR_CUDA, std::string("batched sweep launch: ") + cudaGetErrorString(e));
         nl++;
     }
@@ -1558,15 +1563,6 @@ int batch_capture(biot_batch_s *b, int par)
     }
     if (g) cudaGraphDestroy(g);
     if (rc) return rc;
-    // job tables of this parity
-    std::vector<unsigned char> host;
-    for (int tk = 0; tk < 3; tk++) {
-        if (b->slots[tk].empty()) continue;
-        if (tk == 0) batch_fill_typed<double, double>(b, tk, rec, host);
-        else if (tk == 1) batch_fill_typed<float, double>(b, tk, rec, host);
-        else batch_fill_typed<float, float>(b, tk, rec, host);
-        CUDA_TRY(cudaMemcpy(b->jobs_dev[par][tk], host.data(), host.size(), cudaMemcpyHostToDevice));
-    }
     {
         std::vector<FlowFusedArgs<float>> ff;
         std::vector<FlowFusedArgs<double>> fd;

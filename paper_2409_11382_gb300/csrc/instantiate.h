@@ -7,9 +7,9 @@
 #define BIOT_SWEEP_MOM(T, TC)                                                                          \
     template <> cudaError_t biot::launch_sweep_mom<T, TC>(const biot::SweepArgs<T, TC> &a, cudaStream_t s) \
     { return biot::launch_sweep_mom_impl<T, TC>(a, s); }                                               \
-    template <> cudaError_t biot::launch_sweep_batch<T, TC>(int v, const biot::SweepArgs<T, TC> *j,      \
-                                                            const biot::SweepItem *it, int n, cudaStream_t s) \
-    { return biot::launch_sweep_batch_impl<T, TC>(v, j, it, n, s); }                                   \
+    template <> cudaError_t biot::launch_sweep_batch<T, TC>(int v, const biot::BatchParams<T, TC> &P,   \
+                                                            cudaStream_t s)                            \
+    { return biot::launch_sweep_batch_impl<T, TC>(v, P, s); }                                          \
     template <> int biot::sweep_slots<T, TC>(int v) { return biot::sweep_slots_impl<T, TC>(v); }
 #define BIOT_FIELDS(T)                                                                                 \
     template <> cudaError_t biot::launch_sexp<T>(const biot::SexpArgs<T> &a, cudaStream_t s)             \

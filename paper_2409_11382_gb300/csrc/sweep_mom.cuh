@@ -743,23 +743,33 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 6 : 1) k_sweep_mom(const 
     sweep_strip<T, TC, NT, KIND, LO, RESTRICT>(a, blockIdx.x, blockIdx.y, TY, smem_raw, red);
 }
 
-// Batched form: CTA b processes work item items[b], a strip of the sweep
-// described by jobs[items[b].job] (the jobs of one launch may belong to
-// different instances and different multigrid levels of one storage kind).
-// (7 resident CTAs per SM with FP32 storage, as the single-instance kernel reaches
-// on its own: the job arguments live in shared memory here, and without the bound
-// the compiler keeps more of them in registers at the cost of one CTA per SM)
+// The job of work item b of a batched launch (binary search over the item
+// ranges; the same for every thread of a CTA).
+template <typename T, typename TC>
+__device__ __forceinline__ int batch_job(const BatchParams<T, TC> &P, int b)
+{
+    int lo = 0, hi = P.njobs - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (P.start[mid] <= b) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Batched form: CTA b processes work item b, a strip of the sweep of its job (the
+// jobs of one launch may belong to different instances and different multigrid
+// levels of one storage kind).  The arguments are read from the launch's
+// parameter block, which lives in constant memory.
 template <typename T, typename TC, int NT, int KIND, bool LO, bool RESTRICT>
 __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 7 : 1)
-    k_sweep_batch(const SweepArgs<T, TC> *__restrict__ jobs, const SweepItem *__restrict__ items)
+    k_sweep_batch(const __grid_constant__ BatchParams<T, TC> P)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double red[2][NT / 32];
-    __shared__ SweepArgs<T, TC> sa;
-    const SweepItem it = items[blockIdx.x];
-    if (threadIdx.x == 0) sa = jobs[it.job];
-    __syncthreads();
-    sweep_strip<T, TC, NT, KIND, LO, RESTRICT>(sa, it.bx, it.by, it.ty, smem_raw, red);
+    const int j = batch_job(P, blockIdx.x);
+    const int local = blockIdx.x - P.start[j], sx = P.sx[j];
+    sweep_strip<T, TC, NT, KIND, LO, RESTRICT>(P.job[j], local % sx, local / sx, P.ty[j], smem_raw, red);
 }
 
 // ---------------------------------------------------------------------------
@@ -908,19 +918,16 @@ __global__ void __launch_bounds__(TileShape<TX, TY>::NT) k_sweep_tile(const Swee
     tile_body<T, TC, TX, TY, KIND, LO, RESTRICT>(a, blockIdx.x, blockIdx.y, smem_raw, red);
 }
 
-// Batched form: CTA b processes tile (items[b].bx, items[b].by) of the sweep
-// jobs[items[b].job] (items[b].ty is unused).
+// Batched form: CTA b processes work item b, a tile of the sweep of its job.
 template <typename T, typename TC, int TX, int TY, int KIND, bool LO, bool RESTRICT>
 __global__ void __launch_bounds__(TileShape<TX, TY>::NT)
-    k_sweep_tile_batch(const SweepArgs<T, TC> *__restrict__ jobs, const SweepItem *__restrict__ items)
+    k_sweep_tile_batch(const __grid_constant__ BatchParams<T, TC> P)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double red[2][TileShape<TX, TY>::NT / 32];
-    __shared__ SweepArgs<T, TC> sa;
-    const SweepItem it = items[blockIdx.x];
-    if (threadIdx.x == 0) sa = jobs[it.job];
-    __syncthreads();
-    tile_body<T, TC, TX, TY, KIND, LO, RESTRICT>(sa, it.bx, it.by, smem_raw, red);
+    const int j = batch_job(P, blockIdx.x);
+    const int local = blockIdx.x - P.start[j], sx = P.sx[j];
+    tile_body<T, TC, TX, TY, KIND, LO, RESTRICT>(P.job[j], local % sx, local / sx, smem_raw, red);
 }
 
 // Tile shape per storage type: FP64 levels use small tiles, so that the few
@@ -962,7 +969,7 @@ cudaError_t launch_tile(const SweepArgs<T, TC> &a, cudaStream_t s)
 }
 
 template <typename T, typename TC, int KIND, bool LO, bool RESTRICT>
-cudaError_t launch_tile_batch(const SweepArgs<T, TC> *jobs, const SweepItem *items, int n, cudaStream_t s)
+cudaError_t launch_tile_batch(const BatchParams<T, TC> &P, cudaStream_t s)
 {
     constexpr int TX = TileFor<T>::X, TY = TileFor<T>::Y;
     constexpr size_t smem = tile_smem_bytes<T, TX, TY, KIND, LO>();
@@ -973,8 +980,9 @@ cudaError_t launch_tile_batch(const SweepArgs<T, TC> *jobs, const SweepItem *ite
         if (e != cudaSuccess) return e;
         configured = true;
     }
+    const int n = P.start[P.njobs];
     if (n <= 0) return cudaSuccess;
-    kern<<<n, TileShape<TX, TY>::NT, smem, s>>>(jobs, items);
+    kern<<<n, TileShape<TX, TY>::NT, smem, s>>>(P);
     return cudaGetLastError();
 }
 
@@ -1017,12 +1025,13 @@ cudaError_t launch_rows(const SweepArgs<T, TC> &a, cudaStream_t s)
 }
 
 template <typename T, typename TC, int KIND, bool LO, bool RESTRICT>
-cudaError_t launch_batch_v(const SweepArgs<T, TC> *jobs, const SweepItem *items, int n, cudaStream_t s)
+cudaError_t launch_batch_v(const BatchParams<T, TC> &P, cudaStream_t s)
 {
     using SK = SweepKernel<T, TC, KIND, LO, RESTRICT>;
+    const int n = P.start[P.njobs];
     if (n <= 0) return cudaSuccess;
     if (!SK::slots()) return cudaErrorInvalidConfiguration;
-    k_sweep_batch<T, TC, SWEEP_NT, KIND, LO, RESTRICT><<<n, SWEEP_NT, SK::smem, s>>>(jobs, items);
+    k_sweep_batch<T, TC, SWEEP_NT, KIND, LO, RESTRICT><<<n, SWEEP_NT, SK::smem, s>>>(P);
     return cudaGetLastError();
 }
 
@@ -1053,10 +1062,9 @@ auto dispatch_kind(bool coarse, bool lo, bool rs, bool ghosts, A &&...args)
 
 template <typename T, typename TC, int KIND, bool LO, bool RS>
 struct BatchRun {
-    static cudaError_t run(bool tile, const SweepArgs<T, TC> *jobs, const SweepItem *items, int n, cudaStream_t s)
+    static cudaError_t run(bool tile, const BatchParams<T, TC> &P, cudaStream_t s)
     {
-        return tile ? launch_tile_batch<T, TC, KIND, LO, RS>(jobs, items, n, s)
-                    : launch_batch_v<T, TC, KIND, LO, RS>(jobs, items, n, s);
+        return tile ? launch_tile_batch<T, TC, KIND, LO, RS>(P, s) : launch_batch_v<T, TC, KIND, LO, RS>(P, s);
     }
 };
 template <typename T, typename TC, int KIND, bool LO, bool RS>
@@ -1069,10 +1077,10 @@ struct RowsRun {
 };
 
 template <typename T, typename TC>
-cudaError_t launch_sweep_batch_impl(int v, const SweepArgs<T, TC> *jobs, const SweepItem *items, int n, cudaStream_t s)
+cudaError_t launch_sweep_batch_impl(int v, const BatchParams<T, TC> &P, cudaStream_t s)
 {
     return dispatch_kind<T, TC, BatchRun>(v & SWEEP_V_COARSE, v & SWEEP_V_LO, v & SWEEP_V_RESTRICT,
-                                         !(v & SWEEP_V_NOGHOST), (v & SWEEP_V_TILE) != 0, jobs, items, n, s);
+                                         !(v & SWEEP_V_NOGHOST), (v & SWEEP_V_TILE) != 0, P, s);
 }
 
 template <typename T, typename TC>
