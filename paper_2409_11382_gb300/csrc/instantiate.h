@@ -2,6 +2,7 @@
 // precision; included once by each kernels_*.cu translation unit.
 #pragma once
 #include "field_kernels.cuh"
+#include "sweep_batch.cuh"
 #include "sweep_mom.cuh"
 
 #define BIOT_SWEEP_MOM(T, TC)                                                                          \

@@ -743,35 +743,6 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 6 : 1) k_sweep_mom(const 
     sweep_strip<T, TC, NT, KIND, LO, RESTRICT>(a, blockIdx.x, blockIdx.y, TY, smem_raw, red);
 }
 
-// The job of work item b of a batched launch (binary search over the item
-// ranges; the same for every thread of a CTA).
-template <typename T, typename TC>
-__device__ __forceinline__ int batch_job(const BatchParams<T, TC> &P, int b)
-{
-    int lo = 0, hi = P.njobs - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (P.start[mid] <= b) lo = mid;
-        else hi = mid - 1;
-    }
-    return lo;
-}
-
-// Batched form: CTA b processes work item b, a strip of the sweep of its job (the
-// jobs of one launch may belong to different instances and different multigrid
-// levels of one storage kind).  The arguments are read from the launch's
-// parameter block, which lives in constant memory.
-template <typename T, typename TC, int NT, int KIND, bool LO, bool RESTRICT>
-__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 7 : 1)
-    k_sweep_batch(const __grid_constant__ BatchParams<T, TC> P)
-{
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ double red[2][NT / 32];
-    const int j = batch_job(P, blockIdx.x);
-    const int local = blockIdx.x - P.start[j], sx = P.sx[j];
-    sweep_strip<T, TC, NT, KIND, LO, RESTRICT>(P.job[j], local % sx, local / sx, P.ty[j], smem_raw, red);
-}
-
 // ---------------------------------------------------------------------------
 // Tile sweep for small, latency-bound levels.  A CTA of (TX+4) x (TY+4) threads
 // (rounded up to whole warps) stages its TX x TY tile and a 2-cell halo in one
@@ -918,18 +889,6 @@ __global__ void __launch_bounds__(TileShape<TX, TY>::NT) k_sweep_tile(const Swee
     tile_body<T, TC, TX, TY, KIND, LO, RESTRICT>(a, blockIdx.x, blockIdx.y, smem_raw, red);
 }
 
-// Batched form: CTA b processes work item b, a tile of the sweep of its job.
-template <typename T, typename TC, int TX, int TY, int KIND, bool LO, bool RESTRICT>
-__global__ void __launch_bounds__(TileShape<TX, TY>::NT)
-    k_sweep_tile_batch(const __grid_constant__ BatchParams<T, TC> P)
-{
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ double red[2][TileShape<TX, TY>::NT / 32];
-    const int j = batch_job(P, blockIdx.x);
-    const int local = blockIdx.x - P.start[j], sx = P.sx[j];
-    tile_body<T, TC, TX, TY, KIND, LO, RESTRICT>(P.job[j], local % sx, local / sx, smem_raw, red);
-}
-
 // Tile shape per storage type: FP64 levels use small tiles, so that the few
 // cells of a coarse FP64 level spread over many SMs (FP64 issue rate per SM is
 // the limit there).
@@ -968,24 +927,6 @@ cudaError_t launch_tile(const SweepArgs<T, TC> &a, cudaStream_t s)
     return cudaGetLastError();
 }
 
-template <typename T, typename TC, int KIND, bool LO, bool RESTRICT>
-cudaError_t launch_tile_batch(const BatchParams<T, TC> &P, cudaStream_t s)
-{
-    constexpr int TX = TileFor<T>::X, TY = TileFor<T>::Y;
-    constexpr size_t smem = tile_smem_bytes<T, TX, TY, KIND, LO>();
-    auto kern = k_sweep_tile_batch<T, TC, TX, TY, KIND, LO, RESTRICT>;
-    static bool configured = false;
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        configured = true;
-    }
-    const int n = P.start[P.njobs];
-    if (n <= 0) return cudaSuccess;
-    kern<<<n, TileShape<TX, TY>::NT, smem, s>>>(P);
-    return cudaGetLastError();
-}
-
 constexpr int SWEEP_NT = 128;
 static_assert(SWEEP_NT - 4 == SWEEP_STRIP_COLS, "strip geometry shared with the host planner");
 
@@ -998,13 +939,11 @@ struct SweepKernel {
         static int n = 0;
         if (!n) {
             auto k1 = k_sweep_mom<T, TC, SWEEP_NT, KIND, LO, RESTRICT>;
-            auto k2 = k_sweep_batch<T, TC, SWEEP_NT, KIND, LO, RESTRICT>;
             if (cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
-            if (cudaFuncSetAttribute(k2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
             int dev = 0, sms = 0, per_sm = 0;
             if (cudaGetDevice(&dev) != cudaSuccess) return 0;
             if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
-            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k2, SWEEP_NT, smem) != cudaSuccess) return 0;
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k1, SWEEP_NT, smem) != cudaSuccess) return 0;
             n = sms * (per_sm > 0 ? per_sm : 1);
         }
         return n;
@@ -1021,17 +960,6 @@ cudaError_t launch_rows(const SweepArgs<T, TC> &a, cudaStream_t s)
     int ty = a.rows > 0 ? a.rows + (a.rows & 1) : sweep_strip_rows(a.nx, a.ny, slots);
     dim3 grid((a.nx + SWEEP_NT - 5) / (SWEEP_NT - 4), (a.ny + ty - 1) / ty);
     k_sweep_mom<T, TC, SWEEP_NT, KIND, LO, RESTRICT><<<grid, SWEEP_NT, SK::smem, s>>>(a, ty);
-    return cudaGetLastError();
-}
-
-template <typename T, typename TC, int KIND, bool LO, bool RESTRICT>
-cudaError_t launch_batch_v(const BatchParams<T, TC> &P, cudaStream_t s)
-{
-    using SK = SweepKernel<T, TC, KIND, LO, RESTRICT>;
-    const int n = P.start[P.njobs];
-    if (n <= 0) return cudaSuccess;
-    if (!SK::slots()) return cudaErrorInvalidConfiguration;
-    k_sweep_batch<T, TC, SWEEP_NT, KIND, LO, RESTRICT><<<n, SWEEP_NT, SK::smem, s>>>(P);
     return cudaGetLastError();
 }
 
@@ -1061,33 +989,9 @@ auto dispatch_kind(bool coarse, bool lo, bool rs, bool ghosts, A &&...args)
 }
 
 template <typename T, typename TC, int KIND, bool LO, bool RS>
-struct BatchRun {
-    static cudaError_t run(bool tile, const BatchParams<T, TC> &P, cudaStream_t s)
-    {
-        return tile ? launch_tile_batch<T, TC, KIND, LO, RS>(P, s) : launch_batch_v<T, TC, KIND, LO, RS>(P, s);
-    }
-};
-template <typename T, typename TC, int KIND, bool LO, bool RS>
-struct SlotsRun {
-    static int run() { return SweepKernel<T, TC, KIND, LO, RS>::slots(); }
-};
-template <typename T, typename TC, int KIND, bool LO, bool RS>
 struct RowsRun {
     static cudaError_t run(const SweepArgs<T, TC> &a, cudaStream_t s) { return launch_rows<T, TC, KIND, LO, RS>(a, s); }
 };
-
-template <typename T, typename TC>
-cudaError_t launch_sweep_batch_impl(int v, const BatchParams<T, TC> &P, cudaStream_t s)
-{
-    return dispatch_kind<T, TC, BatchRun>(v & SWEEP_V_COARSE, v & SWEEP_V_LO, v & SWEEP_V_RESTRICT,
-                                         !(v & SWEEP_V_NOGHOST), (v & SWEEP_V_TILE) != 0, P, s);
-}
-
-template <typename T, typename TC>
-int sweep_slots_impl(int v)
-{
-    return dispatch_kind<T, TC, SlotsRun>(v & SWEEP_V_COARSE, v & SWEEP_V_LO, v & SWEEP_V_RESTRICT, !(v & SWEEP_V_NOGHOST));
-}
 
 // Level kind from the arguments: F~ present = finest level; low parts only
 // with FP32 storage on the finest level.
