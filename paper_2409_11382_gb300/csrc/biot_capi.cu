@@ -1311,7 +1311,7 @@ int tkind_slots(int tkind, int variant)
 // One launch of the batched schedule.
 struct BatchLaunch {
     int tkind, variant;
-    size_t job_off, item_off;  // offsets into the job table of tkind and the item table
+    size_t job_off, item_off;  // offsets into slots[tkind] and into the work items
     int njobs, nitems;
 };
 
@@ -1327,7 +1327,7 @@ struct biot_batch_s {
     cudaStream_t stream = nullptr;
     int K = 0, ne = 0, Dmax = 0;
     std::vector<BatchLaunch> launches;            // in issue order
-    std::vector<BatchSlot> slots[3];              // per tkind, parallel to the job tables
+    std::vector<BatchSlot> slots[3];              // per tkind: the recorded sweep of each job
     std::vector<SweepItem> items;
     std::vector<size_t> nops;                     // recorded sweeps per instance and step
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
