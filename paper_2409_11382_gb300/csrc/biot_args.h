@@ -159,6 +159,13 @@ struct StopArgs {
 cudaError_t launch_stop_test(const StopArgs &a, cudaStream_t s);
 
 template <typename T, typename TC> cudaError_t launch_sweep_mom(const SweepArgs<T, TC> &a, cudaStream_t s);
+// n consecutive smoothing sweeps of one small FP64 level (at most
+// SWEEP_CHAIN_MAX x SWEEP_CHAIN_MAX cells) in one launch: sweep k reads the
+// output of sweep k-1 (ping-pong between a.g and a.gout), only the first
+// sweep may start from zero (a.zero_init), the bounce-back history is valid
+// after it.  The result lies in a.g for even n and in a.gout for odd n.
+constexpr int SWEEP_CHAIN_MAX = 8;
+template <typename T, typename TC> cudaError_t launch_sweep_chain(const SweepArgs<T, TC> &a, int n, cudaStream_t s);
 // The jobs of one batched sweep launch, passed as a kernel parameter -- so that,
 // as in a single-instance launch, the arguments sit in constant memory rather
 // than in shared memory and registers.  Job j owns the work items

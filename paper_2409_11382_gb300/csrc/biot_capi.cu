@@ -284,7 +284,7 @@ bool level_lo(const biot_ctx *h, int l, bool cold)
 }
 
 template <typename T, typename TC>
-int sweep_typed(biot_ctx *h, int l, int mode, bool zero_init, bool prolong, bool want_res)
+int sweep_typed(biot_ctx *h, int l, int mode, bool zero_init, bool prolong, bool want_res, int chain)
 {
     Level &Lv = h->lv[l];
     const bool fine = (l == h->L - 1);
@@ -347,24 +347,26 @@ int sweep_typed(biot_ctx *h, int l, int mode, bool zero_init, bool prolong, bool
         }
         CUDA_TRY(cudaEventRecord(h->ev[h->ev_used], h->stream));
     }
-    CUDA_TRY((launch_sweep_mom<T, TC>(a, h->stream)));
+    if (chain > 1) CUDA_TRY((launch_sweep_chain<T, TC>(a, chain, h->stream)));
+    else CUDA_TRY((launch_sweep_mom<T, TC>(a, h->stream)));
     if (timed) {
         CUDA_TRY(cudaEventRecord(h->ev[h->ev_used + 1], h->stream));
         h->ev_used += 2;
     }
     h->launches++;
     Lv.hist_valid = 1;
-    if (mode == SWEEP_SMOOTH) Lv.cur ^= 1;
+    if (mode == SWEEP_SMOOTH && (chain <= 1 || (chain & 1))) Lv.cur ^= 1;
     return BIOT_OK;
 }
 
-int sweep(biot_ctx *h, int l, int mode, bool zero_init, bool prolong, bool want_res)
+// chain > 1: that many smoothing sweeps of a small FP64 level in one launch.
+int sweep(biot_ctx *h, int l, int mode, bool zero_init, bool prolong, bool want_res, int chain = 1)
 {
     const bool t64 = h->lv[l].fp64;
     const bool c64 = (l > 0) ? h->lv[l - 1].fp64 : t64;
-    if (t64) return sweep_typed<double, double>(h, l, mode, zero_init, prolong, want_res);
-    if (c64) return sweep_typed<float, double>(h, l, mode, zero_init, prolong, want_res);
-    return sweep_typed<float, float>(h, l, mode, zero_init, prolong, want_res);
+    if (t64) return sweep_typed<double, double>(h, l, mode, zero_init, prolong, want_res, chain);
+    if (c64) return sweep_typed<float, double>(h, l, mode, zero_init, prolong, want_res, chain);
+    return sweep_typed<float, float>(h, l, mode, zero_init, prolong, want_res, chain);
 }
 
 // ELASTIC_MULTIGRID (Alg. 4) on level l; zero_start: the iterate is zero
@@ -374,6 +376,11 @@ int vcycle(biot_ctx *h, int l, bool zero_start)
     const int K = h->P.K;
     const bool fine = (l == h->L - 1);
     int rc;
+    // the coarsest level's 2K sweeps, when it is a small FP64 level below the
+    // finest, in one launch (a batch records them one by one)
+    const Level &Lv = h->lv[l];
+    if (l == 0 && !fine && !h->rec && Lv.fp64 && Lv.nx <= SWEEP_CHAIN_MAX && Lv.ny <= SWEEP_CHAIN_MAX)
+        return sweep(h, 0, SWEEP_SMOOTH, zero_start, false, false, 2 * K);
     for (int k = 0; k < K; k++)
         if ((rc = sweep(h, l, SWEEP_SMOOTH, zero_start && k == 0, false, false))) return rc;
     if (l > 0) {

@@ -3,6 +3,7 @@
 #pragma once
 #include "field_kernels.cuh"
 #include "sweep_batch.cuh"
+#include "sweep_chain.cuh"
 #include "sweep_mom.cuh"
 
 #define BIOT_SWEEP_MOM(T, TC)                                                                          \
@@ -11,7 +12,10 @@
     template <> cudaError_t biot::launch_sweep_batch<T, TC>(int v, const biot::BatchParams<T, TC> &P,   \
                                                             cudaStream_t s)                            \
     { return biot::launch_sweep_batch_impl<T, TC>(v, P, s); }                                          \
-    template <> int biot::sweep_slots<T, TC>(int v) { return biot::sweep_slots_impl<T, TC>(v); }
+    template <> int biot::sweep_slots<T, TC>(int v) { return biot::sweep_slots_impl<T, TC>(v); }       \
+    template <> cudaError_t biot::launch_sweep_chain<T, TC>(const biot::SweepArgs<T, TC> &a, int n,     \
+                                                            cudaStream_t s)                            \
+    { return biot::launch_sweep_chain_impl<T, TC>(a, n, s); }
 #define BIOT_FIELDS(T)                                                                                 \
     template <> cudaError_t biot::launch_sexp<T>(const biot::SexpArgs<T> &a, cudaStream_t s)             \
     { return biot::launch_sexp_impl<T>(a, s); }                                                        \
