@@ -102,8 +102,10 @@ struct FlowFusedArgs {
     const T *f;           // flow populations, 9 planes
     T *fout;              // streamed populations, 9 planes
     const T *ms;          // m_s plane of the finest elastic state
-    const double *D1, *D2;  // D(t - dt), D(t - 2 dt)
-    double *Dnew;         // D(t) (a third buffer: neighbours still read D1, D2)
+    const double *D1;     // D(t - dt)
+    const T *dBprev;      // D(t - dt) - D(t - 2 dt) as the previous flow step rounded it
+    double *Dnew;         // D(t), into the buffer of D(t - 2 dt) (which no CTA reads)
+    T *dAout;             // D(t) - D(t - dt) rounded, for the next flow step
     const double *src;    // fluid source (dimensional) or nullptr
     const double *fbody;  // body force (2 planes) or nullptr
     T *Ft;                // explicit force of the next step, 2 planes
@@ -226,13 +228,6 @@ template <typename T> cudaError_t launch_flow_fused(const FlowFusedArgs<T> &a, c
 // Batched flow steps: one work item per FLOW_TILE_X x FLOW_TILE_Y tile of an instance (job).
 template <typename T>
 cudaError_t launch_flow_fused_batch(const FlowFusedArgs<T> *jobs, const SweepItem *items, int n, cudaStream_t s);
-// Batched copies of FP64 planes: one work item per 1024 values of a job.
-struct CopyJob {
-    double *dst;
-    const double *src;
-    size_t n;
-};
-cudaError_t launch_copy_batch(const CopyJob *jobs, const SweepItem *items, int n, cudaStream_t s);
 
 // The finest-level state of an FP64 instance narrowed into an FP32 instance:
 // the 8 moment planes rounded to FP32, the first moments m_10, m_01 as

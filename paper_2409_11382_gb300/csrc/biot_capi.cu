@@ -40,12 +40,11 @@ struct SweepJob {
     SweepArgs<float, double> fd;
     SweepArgs<float, float> ff;
 };
-// A flow step prepared for a batched launch, with its history copy.
+// A flow step prepared for a batched launch.
 struct FlowRec {
     int fp64;
     FlowFusedArgs<float> f;
     FlowFusedArgs<double> d;
-    CopyJob copy;
 };
 template <typename T> FlowFusedArgs<T> &flow_args(FlowRec &r);
 template <> FlowFusedArgs<float> &flow_args<float>(FlowRec &r) { return r.f; }
@@ -120,6 +119,7 @@ struct biot_ctx {
     void *f[2]{};
     int fcur = 0;
     double *D1 = nullptr, *D2 = nullptr, *SE = nullptr;
+    void *dB[2] = {nullptr, nullptr};  // D(t - dt) - D(t - 2 dt) as rounded by the last flow step; by flow parity
     void *Ft = nullptr;
     double *src = nullptr, *fbody = nullptr;
     bool has_src = false, has_fbody = false;
@@ -697,8 +697,9 @@ int flow_typed(biot_ctx *h)
     a.fout = static_cast<T *>(h->f[1 - h->fcur]);
     a.ms = static_cast<const T *>(Lf.g[Lf.cur]) + 3 * np;
     a.D1 = h->D1;
-    a.D2 = h->D2;
-    a.Dnew = h->SE;  // scratch: neighbouring CTAs still read D1, D2
+    a.dBprev = static_cast<const T *>(h->dB[h->fcur]);
+    a.Dnew = h->D2;  // D(t - 2 dt) is no longer read: D(t) takes its buffer
+    a.dAout = static_cast<T *>(h->dB[1 - h->fcur]);
     a.src = h->has_src ? h->src : nullptr;
     a.fbody = h->has_fbody ? h->fbody : nullptr;
     a.Ft = static_cast<T *>(h->Ft);
@@ -724,15 +725,12 @@ int flow_typed(biot_ctx *h)
         FlowRec r{};
         r.fp64 = sizeof(T) == 8;
         flow_args<T>(r) = a;
-        r.copy = CopyJob{h->D2, h->SE, np};
         h->frec->push_back(r);
     } else {
         CUDA_TRY(launch_flow_fused<T>(a, h->stream));
         h->launches++;
-        // D(t) into the buffer of D(t - 2 dt), then D1 <- D(t), D2 <- D(t - dt)
-        CUDA_TRY(cudaMemcpyAsync(h->D2, h->SE, np * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
     }
-    std::swap(h->D1, h->D2);
+    std::swap(h->D1, h->D2);  // D1 <- D(t), D2 <- D(t - dt)
     h->ft_fresh = true;   // F~ of the next elastic solve is computed
     h->se_stale = true;   // the s'_exp buffer was used as scratch
     h->fcur ^= 1;
@@ -1002,6 +1000,8 @@ int biot_create(const biot_params *p, const biot_side sides[4], biot_handle *out
     TRY_RC(dev_alloc(h, &h->Ft, 2 * np * tsz));
     TRY_RC(dev_alloc(h, (void **)&h->D1, np * sizeof(double)));
     TRY_RC(dev_alloc(h, (void **)&h->D2, np * sizeof(double)));
+    TRY_RC(dev_alloc(h, &h->dB[0], np * tsz));
+    TRY_RC(dev_alloc(h, &h->dB[1], np * tsz));
     TRY_RC(dev_alloc(h, (void **)&h->SE, np * sizeof(double)));
     TRY_RC(dev_alloc(h, (void **)&h->resmax, 2 * sizeof(unsigned long long)));
     TRY_RC(dev_alloc(h, (void **)&h->stop, sizeof(StopState)));
@@ -1250,7 +1250,7 @@ extern "C" int biot_read_u_noalloc(biot_handle h, double *eta, double *t_out)
 // the outer phases.  Each phase is one work-list launch per storage kind, whose
 // CTAs take strips (or, for levels of at most 64^2 cells and FP64 levels,
 // tiles) of sweeps of different instances; the flow steps of all instances are
-// one work-list launch and one batched copy of the divergence history.
+// one work-list launch.
 // ============================================================================
 namespace {
 
@@ -1342,10 +1342,9 @@ struct biot_batch_s {
     // batched flow steps: per storage type (0 FP32, 1 FP64) the instances and their
     // tile work items; copy work items of the D(t) history update
     std::vector<int> flow_inst[2];
-    std::vector<SweepItem> flow_items[2], copy_items;
+    std::vector<SweepItem> flow_items[2];
     void *flow_dev[2][2] = {};                    // per graph parity, per type: FlowFusedArgs tables
-    CopyJob *copy_dev[2] = {};
-    SweepItem *flow_items_dev[2] = {}, *copy_items_dev = nullptr;
+    SweepItem *flow_items_dev[2] = {};
     long launches_per_step = 0, kernel_launches = 0, nstep = 0;
     std::vector<void *> allocs;
 };
@@ -1429,12 +1428,11 @@ int batch_plan(biot_batch_s *b)
             }
         }
     }
-    // flow steps and history copies: one job per instance
+    // flow steps: one job per instance
     for (int t = 0; t < 2; t++) {
         b->flow_inst[t].clear();
         b->flow_items[t].clear();
     }
-    b->copy_items.clear();
     for (int i = 0; i < n; i++) {
         const biot_ctx *h = b->inst[i];
         const int t = h->fp32 ? 0 : 1;
@@ -1442,22 +1440,17 @@ int batch_plan(biot_batch_s *b)
         b->flow_inst[t].push_back(i);
         for (int by = 0; by < (h->P.ny + FLOW_TILE_Y - 1) / FLOW_TILE_Y; by++)
             for (int bx = 0; bx < (h->P.nx + FLOW_TILE_X - 1) / FLOW_TILE_X; bx++) b->flow_items[t].push_back({job, bx, by, 0});
-        const size_t np = (size_t)h->P.nx * h->P.ny;
-        for (size_t c = 0; c < (np + 1023) / 1024; c++) b->copy_items.push_back({i, (int)c, 0, 0});
     }
     int rc;
     for (int par = 0; par < 2; par++) {
         if ((rc = batch_alloc(b, &b->flow_dev[par][0], b->flow_inst[0].size() * sizeof(FlowFusedArgs<float>)))) return rc;
         if ((rc = batch_alloc(b, &b->flow_dev[par][1], b->flow_inst[1].size() * sizeof(FlowFusedArgs<double>)))) return rc;
-        if ((rc = batch_alloc(b, (void **)&b->copy_dev[par], n * sizeof(CopyJob)))) return rc;
     }
     for (int t = 0; t < 2; t++) {
         if ((rc = batch_alloc(b, (void **)&b->flow_items_dev[t], b->flow_items[t].size() * sizeof(SweepItem)))) return rc;
         if (!b->flow_items[t].empty())
             CUDA_TRY(cudaMemcpy(b->flow_items_dev[t], b->flow_items[t].data(), b->flow_items[t].size() * sizeof(SweepItem), cudaMemcpyHostToDevice));
     }
-    if ((rc = batch_alloc(b, (void **)&b->copy_items_dev, b->copy_items.size() * sizeof(SweepItem)))) return rc;
-    CUDA_TRY(cudaMemcpy(b->copy_items_dev, b->copy_items.data(), b->copy_items.size() * sizeof(SweepItem), cudaMemcpyHostToDevice));
     return BIOT_OK;
 }
 
@@ -1527,7 +1520,7 @@ int batch_capture(biot_batch_s *b, int par)
                 rc = fail(BIOT_ERR_CUDA, "batched schedule: a recorded sweep differs from its planned kind");
         }
     }
-    // flow steps of all instances, then their history copies
+    // flow steps of all instances
     if (!rc && !b->flow_items[0].empty()) {
         cudaError_t e = launch_flow_fused_batch<float>(static_cast<const FlowFusedArgs<float> *>(b->flow_dev[par][0]),
                                                        b->flow_items_dev[0], (int)b->flow_items[0].size(), b->stream);
@@ -1538,11 +1531,6 @@ int batch_capture(biot_batch_s *b, int par)
         cudaError_t e = launch_flow_fused_batch<double>(static_cast<const FlowFusedArgs<double> *>(b->flow_dev[par][1]),
                                                         b->flow_items_dev[1], (int)b->flow_items[1].size(), b->stream);
         if (e != cudaSuccess) rc = fail(BIOT_ERR_CUDA, std::string("batched flow launch: ") + cudaGetErrorString(e));
-        nl++;
-    }
-    if (!rc) {
-        cudaError_t e = launch_copy_batch(b->copy_dev[par], b->copy_items_dev, (int)b->copy_items.size(), b->stream);
-        if (e != cudaSuccess) rc = fail(BIOT_ERR_CUDA, std::string("batched copy launch: ") + cudaGetErrorString(e));
         nl++;
     }
     for (size_t k = 0; k < b->launches.size() && !rc; k++) {
@@ -1573,13 +1561,10 @@ int batch_capture(biot_batch_s *b, int par)
     {
         std::vector<FlowFusedArgs<float>> ff;
         std::vector<FlowFusedArgs<double>> fd;
-        std::vector<CopyJob> cj(n);
         for (int i : b->flow_inst[0]) ff.push_back(frec[i].f);
         for (int i : b->flow_inst[1]) fd.push_back(frec[i].d);
-        for (int i = 0; i < n; i++) cj[i] = frec[i].copy;
         if (!ff.empty()) CUDA_TRY(cudaMemcpy(b->flow_dev[par][0], ff.data(), ff.size() * sizeof(ff[0]), cudaMemcpyHostToDevice));
         if (!fd.empty()) CUDA_TRY(cudaMemcpy(b->flow_dev[par][1], fd.data(), fd.size() * sizeof(fd[0]), cudaMemcpyHostToDevice));
-        CUDA_TRY(cudaMemcpy(b->copy_dev[par], cj.data(), n * sizeof(CopyJob), cudaMemcpyHostToDevice));
     }
     b->launches_per_step = nl;
     b->epoch[par].clear();
@@ -1763,7 +1748,7 @@ size_t estimate_bytes(const biot_params *p, const biot_side *sides)
         for (int s = 0; s < 4; s++)
             if (sides && sides[s].eta_type == BIOT_DIRICHLET) b += 3 * ((s == BIOT_BOTTOM || s == BIOT_TOP) ? nx : ny) * esz;
     }
-    b += (2 * 9 + 2) * np * tsz + 3 * np * 8 + 16 + sizeof(StopState);
+    b += (2 * 9 + 2 + 2) * np * tsz + 3 * np * 8 + 16 + sizeof(StopState);
     for (int s = 0; s < 4; s++) {
         const size_t m = 2 * (size_t)((s == BIOT_BOTTOM || s == BIOT_TOP) ? p->nx : p->ny) + 1;
         if (sides && sides[s].eta_profile) b += 2 * m * 8;
@@ -2205,6 +2190,7 @@ std::vector<CkptPart> ckpt_parts(biot_ctx *h)
     v.push_back({h->Ft, 2 * np * tsz});
     v.push_back({h->D1, np * sizeof(double)});
     v.push_back({h->D2, np * sizeof(double)});
+    v.push_back({h->dB[h->fcur], np * tsz});  // the difference the next flow step reads
     return v;
 }
 

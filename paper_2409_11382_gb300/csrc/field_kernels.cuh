@@ -202,8 +202,9 @@ __device__ __forceinline__ void flow_tile(const FlowFusedArgs<T> &a, int bx, int
         }
         const T msv = a.ms[idx];
         const double dt_ = a.kD * (double)msv;  // D(t)
-        const double d1 = a.D1[idx], d2 = a.D2[idx];
-        const T dA = T(dt_ - d1), dB = T(d1 - d2);  // FP64 differences of the history
+        const double d1 = a.D1[idx];
+        const T dA = T(dt_ - d1);  // FP64 difference of the history
+        const T dB = a.dBprev[idx];  // the same difference one step earlier
         const T s0 = a.src ? T(a.dt * a.src[idx]) : T(0);
         const T sp = s0 - (a.k_a1r * dB + a.k_ar * dA);  // s' of eq. source:implicit
         const T P = sum + T(0.5) * sp, S = sp;
@@ -216,7 +217,10 @@ __device__ __forceinline__ void flow_tile(const FlowFusedArgs<T> &a, int bx, int
         qA[cy][cx] = dA;
         qms[cy][cx] = msv;
         const int gx = x0 - 1 + cx, gy = y0 - 1 + cy;
-        if (cx >= 1 && cx <= FF_TX && cy >= 1 && cy <= FF_TY && gx < nx && gy < ny) a.Dnew[idx] = dt_;
+        if (cx >= 1 && cx <= FF_TX && cy >= 1 && cy <= FF_TY && gx < nx && gy < ny) {
+            a.Dnew[idx] = dt_;
+            a.dAout[idx] = dA;
+        }
     }
     __syncthreads();
     const int tx = tid % FF_TX, ty = tid / FF_TX;

@@ -37,17 +37,6 @@ cudaError_t biot::launch_stop_test(const biot::StopArgs &a, cudaStream_t s)
     return cudaGetLastError();
 }
 
-// Batched plane copies (the D(t) history update of every instance of a batch):
-// CTA b copies chunk items[b].bx of 1024 values of copy jobs[items[b].job].
-__global__ void __launch_bounds__(256) k_copy_batch(const biot::CopyJob *__restrict__ jobs,
-                                                    const biot::SweepItem *__restrict__ items)
-{
-    const biot::SweepItem it = items[blockIdx.x];
-    const biot::CopyJob j = jobs[it.job];
-    const size_t base = (size_t)it.bx * 1024;
-    for (size_t i = base + threadIdx.x; i < base + 1024 && i < j.n; i += 256) j.dst[i] = j.src[i];
-}
-
 // State hand-over from an FP64 instance to an FP32 one (see NarrowArgs).
 __global__ void __launch_bounds__(256) k_narrow_state(const biot::NarrowArgs a)
 {
@@ -71,12 +60,5 @@ cudaError_t biot::launch_narrow_state(const biot::NarrowArgs &a, cudaStream_t s)
     if (a.np == 0) return cudaSuccess;
     const unsigned blocks = (unsigned)((a.np + 255) / 256 < 65536 ? (a.np + 255) / 256 : 65536);
     k_narrow_state<<<blocks, 256, 0, s>>>(a);
-    return cudaGetLastError();
-}
-
-cudaError_t biot::launch_copy_batch(const biot::CopyJob *jobs, const biot::SweepItem *items, int n, cudaStream_t s)
-{
-    if (n <= 0) return cudaSuccess;
-    k_copy_batch<<<n, 256, 0, s>>>(jobs, items);
     return cudaGetLastError();
 }
