@@ -186,6 +186,28 @@ BIOT_API int biot_read_p(biot_handle h, double *p, double *t_out);
  * moments:bared. */
 BIOT_API int biot_read_stress(biot_handle h, double *sigma);
 
+/* Read-out that overlaps later steps.  biot_read_async forms the same fields
+ * as biot_read_u / biot_read_p / biot_read_stress at the current time (each
+ * of eta, p, sigma may be NULL; same layouts) on the instance's stream, then
+ * copies them to the host buffers on a copy stream of its own and returns
+ * without waiting for the copy.  Steps issued afterwards run while it is in
+ * flight: the fields are formed before them in stream order, so they are
+ * those of the time returned in *t_out.
+ * - The host buffers belong to the library until biot_read_wait returns: the
+ *   caller neither reads nor frees them before.  Page-locked buffers (e.g.
+ *   cudaHostAlloc) make the copy asynchronous; pageable ones are accepted, and
+ *   then the copy may block the calling thread.
+ * - At most two reads are in flight; a third waits on the device for the
+ *   oldest one's copy before it overwrites that device staging buffer.  The
+ *   two staging buffers (3 FP64 planes each, 6 with sigma) are allocated at
+ *   the first call and held until biot_destroy.
+ * - Errors: BIOT_ERR_INVALID_ARG (null handle, all three outputs NULL), the
+ *   step errors of a pending solve, BIOT_ERR_OOM, BIOT_ERR_CUDA.
+ * biot_read_wait blocks until every read issued so far has reached the host
+ * (BIOT_OK also when none is in flight). */
+BIOT_API int biot_read_async(biot_handle h, double *eta, double *p, double *sigma, double *t_out);
+BIOT_API int biot_read_wait(biot_handle h);
+
 BIOT_API int biot_stats_get(biot_handle h, biot_stats *out);
 
 /* Static description of an error code, and the last error of this thread. */

@@ -27,7 +27,7 @@ API_FUNCTIONS = (
     "biot_create", "biot_destroy", "biot_set_stream", "biot_set_sources", "biot_set_side_profile",
     "biot_step", "biot_solve_to", "biot_read_u", "biot_read_p", "biot_read_stress",
     "biot_stats_get", "biot_error_string", "biot_last_error", "biot_sweep_timing",
-    "biot_sweep_timing_get", "biot_read_u_noalloc",
+    "biot_sweep_timing_get", "biot_read_u_noalloc", "biot_read_async", "biot_read_wait",
     "biot_batch_create", "biot_batch_destroy", "biot_batch_size", "biot_batch_instance",
     "biot_batch_step", "biot_batch_stats_get",
     "biot_estimate_bytes", "biot_server_create", "biot_server_submit", "biot_server_poll",
@@ -110,6 +110,8 @@ def load_library(path: str = LIB_PATH):
     lib.biot_sweep_timing.argtypes = [H, C.c_int]
     lib.biot_sweep_timing_get.argtypes = [H, P, C.POINTER(C.c_long)]
     lib.biot_read_u_noalloc.argtypes = [H, P, P]
+    lib.biot_read_async.argtypes = [H, P, P, P, P]
+    lib.biot_read_wait.argtypes = [H]
     lib.biot_batch_create.argtypes = [C.c_int, C.POINTER(biot_params), C.POINTER(biot_side), C.POINTER(H)]
     lib.biot_batch_destroy.argtypes = [H]
     lib.biot_batch_size.argtypes = [H, C.POINTER(C.c_int)]
@@ -272,6 +274,27 @@ class Solver:
         t = C.c_double()
         self._check(self._lib.biot_read_p(self._h, _dptr(out), C.byref(t)), "biot_read_p")
         return out, t.value
+
+    def read_async(self, eta: Optional[np.ndarray] = None, p: Optional[np.ndarray] = None,
+                   sigma: Optional[np.ndarray] = None) -> float:
+        """biot_read_async: enqueue the read-out of the given fields into these
+        host arrays and return their time; the arrays are filled once read_wait
+        returns (page-locked arrays make the copy overlap later steps)."""
+        shapes = ((eta, (2, self.ny, self.nx)), (p, (self.ny, self.nx)), (sigma, (3, self.ny, self.nx)))
+        for a, shape in shapes:
+            if a is not None and (a.dtype != np.float64 or a.shape != shape or not a.flags.c_contiguous
+                                  or not a.flags.writeable):
+                raise ValueError(f"read_async needs a writeable C-contiguous float64 array of shape {shape}")
+        t = C.c_double()
+        self._check(self._lib.biot_read_async(self._h, _dptr(eta), _dptr(p), _dptr(sigma), C.byref(t)),
+                    "biot_read_async")
+        self._inflight = getattr(self, "_inflight", []) + [a for a, _ in shapes if a is not None]
+        return t.value
+
+    def read_wait(self):
+        """biot_read_wait: every read_async issued so far has reached its arrays."""
+        self._check(self._lib.biot_read_wait(self._h), "biot_read_wait")
+        self._inflight = []
 
     def read_stress(self, out: Optional[np.ndarray] = None):
         out = np.empty((3, self.ny, self.nx)) if out is None else out

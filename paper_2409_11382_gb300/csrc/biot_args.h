@@ -126,8 +126,12 @@ struct ReadoutArgs {
     const double *D1, *D2, *src;
     double *eta, *p, *sigma;  // outputs (any may be nullptr)
     int perx, pery;
-    double dt, a_over_h, r, lm, mu_hat, coef_fstar, c0, c0h;
+    double dt, a_over_h, r;
     double kD;  // dD/dm_s = -3 / (2 (3 lm + 1)) (host-evaluated)
+    // host-evaluated coefficients: F_* = c_axis (m_s(E) - m_s(W)) + c_diag ((m_s(NE) + m_s(SE))
+    // - (m_s(NW) + m_s(SW))) (and rotated), p = (...) inv_c0, and the stress
+    // sigma_11,22 = c_s m_s +- c_d m_d, sigma_12 = c_11 m_11
+    double c_axis, c_diag, inv_c0, c_s, c_d, c_11;
 };
 
 // Initial populations of eqs. ICs / ICs:moments.

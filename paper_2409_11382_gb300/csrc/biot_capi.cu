@@ -124,6 +124,14 @@ struct biot_ctx {
     double *src = nullptr, *fbody = nullptr;
     bool has_src = false, has_fbody = false;
     double *out = nullptr;  // readout scratch, 6 planes
+    // biot_read_async: two device staging buffers (3 or 6 FP64 planes), a copy
+    // stream, and per buffer the events "fields formed" and "copy done"
+    double *aout[2] = {nullptr, nullptr};
+    int aout_planes[2] = {0, 0};
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t aready[2] = {nullptr, nullptr}, acopied[2] = {nullptr, nullptr};
+    bool ainflight[2] = {false, false};
+    int aslot = 0;
     unsigned long long *resmax = nullptr;      // device [2]
     unsigned long long *resmax_host = nullptr; // pinned [2]
     // device-side stopping test (tolerance mode inside graphs)
@@ -792,12 +800,15 @@ int readout_typed(biot_ctx *h, double *eta, double *p, double *sigma)
     a.dt = h->P.dt;
     a.a_over_h = h->P.alpha / h->h;
     a.r = h->P.r_coupling;
-    a.lm = h->lm;
-    a.mu_hat = h->mu;
-    a.coef_fstar = 0.5 * h->P.alpha * h->P.alpha * h->P.r_coupling;
-    a.c0 = h->P.c0;
-    a.c0h = h->P.c0 * h->h;
     a.kD = -1.5 / (3.0 * h->lm + 1.0);
+    const double coef_fstar = 0.5 * h->P.alpha * h->P.alpha * h->P.r_coupling;  // alpha^2 r / 2
+    a.c_axis = coef_fstar * a.kD / 3.0;
+    a.c_diag = coef_fstar * a.kD / 12.0;
+    a.inv_c0 = 1.0 / h->P.c0;
+    const double lm3 = 3.0 * h->lm, mu6 = 6.0 * h->mu, sc = -0.5 / (h->P.c0 * h->h);
+    a.c_s = sc * lm3 / (lm3 + 1.0);   // mbar_s = 3 lm / (3 lm + 1) m_s
+    a.c_d = sc * mu6 / (mu6 + 1.0);   // mbar_d = 6 mu / (6 mu + 1) m_d, same for m_11
+    a.c_11 = 2.0 * a.c_d;
     CUDA_TRY(launch_readout<T>(a, h->stream));
     h->launches++;
     return BIOT_OK;
@@ -825,6 +836,65 @@ int readout(biot_ctx *h, double *eta_host, double *p_host, double *sigma_host)
     if (p_host) CUDA_TRY(cudaMemcpyAsync(p_host, dp, np * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     if (sigma_host) CUDA_TRY(cudaMemcpyAsync(sigma_host, ds, 3 * np * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     CUDA_TRY(cudaStreamSynchronize(h->stream));
+    return BIOT_OK;
+}
+
+// biot_read_async: fields formed on the instance's stream into staging buffer
+// aslot, copied to the host on the copy stream; the buffer is reused only after
+// its previous copy is done (a device-side wait).
+int read_async(biot_ctx *h, double *eta_host, double *p_host, double *sigma_host)
+{
+    int rc;
+    if ((rc = ensure_initialized(h))) return rc;
+    if (!h->solved) {
+        rc = elastic_solve(h);
+        if (rc && rc != BIOT_ERR_NOT_CONVERGED) return rc;
+    }
+    if ((rc = finish_pending(h))) return rc;
+    if (!h->copy_stream) {
+        CUDA_TRY(cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking));
+        for (int i = 0; i < 2; i++) {
+            CUDA_TRY(cudaEventCreateWithFlags(&h->aready[i], cudaEventDisableTiming));
+            CUDA_TRY(cudaEventCreateWithFlags(&h->acopied[i], cudaEventDisableTiming));
+        }
+    }
+    const int s = h->aslot;
+    const size_t np = (size_t)h->P.nx * h->P.ny;
+    const int planes = sigma_host ? 6 : 3;
+    if (h->aout_planes[s] < planes) {
+        if (h->aout[s]) {  // grow: the buffer's last copy must be done before it is freed
+            CUDA_TRY(cudaEventSynchronize(h->acopied[s]));
+            CUDA_TRY(cudaFree(h->aout[s]));
+            h->bytes -= (size_t)h->aout_planes[s] * np * sizeof(double);
+            h->aout[s] = nullptr;
+            h->aout_planes[s] = 0;
+            h->ainflight[s] = false;
+        }
+        cudaError_t e = cudaMalloc((void **)&h->aout[s], (size_t)planes * np * sizeof(double));
+        if (e != cudaSuccess) {
+            h->aout[s] = nullptr;
+            cudaGetLastError();
+            return fail(e == cudaErrorMemoryAllocation ? BIOT_ERR_OOM : BIOT_ERR_CUDA,
+                        std::string("cudaMalloc (read-out staging): ") + cudaGetErrorString(e));
+        }
+        h->aout_planes[s] = planes;
+        h->bytes += (size_t)planes * np * sizeof(double);
+    }
+    if (h->ainflight[s]) CUDA_TRY(cudaStreamWaitEvent(h->stream, h->acopied[s], 0));
+    double *base = h->aout[s];
+    double *deta = eta_host ? base : nullptr;
+    double *dp = p_host ? base + 2 * np : nullptr;
+    double *ds = sigma_host ? base + 3 * np : nullptr;
+    rc = h->fp32 ? readout_typed<float>(h, deta, dp, ds) : readout_typed<double>(h, deta, dp, ds);
+    if (rc) return rc;
+    CUDA_TRY(cudaEventRecord(h->aready[s], h->stream));
+    CUDA_TRY(cudaStreamWaitEvent(h->copy_stream, h->aready[s], 0));
+    if (eta_host) CUDA_TRY(cudaMemcpyAsync(eta_host, deta, 2 * np * sizeof(double), cudaMemcpyDeviceToHost, h->copy_stream));
+    if (p_host) CUDA_TRY(cudaMemcpyAsync(p_host, dp, np * sizeof(double), cudaMemcpyDeviceToHost, h->copy_stream));
+    if (sigma_host) CUDA_TRY(cudaMemcpyAsync(sigma_host, ds, 3 * np * sizeof(double), cudaMemcpyDeviceToHost, h->copy_stream));
+    CUDA_TRY(cudaEventRecord(h->acopied[s], h->copy_stream));
+    h->ainflight[s] = true;
+    h->aslot = s ^ 1;
     return BIOT_OK;
 }
 
@@ -899,7 +969,14 @@ void release(biot_ctx *h)
 {
     if (!h) return;
     if (h->stream) cudaStreamSynchronize(h->stream);
+    if (h->copy_stream) cudaStreamSynchronize(h->copy_stream);
     drop_graphs(h);
+    for (int i = 0; i < 2; i++) {
+        if (h->aout[i]) cudaFree(h->aout[i]);
+        if (h->aready[i]) cudaEventDestroy(h->aready[i]);
+        if (h->acopied[i]) cudaEventDestroy(h->acopied[i]);
+    }
+    if (h->copy_stream) cudaStreamDestroy(h->copy_stream);
     for (void *p : h->allocs) cudaFree(p);
     h->allocs.clear();
     if (h->resmax_host) cudaFreeHost(h->resmax_host);
@@ -1132,6 +1209,23 @@ int biot_read_stress(biot_handle h, double *sigma)
 {
     if (!h || !sigma) return fail(BIOT_ERR_INVALID_ARG, "null argument");
     return readout(h, nullptr, nullptr, sigma);
+}
+
+int biot_read_async(biot_handle h, double *eta, double *p, double *sigma, double *t_out)
+{
+    if (!h || (!eta && !p && !sigma)) return fail(BIOT_ERR_INVALID_ARG, "null handle or no output");
+    int rc = read_async(h, eta, p, sigma);
+    if (t_out) *t_out = h->P.dt * (double)h->nstep;
+    return rc;
+}
+
+int biot_read_wait(biot_handle h)
+{
+    if (!h) return fail(BIOT_ERR_INVALID_ARG, "null handle");
+    if (!h->copy_stream) return BIOT_OK;
+    CUDA_TRY(cudaStreamSynchronize(h->copy_stream));
+    h->ainflight[0] = h->ainflight[1] = false;
+    return BIOT_OK;
 }
 
 int biot_stats_get(biot_handle h, biot_stats *o)
@@ -1805,8 +1899,9 @@ void server_finish(biot_server_s *S, Request &r, int status, const std::string &
         const size_t np = (size_t)r.P.nx * r.P.ny;
         r.eta.resize(2 * np);
         r.p.resize(np);
-        int rc = biot_read_u(r.h, r.eta.data(), &r.t_result);
-        if (!rc) rc = biot_read_p(r.h, r.p.data(), nullptr);
+        // eta and p of one read-out pass (the fields biot_read_u and biot_read_p return)
+        int rc = readout(r.h, r.eta.data(), r.p.data(), nullptr);
+        r.t_result = r.h->P.dt * (double)r.h->nstep;
         if (rc) {
             status = rc;
             r.error = g_last_error;

@@ -68,14 +68,21 @@ __global__ void __launch_bounds__(256) k_force(const ForceArgs<T> a)
 //   eta = mbar_10,01 with mbar = m + F/2, F = F~ + F_*(g)   (eq. displacement)
 //   sigma = -(1/(2 c0 h)) [[mbar_s+mbar_d, 2 mbar_11], [2 mbar_11, mbar_s-mbar_d]]
 //   p = (sum_i f_i + s'/2) / c0                              (eq. pressure)
+// F_* = (alpha^2 r / 2) grad^c D with D = kD m_s (the D2Q9 central gradient)
+// and s' of the flow step's source (centered coupling, eq. pressure:gradient).
+// Arithmetic in the storage type T, except where the state carries more than T
+// holds: the double-float displacement (high part + (low part + F/2)) and the
+// FP64 divergence history, whose differences are formed in FP64.  On the FP64
+// path everything is FP64.  GB300 runs FP64 at a small fraction of the FP32
+// rate, so the FP32 path keeps FP64 to about a dozen operations per cell.
 // ---------------------------------------------------------------------------
 template <typename T>
-__device__ __forceinline__ double div_at(const ReadoutArgs<T> &a, int x, int y)
+__device__ __forceinline__ T ms_at(const ReadoutArgs<T> &a, int x, int y)
 {
     if (a.perx) x = wrapi(x, a.nx); else x = clampi(x, a.nx);
     if (a.pery) y = wrapi(y, a.ny); else y = clampi(y, a.ny);
     const size_t NP = (size_t)a.nx * a.ny;
-    return a.kD * (double)a.g[3 * NP + (size_t)y * a.nx + x];
+    return a.g[3 * NP + (size_t)y * a.nx + x];
 }
 
 template <typename T>
@@ -85,43 +92,34 @@ __global__ void __launch_bounds__(256) k_readout(const ReadoutArgs<T> a)
     const int y = blockIdx.y * 8 + (threadIdx.x >> 5);
     if (x >= a.nx || y >= a.ny) return;
     const size_t NP = (size_t)a.nx * a.ny, idx = (size_t)y * a.nx + x;
-    double m10 = a.g[idx], m01 = a.g[NP + idx];
-    if (a.glo) {  // low parts of the double-float first moments
-        m10 += (double)a.glo[idx];
-        m01 += (double)a.glo[NP + idx];
-    }
-    const double m11 = a.g[2 * NP + idx], ms = a.g[3 * NP + idx], md = a.g[4 * NP + idx];
+    const T ms = a.g[3 * NP + idx];
     if (a.eta) {
-        const double dE = div_at(a, x + 1, y), dW = div_at(a, x - 1, y);
-        const double dN = div_at(a, x, y + 1), dS = div_at(a, x, y - 1);
-        const double dNE = div_at(a, x + 1, y + 1), dNW = div_at(a, x - 1, y + 1);
-        const double dSE = div_at(a, x + 1, y - 1), dSW = div_at(a, x - 1, y - 1);
-        double Fx = a.coef_fstar * ((dE - dW) / 3.0 + ((dNE + dSE) - (dNW + dSW)) / 12.0);
-        double Fy = a.coef_fstar * ((dN - dS) / 3.0 + ((dNE + dNW) - (dSE + dSW)) / 12.0);
-        Fx += (double)a.Ft[idx];
-        Fy += (double)a.Ft[NP + idx];
-        a.eta[idx] = m10 + 0.5 * Fx;
-        a.eta[NP + idx] = m01 + 0.5 * Fy;
+        const T mE = ms_at(a, x + 1, y), mW = ms_at(a, x - 1, y);
+        const T mN = ms_at(a, x, y + 1), mS = ms_at(a, x, y - 1);
+        const T mNE = ms_at(a, x + 1, y + 1), mNW = ms_at(a, x - 1, y + 1);
+        const T mSE = ms_at(a, x + 1, y - 1), mSW = ms_at(a, x - 1, y - 1);
+        const T ca = T(a.c_axis), cd = T(a.c_diag);
+        const T Fx = a.Ft[idx] + (ca * (mE - mW) + cd * ((mNE + mSE) - (mNW + mSW)));
+        const T Fy = a.Ft[NP + idx] + (ca * (mN - mS) + cd * ((mNE + mNW) - (mSE + mSW)));
+        const T lx = a.glo ? a.glo[idx] : T(0), ly = a.glo ? a.glo[NP + idx] : T(0);
+        a.eta[idx] = (double)a.g[idx] + (double)(lx + T(0.5) * Fx);
+        a.eta[NP + idx] = (double)a.g[NP + idx] + (double)(ly + T(0.5) * Fy);
     }
     if (a.sigma) {
-        const double lm3 = 3.0 * a.lm, mu6 = 6.0 * a.mu_hat;
-        const double mbs = lm3 / (lm3 + 1.0) * ms;
-        const double mbd = mu6 / (mu6 + 1.0) * md;
-        const double mb11 = mu6 / (mu6 + 1.0) * m11;
-        const double sc = -0.5 / a.c0h;
-        a.sigma[idx] = sc * (mbs + mbd);
-        a.sigma[NP + idx] = sc * 2.0 * mb11;
-        a.sigma[2 * NP + idx] = sc * (mbs - mbd);
+        const double m11 = a.g[2 * NP + idx], md = a.g[4 * NP + idx];
+        a.sigma[idx] = a.c_s * (double)ms + a.c_d * md;
+        a.sigma[NP + idx] = a.c_11 * m11;
+        a.sigma[2 * NP + idx] = a.c_s * (double)ms - a.c_d * md;
     }
     if (a.p) {
-        const double dt_ = a.kD * ms;
+        const double dt_ = a.kD * (double)ms;
         const double d1 = a.D1[idx], d2 = a.D2[idx];
-        const double s0 = a.src ? a.dt * a.src[idx] : 0.0;
-        const double sp = s0 - a.a_over_h * ((1.0 - a.r) * (d1 - d2) + a.r * (dt_ - d1));
-        double sum = 0.0;
-#pragma unroll
-        for (int i = 0; i < 9; i++) sum += (double)a.f[i * NP + idx];
-        a.p[idx] = (sum + 0.5 * sp) / a.c0;
+        const T q = T(1.0 - a.r) * T(d1 - d2) + T(a.r) * T(dt_ - d1);
+        const T s0 = a.src ? T(a.dt * a.src[idx]) : T(0);
+        const T sp = s0 - T(a.a_over_h) * q;
+        const T* f = a.f + idx;
+        const T sum = ((f[0] + f[NP]) + (f[2 * NP] + f[3 * NP])) + ((f[4 * NP] + f[5 * NP]) + (f[6 * NP] + f[7 * NP])) + f[8 * NP];
+        a.p[idx] = (double)(sum + T(0.5) * sp) * a.inv_c0;
     }
 }
 
