@@ -274,9 +274,10 @@ BIOT_API int biot_batch_stats_get(biot_batch b, long *kernel_launches, long *lau
 /* ---- serving: continuous batching of solve requests ---------------------------
  * A scheduler thread admits submitted solves in arrival order while the
  * device-memory budget (biot_estimate_bytes per request) and the resident-slot
- * limit allow, keeps each admitted instance resident on its own CUDA stream, and
- * in each tick launches the next time steps of every resident instance before it
- * waits for any, so that their kernels overlap on the GPU.  A finished instance
+ * limit allow, and keeps each admitted instance resident on its own CUDA stream.
+ * It polls those streams without blocking: an instance whose queued work has
+ * completed gets its next four time steps at once, so the residents' kernels
+ * overlap on the GPU and none waits for another.  A finished instance
  * is read out (eta and p at the end time, as biot_read_u / biot_read_p) into host
  * memory and freed at once, which admits the next request.  Every request runs
  * the same kernels as biot_create + biot_solve_to, so its result does not depend
@@ -300,7 +301,7 @@ typedef struct biot_request_info {
 typedef struct biot_server_stats {
     int    queued, peak_resident;
     size_t used_bytes, peak_bytes;
-    long   ticks, graph_launches;
+    long   ticks, graph_launches;  /* ticks: scheduler passes that launched or finished work */
 } biot_server_stats;
 
 /* Device bytes an instance with these parameters holds (allocation plus the

@@ -1342,20 +1342,21 @@ extern "C" int biot_read_u_noalloc(biot_handle h, double *eta, double *t_out)
 // the up-legs start together, so a phase holds one level index of every
 // instance deep enough to have it, and an instance with fewer levels waits in
 // the outer phases.  Each phase is one work-list launch per storage kind, whose
-// CTAs take strips (or, for levels of at most 64^2 cells and FP64 levels,
+// CTAs take strips (or, for levels of at most 128^2 cells and FP64 levels,
 // tiles) of sweeps of different instances; the flow steps of all instances are
 // one work-list launch.
 // ============================================================================
 namespace {
 
-// In a batch, levels of at most this many cells run as tiles (default 64^2;
-// the environment variable BIOT_BATCH_TILE_MAX_CELLS overrides it).
+// In a batch, levels of at most this many cells run as tiles (default 128^2,
+// whose rows would fill only 128 of the 248 columns of two strips; the
+// environment variable BIOT_BATCH_TILE_MAX_CELLS overrides it).
 long batch_tile_max_cells()
 {
     static long v = -1;
     if (v < 0) {
         const char *e = getenv("BIOT_BATCH_TILE_MAX_CELLS");
-        v = e ? atol(e) : 64L * 64L;
+        v = e ? atol(e) : 128L * 128L;
         if (v < 0) v = 0;
     }
     return v;
@@ -1401,6 +1402,36 @@ int level_variant(const biot_ctx *h, int l, int mode)
     return (fine ? 0 : SWEEP_V_COARSE) | (level_lo(h, l, false) ? SWEEP_V_LO : 0) |
            (mode == SWEEP_RESTRICT ? SWEEP_V_RESTRICT : 0) | (h->P.ne_fixed > 0 ? SWEEP_V_NOGHOST : 0) |
            (tile ? SWEEP_V_TILE : 0);
+}
+
+// Strip heights of one batched launch (levels of nx x ny cells): the fewest whole
+// waves of `slots` resident CTAs whose share per level (in proportion to its
+// cells) gives strips of at most sweep_rows_cap() rows.  Each level's strips
+// stay within its share, so the launch's items never spill into a further,
+// almost empty wave.  Heights are even and at least 2.
+std::vector<int> batch_strip_rows(const std::vector<std::pair<int, int>> &dims, int slots)
+{
+    double cells = 0;
+    for (const auto &d : dims) cells += (double)d.first * d.second;
+    const int cap = sweep_rows_cap();
+    std::vector<int> ty(dims.size(), 2);
+    for (int waves = 1; waves <= 64; waves++) {
+        bool ok = true;
+        for (size_t g = 0; g < dims.size(); g++) {
+            const int nx = dims[g].first, ny = dims[g].second;
+            const long sx = (nx + SWEEP_STRIP_COLS - 1) / SWEEP_STRIP_COLS;
+            const long share = (long)((double)waves * slots * ((double)nx * ny) / cells);
+            long nsy = share / sx;
+            if (nsy < 1) nsy = 1;
+            long t = (ny + nsy - 1) / nsy;
+            t += t & 1;
+            if (t < 2) t = 2;
+            ty[g] = (int)t;
+            if (t > cap) ok = false;
+        }
+        if (ok) break;
+    }
+    return ty;
 }
 
 int tkind_slots(int tkind, int variant)
@@ -1487,19 +1518,26 @@ int batch_plan(biot_batch_s *b)
         for (int tk = 0; tk < 3; tk++) {
             for (int v = 0; v < 32; v++) {
                 std::vector<BatchSlot> grp;
-                double cells = 0;
                 for (const BatchSlot &s : bykey[key]) {
                     const biot_ctx *h = b->inst[s.inst];
                     const PlanOp &o = ops[s.inst][s.op];
                     if (level_tkind(h, o.level) != tk || level_variant(h, o.level, o.mode) != v) continue;
                     grp.push_back(s);
-                    cells += (double)h->lv[o.level].np;
                 }
                 if (grp.empty()) continue;
                 const bool tile = (v & SWEEP_V_TILE) != 0;
                 const int slots = tile ? 1 : tkind_slots(tk, v & ~SWEEP_V_TILE);
                 if (!slots) return fail(BIOT_ERR_CUDA, "occupancy query of the batched sweep kernel failed");
                 BatchLaunch L{tk, v, b->slots[tk].size(), b->items.size(), (int)grp.size(), 0};
+                std::vector<int> tys;
+                if (!tile) {
+                    std::vector<std::pair<int, int>> dims;
+                    for (const BatchSlot &s : grp) {
+                        const Level &Lv = b->inst[s.inst]->lv[ops[s.inst][s.op].level];
+                        dims.push_back({Lv.nx, Lv.ny});
+                    }
+                    tys = batch_strip_rows(dims, slots);
+                }
                 for (size_t g = 0; g < grp.size(); g++) {
                     const biot_ctx *h = b->inst[grp[g].inst];
                     const Level &Lv = h->lv[ops[grp[g].inst][grp[g].op].level];
@@ -1508,9 +1546,8 @@ int batch_plan(biot_batch_s *b)
                         sweep_tile_shape(tk == 0, &tx, &ty);
                         for (int by = 0; by < (Lv.ny + ty - 1) / ty; by++)
                             for (int bx = 0; bx < (Lv.nx + tx - 1) / tx; bx++) b->items.push_back({(int)g, bx, by, 0});
-                    } else {  // strips sized so that the launch fills the GPU
-                        const int share = (int)(slots * (double)Lv.np / cells) + 1;
-                        const int ty = sweep_strip_rows(Lv.nx, Lv.ny, share);
+                    } else {  // strips sized so that the launch fills whole waves of the GPU
+                        const int ty = tys[g];
                         const int sx = (Lv.nx + SWEEP_STRIP_COLS - 1) / SWEEP_STRIP_COLS, sy = (Lv.ny + ty - 1) / ty;
                         for (int by = 0; by < sy; by++)
                             for (int bx = 0; bx < sx; bx++) b->items.push_back({(int)g, bx, by, ty});
@@ -1867,6 +1904,7 @@ struct Request {
     std::string error;
     double t_submit = 0, t_start = 0, t_done = 0;
     biot_ctx *h = nullptr;
+    bool inflight = false;  // launched work not yet seen complete on the instance's stream
     std::vector<double> eta, p;
     double t_result = 0;
 };
@@ -1958,6 +1996,7 @@ void server_loop(biot_server_s *S)
                 r->shadow = 0;
             }
             r->h = h;
+            r->inflight = h != nullptr;  // the solve at t = 0 is queued on its stream
             if (rc) {
                 const std::string err = g_last_error;
                 if (h) server_finish(S, *r, rc, err);
@@ -1979,30 +2018,46 @@ void server_loop(biot_server_s *S)
             S->peak_resident = (int)S->resident.size() > S->peak_resident ? (int)S->resident.size() : S->peak_resident;
         }
         if (S->resident.empty()) continue;
-        // one tick: launch a few steps of every resident instance, then wait
-        const int per_tick = 4;
-        std::vector<int> st(S->resident.size(), BIOT_OK);
-        for (size_t k = 0; k < S->resident.size(); k++) {
-            Request &r = *S->resident[k];
-            for (int j = 0; j < per_tick && r.h->nstep < r.target && !st[k]; j++) {
-                const bool graphs = r.h->use_graphs;
-                st[k] = graphs ? advance_graph(r.h) : advance(r.h);
-                if (st[k] == BIOT_ERR_NOT_CONVERGED) st[k] = BIOT_OK;
+        // one pass over the residents: an instance whose stream has drained is
+        // checked (residual read-back, divergence), then finished at its end time
+        // or given its next few steps; the others keep running meanwhile
+        const int per_pass = 4;
+        bool progressed = false;
+        std::vector<Request *> keep;
+        for (Request *rp : S->resident) {
+            Request &r = *rp;
+            const cudaError_t q = r.inflight ? cudaStreamQuery(r.h->stream) : cudaSuccess;
+            if (q == cudaErrorNotReady) {
+                keep.push_back(rp);
+                continue;
+            }
+            progressed = true;
+            int rc = BIOT_OK;
+            if (q != cudaSuccess) {
+                cudaGetLastError();
+                rc = fail(BIOT_ERR_CUDA, std::string("instance stream: ") + cudaGetErrorString(q));
+            }
+            if (!rc) rc = finish_pending(r.h);  // the stream is idle: no wait
+            r.inflight = false;
+            if (!rc && r.h->nstep >= r.target) {
+                server_finish(S, r, BIOT_OK, "");
+                continue;
+            }
+            for (int j = 0; j < per_pass && !rc && r.h->nstep < r.target; j++) {
+                rc = r.h->use_graphs ? advance_graph(r.h) : advance(r.h);
+                if (rc == BIOT_ERR_NOT_CONVERGED) rc = BIOT_OK;
                 S->graph_launches++;
             }
-        }
-        std::vector<Request *> keep;
-        for (size_t k = 0; k < S->resident.size(); k++) {
-            Request &r = *S->resident[k];
-            int rc = st[k];
-            std::string err = rc ? g_last_error : std::string();
-            if (!rc && (rc = finish_pending(r.h))) err = g_last_error;  // synchronises this instance's stream
-            if (rc) server_finish(S, r, rc, err);
-            else if (r.h->nstep >= r.target) server_finish(S, r, BIOT_OK, "");
-            else keep.push_back(&r);
+            if (rc) {
+                server_finish(S, r, rc, g_last_error);
+                continue;
+            }
+            r.inflight = true;
+            keep.push_back(rp);
         }
         S->resident.swap(keep);
-        S->ticks++;
+        if (progressed) S->ticks++;
+        else std::this_thread::sleep_for(std::chrono::microseconds(20));
     }
     // shutdown: drop whatever is resident
     for (Request *r : S->resident) {
