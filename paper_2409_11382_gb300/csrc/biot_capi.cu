@@ -172,15 +172,28 @@ struct biot_ctx {
     // record mode (batched execution): sweeps are appended here instead of launched
     std::vector<biot::SweepJob> *rec = nullptr;
     std::vector<biot::FlowRec> *frec = nullptr;  // record mode: flow steps appended here
+    // Allocation source of a server's instance: the server's stream-ordered
+    // pool, so that freeing the instance synchronises only its own stream
+    // (cudaFree would wait for every resident instance); its two pinned host
+    // mirrors are lent from the server's arena for the same reason.
+    cudaMemPool_t pool = nullptr;
+    bool host_lent = false;
 };
 
 namespace {
+
+// What a server lends an instance it creates (see biot_ctx::pool).
+struct Lend {
+    cudaMemPool_t pool;
+    unsigned long long *resmax_host;  // 2 values
+    StopState *stop_host;
+};
 
 int dev_alloc(biot_ctx *h, void **p, size_t bytes)
 {
     *p = nullptr;
     if (bytes == 0) return BIOT_OK;
-    cudaError_t e = cudaMalloc(p, bytes);
+    cudaError_t e = h->pool ? cudaMallocFromPoolAsync(p, bytes, h->pool, h->stream) : cudaMalloc(p, bytes);
     if (e != cudaSuccess) {
         *p = nullptr;
         cudaGetLastError();
@@ -977,10 +990,17 @@ void release(biot_ctx *h)
         if (h->acopied[i]) cudaEventDestroy(h->acopied[i]);
     }
     if (h->copy_stream) cudaStreamDestroy(h->copy_stream);
-    for (void *p : h->allocs) cudaFree(p);
+    if (h->pool) {  // stream-ordered frees, complete before the server may destroy its pool
+        for (void *p : h->allocs) cudaFreeAsync(p, h->stream);
+        cudaStreamSynchronize(h->stream);
+    } else {
+        for (void *p : h->allocs) cudaFree(p);
+    }
     h->allocs.clear();
-    if (h->resmax_host) cudaFreeHost(h->resmax_host);
-    if (h->stop_host) cudaFreeHost(h->stop_host);
+    if (!h->host_lent) {
+        if (h->resmax_host) cudaFreeHost(h->resmax_host);
+        if (h->stop_host) cudaFreeHost(h->stop_host);
+    }
     if (h->aux_stream) cudaStreamDestroy(h->aux_stream);
     for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
     if (h->own_stream) cudaStreamDestroy(h->own_stream);
@@ -1011,7 +1031,12 @@ const char *biot_error_string(int code)
 
 const char *biot_last_error(void) { return g_last_error.c_str(); }
 
-int biot_create(const biot_params *p, const biot_side sides[4], biot_handle *out)
+}  // extern "C"
+
+namespace {
+
+// biot_create, optionally with a server's pool and pinned mirrors (Lend).
+int create_instance(const biot_params *p, const biot_side sides[4], biot_handle *out, const Lend *lend)
 {
     if (!out) return fail(BIOT_ERR_INVALID_ARG, "null output handle");
     *out = nullptr;
@@ -1046,6 +1071,12 @@ int biot_create(const biot_params *p, const biot_side sides[4], biot_handle *out
         return fail(BIOT_ERR_CUDA, "cudaStreamCreate failed");
     }
     h->stream = h->own_stream;
+    if (lend) {
+        h->pool = lend->pool;
+        h->resmax_host = lend->resmax_host;
+        h->stop_host = lend->stop_host;
+        h->host_lent = true;
+    }
 
 #define TRY_RC(x) do { int _r = (x); if (_r) { release(h); return _r; } } while (0)
     const size_t np = (size_t)p->nx * p->ny;
@@ -1082,8 +1113,8 @@ int biot_create(const biot_params *p, const biot_side sides[4], biot_handle *out
     TRY_RC(dev_alloc(h, (void **)&h->SE, np * sizeof(double)));
     TRY_RC(dev_alloc(h, (void **)&h->resmax, 2 * sizeof(unsigned long long)));
     TRY_RC(dev_alloc(h, (void **)&h->stop, sizeof(StopState)));
-    if (cudaMallocHost((void **)&h->resmax_host, 2 * sizeof(unsigned long long)) != cudaSuccess ||
-        cudaMallocHost((void **)&h->stop_host, sizeof(StopState)) != cudaSuccess) {
+    if (!h->host_lent && (cudaMallocHost((void **)&h->resmax_host, 2 * sizeof(unsigned long long)) != cudaSuccess ||
+                          cudaMallocHost((void **)&h->stop_host, sizeof(StopState)) != cudaSuccess)) {
         cudaGetLastError();
         release(h);
         return fail(BIOT_ERR_OOM, "pinned host allocation failed");
@@ -1099,6 +1130,15 @@ int biot_create(const biot_params *p, const biot_side sides[4], biot_handle *out
 #undef TRY_RC
     *out = h;
     return BIOT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int biot_create(const biot_params *p, const biot_side sides[4], biot_handle *out)
+{
+    return create_instance(p, sides, out, nullptr);
 }
 
 int biot_destroy(biot_handle h)
@@ -1904,6 +1944,7 @@ struct Request {
     std::string error;
     double t_submit = 0, t_start = 0, t_done = 0;
     biot_ctx *h = nullptr;
+    int host_slot = -1;     // the instance's pinned mirrors in the server's arena
     bool inflight = false;  // launched work not yet seen complete on the instance's stream
     std::vector<double> eta, p;
     double t_result = 0;
@@ -1925,6 +1966,13 @@ struct biot_server_s {
     std::chrono::steady_clock::time_point t0;
     long ticks = 0, graph_launches = 0;
     int device = 0;
+    // device memory of the instances (stream-ordered, kept up to the budget) and
+    // their pinned host mirrors, one arena slot per resident instance
+    cudaMemPool_t pool = nullptr;
+    unsigned char *host_arena = nullptr;
+    std::vector<int> free_slots;  // worker thread only
+    static constexpr size_t SLOT_BYTES = 256;
+    static_assert(2 * sizeof(unsigned long long) + sizeof(StopState) <= SLOT_BYTES, "arena slot");
     double now() const { return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count(); }
 };
 
@@ -1949,6 +1997,8 @@ void server_finish(biot_server_s *S, Request &r, int status, const std::string &
     }
     release(r.h);
     r.h = nullptr;
+    if (r.host_slot >= 0) S->free_slots.push_back(r.host_slot);
+    r.host_slot = -1;
     std::lock_guard<std::mutex> lock(S->mu);
     S->used -= r.bytes;
     r.status = status;
@@ -1981,7 +2031,17 @@ void server_loop(biot_server_s *S)
         }
         for (Request *r : admit) {
             biot_handle h = nullptr;
-            int rc = biot_create(&r->P, r->sides, &h);
+            int rc;
+            if (S->host_arena && !S->free_slots.empty()) {
+                r->host_slot = S->free_slots.back();
+                S->free_slots.pop_back();
+                unsigned char *slot = S->host_arena + (size_t)r->host_slot * biot_server_s::SLOT_BYTES;
+                const Lend lend{S->pool, reinterpret_cast<unsigned long long *>(slot),
+                                reinterpret_cast<StopState *>(slot + 2 * sizeof(unsigned long long))};
+                rc = create_instance(&r->P, r->sides, &h, &lend);
+            } else {
+                rc = create_instance(&r->P, r->sides, &h, nullptr);
+            }
             if (!rc) {
                 h->cold64 = r->cold64;
                 rc = ensure_initialized(h);
@@ -2001,6 +2061,8 @@ void server_loop(biot_server_s *S)
                 const std::string err = g_last_error;
                 if (h) server_finish(S, *r, rc, err);
                 else {
+                    if (r->host_slot >= 0) S->free_slots.push_back(r->host_slot);
+                    r->host_slot = -1;
                     std::lock_guard<std::mutex> lock(S->mu);
                     S->used -= r->bytes;
                     r->status = rc;
@@ -2063,6 +2125,8 @@ void server_loop(biot_server_s *S)
     for (Request *r : S->resident) {
         if (r->h) release(r->h);
         r->h = nullptr;
+        if (r->host_slot >= 0) S->free_slots.push_back(r->host_slot);
+        r->host_slot = -1;
     }
     S->resident.clear();
 }
@@ -2096,9 +2160,29 @@ int biot_server_create(size_t mem_budget_bytes, int max_resident, biot_server *o
     S->max_resident = max_resident;
     S->t0 = std::chrono::steady_clock::now();
     cudaGetDevice(&S->device);
+    // the instances' allocation sources; without them instances allocate as biot_create does
+    cudaMemPoolProps props{};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = S->device;
+    if (cudaMemPoolCreate(&S->pool, &props) == cudaSuccess) {
+        uint64_t keep = mem_budget_bytes;  // memory returned by finished instances stays mapped up to the budget
+        cudaMemPoolSetAttribute(S->pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    } else {
+        cudaGetLastError();
+        S->pool = nullptr;
+    }
+    if (cudaMallocHost((void **)&S->host_arena, (size_t)max_resident * biot_server_s::SLOT_BYTES) == cudaSuccess) {
+        for (int i = max_resident - 1; i >= 0; i--) S->free_slots.push_back(i);
+    } else {
+        cudaGetLastError();
+        S->host_arena = nullptr;
+    }
     try {
         S->worker = std::thread(server_loop, S);
     } catch (...) {
+        if (S->pool) cudaMemPoolDestroy(S->pool);
+        if (S->host_arena) cudaFreeHost(S->host_arena);
         delete S;
         return fail(BIOT_ERR_OOM, "cannot start the scheduler thread");
     }
@@ -2236,6 +2320,9 @@ int biot_server_destroy(biot_server S)
         S->cv_work.notify_all();
     }
     if (S->worker.joinable()) S->worker.join();
+    // every instance is released (its frees completed on its stream)
+    if (S->pool) cudaMemPoolDestroy(S->pool);
+    if (S->host_arena) cudaFreeHost(S->host_arena);
     delete S;
     return BIOT_OK;
 }
