@@ -162,8 +162,10 @@ BIOT_API int biot_set_sources(biot_handle h, const double *f_body, const double 
 
 /* Replace the boundary data of one side (same layout as biot_side; the types
  * are fixed at creation).  NULL sets zero data.  The data act from the next
- * elastic solve on (the next biot_step); the current state keeps the data it
- * was solved with. */
+ * elastic solve on (the next step queued after this call); the current state
+ * keeps the data it was solved with.  The arrays are copied into page-locked
+ * staging before the call returns; the upload runs after the steps already
+ * queued, without waiting for them. */
 BIOT_API int biot_set_side_profile(biot_handle h, int side, const double *eta_profile, const double *p_profile);
 
 /* Run n iterations of the time loop of Alg. 5 (elastic solve at t, flow step
@@ -172,6 +174,20 @@ BIOT_API int biot_set_side_profile(biot_handle h, int side, const double *eta_pr
  * BIOT_ERR_NOT_CONVERGED (a step hit ne_max; the state is kept) or
  * BIOT_ERR_DIVERGED (the state is no longer meaningful). */
 BIOT_API int biot_step(biot_handle h, int n);
+
+/* Pipelined stepping.  biot_step_async queues the same n steps as biot_step
+ * on the instance's stream and returns without waiting for them (BIOT_OK, or
+ * an error found while queueing them).  biot_sync waits for everything queued
+ * on the instance -- steps and biot_read_async copies -- and reports the steps
+ * queued since the last report: BIOT_OK, BIOT_ERR_NOT_CONVERGED or
+ * BIOT_ERR_DIVERGED, as biot_step would have.  biot_set_side_profile and
+ * biot_read_async do not wait for queued steps either, so a loop of
+ * set_side_profile / step_async / read_async keeps the GPU busy while the host
+ * prepares the next step.  In tolerance mode without CUDA graphs the V-cycle
+ * loop needs the host after every V-cycle, and biot_step_async then runs as
+ * biot_step. */
+BIOT_API int biot_step_async(biot_handle h, int n);
+BIOT_API int biot_sync(biot_handle h);
 
 /* Step until t = round(T/dt)*dt (T not before the current time). */
 BIOT_API int biot_solve_to(biot_handle h, double T);
@@ -267,9 +283,21 @@ BIOT_API int biot_batch_size(biot_batch b, int *count);
 BIOT_API int biot_batch_instance(biot_batch b, int i, biot_handle *out);
 /* n physical steps of every instance (plus the trailing elastic solve, as biot_step). */
 BIOT_API int biot_batch_step(biot_batch b, int n);
+/* As biot_step_async / biot_sync, for every instance of the batch. */
+BIOT_API int biot_batch_step_async(biot_batch b, int n);
+BIOT_API int biot_batch_sync(biot_batch b);
 /* Kernel launches since creation, per captured step, and strip work items per step. */
 BIOT_API int biot_batch_stats_get(biot_batch b, long *kernel_launches, long *launches_per_step,
                                   long *work_items_per_step);
+/* biot_read_async for every instance of the batch in one call: eta[i], p[i],
+ * sigma[i] are instance i's host buffers (an array may be NULL, and so may an
+ * entry, which skips that field of that instance); t_out, if not NULL, receives
+ * count times.  The same ownership rules as biot_read_async; the reads of
+ * earlier instances stay issued when a later one fails.  biot_batch_read_wait
+ * waits for every instance's reads. */
+BIOT_API int biot_batch_read_async(biot_batch b, double *const *eta, double *const *p, double *const *sigma,
+                                   double *t_out);
+BIOT_API int biot_batch_read_wait(biot_batch b);
 
 /* ---- serving: continuous batching of solve requests ---------------------------
  * A scheduler thread admits submitted solves in arrival order while the

@@ -28,8 +28,9 @@ API_FUNCTIONS = (
     "biot_step", "biot_solve_to", "biot_read_u", "biot_read_p", "biot_read_stress",
     "biot_stats_get", "biot_error_string", "biot_last_error", "biot_sweep_timing",
     "biot_sweep_timing_get", "biot_read_u_noalloc", "biot_read_async", "biot_read_wait",
+    "biot_step_async", "biot_sync", "biot_batch_step_async", "biot_batch_sync",
     "biot_batch_create", "biot_batch_destroy", "biot_batch_size", "biot_batch_instance",
-    "biot_batch_step", "biot_batch_stats_get",
+    "biot_batch_step", "biot_batch_stats_get", "biot_batch_read_async", "biot_batch_read_wait",
     "biot_estimate_bytes", "biot_server_create", "biot_server_submit", "biot_server_poll",
     "biot_server_wait", "biot_server_fetch", "biot_server_release", "biot_server_stats_get",
     "biot_server_destroy", "biot_autotune", "biot_checkpoint_size", "biot_save", "biot_load",
@@ -112,12 +113,19 @@ def load_library(path: str = LIB_PATH):
     lib.biot_read_u_noalloc.argtypes = [H, P, P]
     lib.biot_read_async.argtypes = [H, P, P, P, P]
     lib.biot_read_wait.argtypes = [H]
+    lib.biot_step_async.argtypes = [H, C.c_int]
+    lib.biot_sync.argtypes = [H]
+    lib.biot_batch_step_async.argtypes = [H, C.c_int]
+    lib.biot_batch_sync.argtypes = [H]
     lib.biot_batch_create.argtypes = [C.c_int, C.POINTER(biot_params), C.POINTER(biot_side), C.POINTER(H)]
     lib.biot_batch_destroy.argtypes = [H]
     lib.biot_batch_size.argtypes = [H, C.POINTER(C.c_int)]
     lib.biot_batch_instance.argtypes = [H, C.c_int, C.POINTER(H)]
     lib.biot_batch_step.argtypes = [H, C.c_int]
     lib.biot_batch_stats_get.argtypes = [H, C.POINTER(C.c_long), C.POINTER(C.c_long), C.POINTER(C.c_long)]
+    PP = C.POINTER(C.POINTER(C.c_double))
+    lib.biot_batch_read_async.argtypes = [H, PP, PP, PP, P]
+    lib.biot_batch_read_wait.argtypes = [H]
     lib.biot_autotune.argtypes = [H, C.POINTER(C.c_int), P, C.c_int]
     lib.biot_checkpoint_size.argtypes = [H, C.POINTER(C.c_size_t)]
     lib.biot_save.argtypes = [H, C.c_void_p, C.c_size_t]
@@ -251,6 +259,17 @@ class Solver:
         allow = (OK, ERR_NOT_CONVERGED) if allow_not_converged else (OK,)
         return self._check(self._lib.biot_step(self._h, int(n)), "biot_step", allow)
 
+    def step_async(self, n: int = 1):
+        """biot_step_async: queue n steps and return without waiting for them."""
+        self._check(self._lib.biot_step_async(self._h, int(n)), "biot_step_async")
+
+    def sync(self, allow_not_converged: bool = True) -> int:
+        """biot_sync: wait for the queued steps and reads; their status."""
+        allow = (OK, ERR_NOT_CONVERGED) if allow_not_converged else (OK,)
+        code = self._check(self._lib.biot_sync(self._h), "biot_sync", allow)
+        self._inflight = []
+        return code
+
     def solve_to(self, T: float, allow_not_converged: bool = True) -> int:
         allow = (OK, ERR_NOT_CONVERGED) if allow_not_converged else (OK,)
         return self._check(self._lib.biot_solve_to(self._h, float(T)), "biot_solve_to", allow)
@@ -377,6 +396,53 @@ class Batch:
         if code not in (OK, ERR_NOT_CONVERGED):
             raise BiotError(code, "biot_batch_step", self._lib.biot_last_error().decode(errors="replace"))
         return code
+
+    def step_async(self, n: int = 1):
+        """biot_batch_step_async: queue n steps of every instance without waiting."""
+        code = self._lib.biot_batch_step_async(self._h, int(n))
+        if code != OK:
+            raise BiotError(code, "biot_batch_step_async", self._lib.biot_last_error().decode(errors="replace"))
+
+    def sync(self) -> int:
+        """biot_batch_sync: wait for every instance's queued steps and reads."""
+        code = self._lib.biot_batch_sync(self._h)
+        if code not in (OK, ERR_NOT_CONVERGED):
+            raise BiotError(code, "biot_batch_sync", self._lib.biot_last_error().decode(errors="replace"))
+        self._inflight = []
+        for v in self._views:
+            v._inflight = []
+        return code
+
+    def read_async(self, eta=None, p=None, sigma=None):
+        """biot_batch_read_async: per instance i, eta[i] / p[i] / sigma[i] are its
+        host arrays (a list or an entry may be None); returns the instances'
+        times.  The arrays are filled once read_wait returns."""
+        n = len(self._views)
+        lists = []
+        for arrs, comps in ((eta, 2), (p, 1), (sigma, 3)):
+            if arrs is None:
+                lists.append(None)
+                continue
+            if len(arrs) != n:
+                raise ValueError(f"need one entry per instance ({n})")
+            for v, a in zip(self._views, arrs):
+                shape = (v.ny, v.nx) if comps == 1 else (comps, v.ny, v.nx)
+                if a is not None and (a.dtype != np.float64 or a.shape != shape or not a.flags.c_contiguous
+                                      or not a.flags.writeable):
+                    raise ValueError(f"read_async needs writeable C-contiguous float64 arrays of shape {shape}")
+            lists.append((C.POINTER(C.c_double) * n)(*[_dptr(a) for a in arrs]))
+        t = np.zeros(n)
+        code = self._lib.biot_batch_read_async(self._h, *lists, _dptr(t))
+        if code != OK:
+            raise BiotError(code, "biot_batch_read_async", self._lib.biot_last_error().decode(errors="replace"))
+        self._inflight = getattr(self, "_inflight", []) + [x for x in (eta, p, sigma) if x is not None]
+        return t
+
+    def read_wait(self):
+        code = self._lib.biot_batch_read_wait(self._h)
+        if code != OK:
+            raise BiotError(code, "biot_batch_read_wait", self._lib.biot_last_error().decode(errors="replace"))
+        self._inflight = []
 
     def stats(self) -> dict:
         a, b, c = C.c_long(), C.c_long(), C.c_long()

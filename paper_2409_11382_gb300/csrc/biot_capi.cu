@@ -112,6 +112,13 @@ struct biot_ctx {
     biot_params P{};
     int bc_eta[4]{}, bc_p[4]{};
     double *eta_prof[4]{}, *p_prof[4]{};  // device copies of the boundary data (finest level)
+    // biot_set_side_profile stages the caller's data in page-locked memory and
+    // uploads it in stream order: two slots per side, each reused once its
+    // previous upload has run (an event), so the call never waits for the steps
+    double *prof_stage[4][2] = {};
+    cudaEvent_t prof_ev[4][2] = {};
+    int prof_slot[4] = {};
+    int notconv_reported = 0;  // notconv_steps when biot_step / biot_sync last reported
     double h = 0, lam = 0, mu = 0, kap = 0, omega = 0, om_s = 0, om_d = 0, lm = 0;
     int L = 0;
     bool fp32 = false;  // FP32 state (finest and middle levels)
@@ -268,6 +275,49 @@ int set_profiles(biot_ctx *h, int side, const double *eta, const double *p)
     }
     // Host sources may be pageable and reused by the caller after return.
     CUDA_TRY(cudaStreamSynchronize(h->stream));
+    return BIOT_OK;
+}
+
+// As set_profiles, without waiting for the stream: the caller's data is copied
+// into a page-locked staging slot on the host, and the upload from there runs
+// in stream order after the steps already queued.
+int set_profiles_staged(biot_ctx *h, int side, const double *eta, const double *p)
+{
+    const size_t m = 2 * (size_t)side_cells(h, side) + 1;
+    const int k = h->prof_slot[side];
+    double *&st = h->prof_stage[side][k];
+    if (!st) {
+        if (cudaMallocHost((void **)&st, 3 * m * sizeof(double)) != cudaSuccess) {
+            cudaGetLastError();
+            st = nullptr;
+            return fail(BIOT_ERR_OOM, "pinned host allocation failed (profile staging)");
+        }
+        CUDA_TRY(cudaEventCreateWithFlags(&h->prof_ev[side][k], cudaEventDisableTiming));
+    } else {
+        CUDA_TRY(cudaEventSynchronize(h->prof_ev[side][k]));  // the upload that last used this slot has run
+    }
+    if (eta) {
+        if (!h->eta_prof[side]) {
+            int rc = dev_alloc(h, (void **)&h->eta_prof[side], 2 * m * sizeof(double));
+            if (rc) return rc;
+        }
+        std::memcpy(st, eta, 2 * m * sizeof(double));
+        CUDA_TRY(cudaMemcpyAsync(h->eta_prof[side], st, 2 * m * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    } else if (h->eta_prof[side]) {
+        CUDA_TRY(cudaMemsetAsync(h->eta_prof[side], 0, 2 * m * sizeof(double), h->stream));
+    }
+    if (p) {
+        if (!h->p_prof[side]) {
+            int rc = dev_alloc(h, (void **)&h->p_prof[side], m * sizeof(double));
+            if (rc) return rc;
+        }
+        std::memcpy(st + 2 * m, p, m * sizeof(double));
+        CUDA_TRY(cudaMemcpyAsync(h->p_prof[side], st + 2 * m, m * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    } else if (h->p_prof[side]) {
+        CUDA_TRY(cudaMemsetAsync(h->p_prof[side], 0, m * sizeof(double), h->stream));
+    }
+    CUDA_TRY(cudaEventRecord(h->prof_ev[side][k], h->stream));
+    h->prof_slot[side] = k ^ 1;
     return BIOT_OK;
 }
 
@@ -863,7 +913,8 @@ int read_async(biot_ctx *h, double *eta_host, double *p_host, double *sigma_host
         rc = elastic_solve(h);
         if (rc && rc != BIOT_ERR_NOT_CONVERGED) return rc;
     }
-    if ((rc = finish_pending(h))) return rc;
+    // steps still queued keep their residual check pending: the read-out runs
+    // after them in stream order, and the next synchronising call reports them
     if (!h->copy_stream) {
         CUDA_TRY(cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking));
         for (int i = 0; i < 2; i++) {
@@ -1001,6 +1052,11 @@ void release(biot_ctx *h)
         if (h->resmax_host) cudaFreeHost(h->resmax_host);
         if (h->stop_host) cudaFreeHost(h->stop_host);
     }
+    for (int side = 0; side < 4; side++)
+        for (int k = 0; k < 2; k++) {
+            if (h->prof_stage[side][k]) cudaFreeHost(h->prof_stage[side][k]);
+            if (h->prof_ev[side][k]) cudaEventDestroy(h->prof_ev[side][k]);
+        }
     if (h->aux_stream) cudaStreamDestroy(h->aux_stream);
     for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
     if (h->own_stream) cudaStreamDestroy(h->own_stream);
@@ -1186,7 +1242,7 @@ int biot_set_side_profile(biot_handle h, int side, const double *eta_profile, co
 {
     if (!h || side < 0 || side > 3) return fail(BIOT_ERR_INVALID_ARG, "bad handle or side");
     const double *e0 = h->eta_prof[side], *p0 = h->p_prof[side];
-    int rc = set_profiles(h, side, eta_profile, p_profile);
+    int rc = set_profiles_staged(h, side, eta_profile, p_profile);
     if (rc) return rc;
     // captured launches read the profile buffers when they run; only a newly
     // allocated buffer makes them stale
@@ -1218,7 +1274,45 @@ int biot_step(biot_handle h, int n)
     }
     if ((rc = finish_pending(h))) return rc;
     if (h->notconv_steps > notconv0) status = BIOT_ERR_NOT_CONVERGED;
+    h->notconv_reported = h->notconv_steps;
     return status;
+}
+
+int biot_step_async(biot_handle h, int n)
+{
+    if (!h || n < 0) return fail(BIOT_ERR_INVALID_ARG, "bad handle or step count");
+    if (h->diverged) return fail(BIOT_ERR_DIVERGED, "instance has diverged");
+    const bool graphs = h->use_graphs && !h->timing;
+    if (!graphs && h->P.ne_fixed <= 0) {  // host-driven V-cycle loop: reads back after every step
+        const int rc = biot_step(h, n);
+        return rc == BIOT_ERR_NOT_CONVERGED ? BIOT_OK : rc;
+    }
+    int rc;
+    if ((rc = ensure_initialized(h))) return rc;
+    if (!h->solved) {
+        rc = elastic_solve(h);
+        if (rc && rc != BIOT_ERR_NOT_CONVERGED) return rc;
+    }
+    for (int i = 0; i < n; i++) {
+        rc = graphs ? advance_graph(h) : advance(h);
+        if (rc && rc != BIOT_ERR_NOT_CONVERGED) return rc;
+    }
+    return BIOT_OK;
+}
+
+int biot_sync(biot_handle h)
+{
+    if (!h) return fail(BIOT_ERR_INVALID_ARG, "null handle");
+    CUDA_TRY(cudaStreamSynchronize(h->stream));
+    if (h->copy_stream) {
+        CUDA_TRY(cudaStreamSynchronize(h->copy_stream));
+        h->ainflight[0] = h->ainflight[1] = false;
+    }
+    const int rc = finish_pending(h);
+    if (rc) return rc;
+    const bool nc = h->notconv_steps > h->notconv_reported;
+    h->notconv_reported = h->notconv_steps;
+    return nc ? BIOT_ERR_NOT_CONVERGED : BIOT_OK;
 }
 
 int biot_solve_to(biot_handle h, double T)
@@ -1505,7 +1599,7 @@ struct biot_batch_s {
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     std::vector<long> epoch[2];                   // instance epochs the graphs were captured at
     // batched flow steps: per storage type (0 FP32, 1 FP64) the instances and their
-    // tile work items; copy work items of the D(t) history update
+    // tile work items
     std::vector<int> flow_inst[2];
     std::vector<SweepItem> flow_items[2];
     void *flow_dev[2][2] = {};                    // per graph parity, per type: FlowFusedArgs tables
@@ -1835,6 +1929,21 @@ int biot_batch_instance(biot_batch b, int i, biot_handle *out)
 
 int biot_batch_step(biot_batch b, int n)
 {
+    int rc = biot_batch_step_async(b, n);
+    return rc ? rc : biot_batch_sync(b);
+}
+
+int biot_batch_sync(biot_batch b)
+{
+    if (!b) return fail(BIOT_ERR_INVALID_ARG, "null batch");
+    int status = BIOT_OK, rc;
+    for (biot_ctx *h : b->inst)
+        if ((rc = biot_sync(h)) && status != BIOT_ERR_DIVERGED && status != BIOT_ERR_CUDA) status = rc;
+    return status;
+}
+
+int biot_batch_step_async(biot_batch b, int n)
+{
     if (!b || n < 0) return fail(BIOT_ERR_INVALID_ARG, "bad batch or step count");
     int rc;
     for (biot_ctx *h : b->inst) {
@@ -1874,10 +1983,7 @@ int biot_batch_step(biot_batch b, int n)
             h->pending_res = true;
         }
     }
-    int status = BIOT_OK;
-    for (biot_ctx *h : b->inst)
-        if ((rc = finish_pending(h))) status = rc;
-    return status;
+    return BIOT_OK;
 }
 
 int biot_batch_stats_get(biot_batch b, long *kernel_launches, long *launches_per_step, long *work_items_per_step)
@@ -1886,6 +1992,29 @@ int biot_batch_stats_get(biot_batch b, long *kernel_launches, long *launches_per
     if (kernel_launches) *kernel_launches = b->kernel_launches;
     if (launches_per_step) *launches_per_step = b->launches_per_step;
     if (work_items_per_step) *work_items_per_step = (long)b->items.size();
+    return BIOT_OK;
+}
+
+int biot_batch_read_async(biot_batch b, double *const *eta, double *const *p, double *const *sigma, double *t_out)
+{
+    if (!b || (!eta && !p && !sigma)) return fail(BIOT_ERR_INVALID_ARG, "null batch or no output");
+    for (size_t i = 0; i < b->inst.size(); i++) {
+        double *e = eta ? eta[i] : nullptr, *q = p ? p[i] : nullptr, *sg = sigma ? sigma[i] : nullptr;
+        if (!e && !q && !sg) continue;
+        const int rc = read_async(b->inst[i], e, q, sg);
+        if (rc) return rc;
+        if (t_out) t_out[i] = b->inst[i]->P.dt * (double)b->inst[i]->nstep;
+    }
+    return BIOT_OK;
+}
+
+int biot_batch_read_wait(biot_batch b)
+{
+    if (!b) return fail(BIOT_ERR_INVALID_ARG, "null batch");
+    for (biot_ctx *h : b->inst) {
+        const int rc = biot_read_wait(h);
+        if (rc) return rc;
+    }
     return BIOT_OK;
 }
 

@@ -101,3 +101,22 @@ def test_bad_calls_are_rejected():
         with pytest.raises(ValueError):
             s.read_async(p=np.zeros((16, 8)))
         s.read_wait()                        # no read issued yet
+
+
+def test_batch_read_async_equals_instance_reads():
+    probs = W.batched_instances(count=4, seed=5)
+    with biot.Batch(probs) as b:
+        b.step(1)
+        etas = [pinned((2, p["ny"], p["nx"])) for p, _ in probs]
+        ps = [pinned((p["ny"], p["nx"])) for p, _ in probs]
+        ps[2] = None                         # skip one field of one instance
+        t = b.read_async(eta=etas, p=ps)
+        b.step(1)                            # runs while the copies are in flight
+        b.read_wait()
+        assert np.array_equal(t, [p["dt"] for p, _ in probs])  # one step taken before the read
+        with biot.Batch(probs) as ref:
+            ref.step(1)
+            for i in range(len(ref)):
+                assert np.array_equal(etas[i], ref[i].read_u()[0])
+                if ps[i] is not None:
+                    assert np.array_equal(ps[i], ref[i].read_p()[0])
