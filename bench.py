@@ -344,9 +344,10 @@ def run_ours(args):
     pin_p = [pin((ny, nx)) for _ in range(2)]
     pin_prof, pin_pprof = pin((2, 2 * nx + 1)), pin((2 * nx + 1,))
     pin_prof[1] = -load
-    for k in range(2):  # the read-out's staging buffers are allocated outside the timed region
+    for k in range(2):  # the read-out's and the profile upload's staging buffers: set up untimed
         solver.read_async(eta=pin_eta[k], p=pin_p[k])
-    solver.read_wait()
+        solver.set_side_profile(W.TOP, pin_prof, pin_pprof)
+    solver.sync()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for k in range(e2e_steps):
@@ -513,9 +514,11 @@ def run_batched(args):
             for _ in range(2)]
     etas = [[eta for eta, _ in o] for o in outs]
     prs = [[pr for _, pr in o] for o in outs]
-    for k in range(2):  # staging buffers allocated outside the timed region
+    for k in range(2):  # read-out and profile staging buffers set up outside the timed region
         b.read_async(eta=etas[k], p=prs[k])
-    b.read_wait()
+        for v, (ep, pp) in zip(views, profs):
+            v.set_side_profile(W.TOP, ep, pp)
+    b.sync()
     torch.cuda.synchronize()
     t1 = time.perf_counter()
     for k in range(e2e_steps):
