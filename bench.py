@@ -344,9 +344,10 @@ def run_ours(args):
     pin_p = [pin((ny, nx)) for _ in range(2)]
     pin_prof, pin_pprof = pin((2, 2 * nx + 1)), pin((2 * nx + 1,))
     pin_prof[1] = -load
-    for k in range(2):  # the read-out's and the profile upload's staging buffers: set up untimed
-        solver.read_async(eta=pin_eta[k], p=pin_p[k])
+    for k in range(2):  # two untimed iterations: staging buffers, graphs of both flow parities
         solver.set_side_profile(W.TOP, pin_prof, pin_pprof)
+        solver.step_async(1)
+        solver.read_async(eta=pin_eta[k], p=pin_p[k])
     solver.sync()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -514,10 +515,11 @@ def run_batched(args):
             for _ in range(2)]
     etas = [[eta for eta, _ in o] for o in outs]
     prs = [[pr for _, pr in o] for o in outs]
-    for k in range(2):  # read-out and profile staging buffers set up outside the timed region
-        b.read_async(eta=etas[k], p=prs[k])
+    for k in range(2):  # two untimed iterations: staging buffers, graphs of both flow parities
         for v, (ep, pp) in zip(views, profs):
             v.set_side_profile(W.TOP, ep, pp)
+        b.step_async(1)
+        b.read_async(eta=etas[k], p=prs[k])
     b.sync()
     torch.cuda.synchronize()
     t1 = time.perf_counter()
@@ -532,7 +534,7 @@ def run_batched(args):
     h2d = sum(ep.nbytes + pp.nbytes for ep, pp in profs)
     d2h = e2e_steps * sum(eta.nbytes + pr.nbytes for eta, pr in outs[0])
     e2e_finite = bool(all(np.isfinite(a).all() for o in outs for pair in o for a in pair))
-    total_steps = args.warmup + args.steps + e2e_steps
+    total_steps = args.warmup + args.steps + 2 + e2e_steps
     small = sorted(range(len(probs)), key=lambda i: probs[i][0]["nx"])[:2]
     got = {i: (b[i].read_u()[0], b[i].read_p()[0]) for i in small}
     b.close()
