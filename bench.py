@@ -87,19 +87,21 @@ def step_model(params, n, fp64):
       finest residual + restriction: the same inputs, 5 coarse moments per 4 cells out;
       coarse smoothing: 5 moments and 5 of r in, 5 moments out (+ prolongation);
       coarse residual + restriction: 10 in, 5 coarse out per 4 cells;
-      coarsest level (FP64): as coarse smoothing;
-      flow step: 9 f in and out, m_s in, two FP64 history planes in, D(t) and F~
-        out, and the copy of D(t) into the history.
+      coarsest level: as coarse smoothing (FP32 on the FP32 path, FP64 with
+        BIOT_COARSEST_FP64=1);
+      flow step: 9 f in and out, m_s, D(t - dt) (FP64) and the previous history
+        difference in, D(t) (FP64), the new difference and F~ out.
     Returns (cell-sweeps per step, bytes per step)."""
     L, K, ne = params["levels"], params["K"], params["ne_fixed"]
     esz = 8 if fp64 else 4
+    c64 = os.environ.get("BIOT_COARSEST_FP64", "0") == "1"  # as the library reads it
     cell_sweeps = 0.0
     nbytes = 0.0
     for l in range(L - 1, -1, -1):  # finest first
         side = n >> (L - 1 - l)
         c = float(side * side)
-        e = 8 if (l == 0 and L > 1) or fp64 else esz
-        ec = 8 if (l == 1 and L > 1) or fp64 else esz  # storage of the next coarser level
+        e = 8 if (l == 0 and L > 1 and c64) or fp64 else esz
+        ec = 8 if (l == 1 and L > 1 and c64) or fp64 else esz  # storage of the next coarser level
         fine = l == L - 1
         nlo = 2 if (fine and not fp64) else 0
         xin = 2 if fine else 5  # F~ or r
@@ -112,7 +114,7 @@ def step_model(params, n, fp64):
             nbytes += ne * c * ((5 + nlo + xin) * e + 5 * ec / 4.0)
     fine_cells = float(n * n)
     fe = 8 if fp64 else 4
-    nbytes += fine_cells * (9 * fe * 2 + fe + 16 + 8 + 2 * fe + 16)
+    nbytes += fine_cells * (9 * fe * 2 + fe + 8 + fe + 8 + fe + 2 * fe)
     return cell_sweeps, nbytes
 
 

@@ -93,6 +93,20 @@ int coarse_lo_mode()
     return v;
 }
 
+// Precision of the coarsest level of the FP32 path: FP32 like the other coarse
+// levels (default; its corrections are the smoothest error components, and the
+// solve from a zero iterate has the FP64 cold start or double-float coarse
+// levels), or FP64 with BIOT_COARSEST_FP64=1, for comparisons.
+bool coarsest_fp64()
+{
+    static int v = -1;
+    if (v < 0) {
+        const char *e = getenv("BIOT_COARSEST_FP64");
+        v = (e && e[0] == '1') ? 1 : 0;
+    }
+    return v != 0;
+}
+
 struct Level {
     int nx = 0, ny = 0;
     size_t np = 0;
@@ -1144,7 +1158,7 @@ int create_instance(const biot_params *p, const biot_side sides[4], biot_handle 
         Lv.ny = p->ny >> shift;
         Lv.np = (size_t)Lv.nx * Lv.ny;
         // coarsest level in FP64; with BIOT_FP32_COARSE64 every level below the finest
-        Lv.fp64 = !h->fp32 || (l == 0 && h->L > 1) || (p->precision == BIOT_FP32_COARSE64 && l < h->L - 1);
+        Lv.fp64 = !h->fp32 || (l == 0 && h->L > 1 && coarsest_fp64()) || (p->precision == BIOT_FP32_COARSE64 && l < h->L - 1);
         const size_t esz = Lv.fp64 ? sizeof(double) : sizeof(float);
         TRY_RC(dev_alloc(h, &Lv.g[0], 8 * Lv.np * esz));
         TRY_RC(dev_alloc(h, &Lv.g[1], 8 * Lv.np * esz));
@@ -2040,7 +2054,8 @@ size_t estimate_bytes(const biot_params *p, const biot_side *sides)
     for (int l = 0; l < p->mg_levels; l++) {
         const int shift = p->mg_levels - 1 - l;
         const size_t nx = (size_t)(p->nx >> shift), ny = (size_t)(p->ny >> shift), n = nx * ny;
-        const bool fp64 = !fp32 || (l == 0 && p->mg_levels > 1) || (p->precision == BIOT_FP32_COARSE64 && l < p->mg_levels - 1);
+        const bool fp64 = !fp32 || (l == 0 && p->mg_levels > 1 && coarsest_fp64()) ||
+                          (p->precision == BIOT_FP32_COARSE64 && l < p->mg_levels - 1);
         const size_t esz = fp64 ? 8 : 4;
         b += 2 * 8 * n * esz;
         if (!fp64 && (l == p->mg_levels - 1 || coarse_lo_mode() != COARSE_LO_OFF)) b += 2 * 2 * n * esz;

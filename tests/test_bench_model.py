@@ -28,17 +28,27 @@ def test_step_model_terzaghi_4096_fp32():
     fine = cells[-1]
     restrict_fine = (5 + 2 + 2) * 4 + 5 * 4 / 4
     coarse = 0.0
-    for l in range(L - 1):
-        e = 8 if l == 0 else 4
-        ec = 8 if l == 1 else 4
-        prol = 5 * ec / 4 / (2 * K) if l > 0 else 0.0
-        coarse += ne * 2 * K * cells[l] * ((5 * 2 + 5) * e + prol)
+    for l in range(L - 1):  # every coarse level in FP32, the coarsest included
+        prol = 5 * 4 / 4 / (2 * K) if l > 0 else 0.0
+        coarse += ne * 2 * K * cells[l] * ((5 * 2 + 5) * 4 + prol)
         if l > 0:
-            coarse += ne * cells[l] * ((5 + 5) * e + 5 * ec / 4)
-    flow = fine * (9 * 4 * 2 + 4 + 16 + 8 + 2 * 4 + 16)
+            coarse += ne * cells[l] * ((5 + 5) * 4 + 5 * 4 / 4)
+    # flow: 9 f in and out, m_s, D(t - dt) (FP64), previous difference in;
+    # D(t) (FP64), new difference, F~ (2) out
+    flow = fine * (9 * 4 * 2 + 4 + 8 + 4 + 8 + 4 + 2 * 4)
+    assert flow / fine == 108
     expect = ne * 2 * K * fine * finest + ne * fine * restrict_fine + coarse + flow
     assert nb == pytest.approx(expect)
-    assert nb / fine == pytest.approx(2328, abs=1.0)
+    assert nb / fine == pytest.approx(2312, abs=1.0)
+
+
+def test_step_model_follows_the_coarsest_precision_switch(monkeypatch):
+    p, _, _ = W.terzaghi_4097()
+    _, nb32 = bench.step_model(p, 4096, fp64=False)
+    monkeypatch.setenv("BIOT_COARSEST_FP64", "1")
+    _, nb64 = bench.step_model(p, 4096, fp64=False)
+    # the 8^2 level's bytes double and its prolongation into 16^2 doubles
+    assert 0 < nb64 - nb32 < 1e-5 * nb32
 
 
 def test_step_model_fp64_has_no_low_parts():
