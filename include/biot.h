@@ -54,10 +54,11 @@ extern "C" {
 
 /* ---- storage precision of the populations --------------------------------- */
 #define BIOT_FP64 0  /* all populations and arithmetic in FP64 (parity path) */
-#define BIOT_FP32 1  /* FP32 elastic state and collisions, the displacement moments of
-                        the finest level kept as double-float (two FP32 planes); FP64
-                        for residual norms, the coarsest multigrid level and the
-                        divergence / pressure accumulations of the coupling.  The
+#define BIOT_FP32 1  /* FP32 elastic state and collisions on every multigrid level, the
+                        displacement moments of the finest level kept as double-float
+                        (two FP32 planes); FP64 for residual norms and the divergence /
+                        pressure accumulations of the coupling (the environment variable
+                        BIOT_COARSEST_FP64=1 makes the coarsest level FP64).  The
                         solve at t = 0, which starts from a zero iterate, runs on a
                         temporary FP64 copy of the problem for grids of at least
                         2048^2 cells (its state then rounded into FP32 storage), and

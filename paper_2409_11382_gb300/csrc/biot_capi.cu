@@ -1157,7 +1157,8 @@ int create_instance(const biot_params *p, const biot_side sides[4], biot_handle 
         Lv.nx = p->nx >> shift;
         Lv.ny = p->ny >> shift;
         Lv.np = (size_t)Lv.nx * Lv.ny;
-        // coarsest level in FP64; with BIOT_FP32_COARSE64 every level below the finest
+        // FP64: the FP64 path; the coarsest level with BIOT_COARSEST_FP64=1; with
+        // BIOT_FP32_COARSE64 every level below the finest
         Lv.fp64 = !h->fp32 || (l == 0 && h->L > 1 && coarsest_fp64()) || (p->precision == BIOT_FP32_COARSE64 && l < h->L - 1);
         const size_t esz = Lv.fp64 ? sizeof(double) : sizeof(float);
         TRY_RC(dev_alloc(h, &Lv.g[0], 8 * Lv.np * esz));
