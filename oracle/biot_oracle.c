@@ -48,6 +48,13 @@
 
 #define ORC_MAX_LEVELS 16
 
+/* Threads of the per-cell loops.  Only loops whose iterations write disjoint
+ * cells run in parallel (collision, streaming, gradients, relaxation,
+ * prolongation, flow step); every sum keeps its serial order, so the results
+ * are bitwise those of one thread.  Default 1 (orc_set_threads). */
+static int orc_threads = 1;
+#define ORC_PAR_FOR _Pragma("omp parallel for schedule(static) if(orc_threads > 1) num_threads(orc_threads)")
+
 enum { ORC_PERIODIC = 0, ORC_SYMMETRY = 1, ORC_DIRICHLET = 2, ORC_NEUMANN = 3 };
 enum { SIDE_BOTTOM = 0, SIDE_RIGHT = 1, SIDE_TOP = 2, SIDE_LEFT = 3 };
 
@@ -102,7 +109,7 @@ typedef struct {
     int solved, initialized;
     /* statistics */
     int last_ne;
-    double last_res, last_gnorm;
+    double last_res, last_gnorm, last_res_l2;
     long total_cycles;
     int notconv_steps, diverged;
 } Orc;
@@ -321,8 +328,10 @@ static double pull_elastic(const Orc *o, const Level *Lv, int fine, int x, int y
 static void elastic_step(Orc *o, Level *Lv, int fine, const double *gin, const double *F, double *gout)
 {
     const int n = Lv->nx * Lv->ny;
+    ORC_PAR_FOR
     for (int c = 0; c < n; c++) collide(o, gin + 8 * c, F + 2 * c, Lv->gs + 8 * c);
     const double *Hold = Lv->hist_valid ? Lv->H : Lv->gs;
+    ORC_PAR_FOR
     for (int y = 0; y < Lv->ny; y++)
         for (int x = 0; x < Lv->nx; x++)
             for (int k = 0; k < 8; k++)
@@ -362,8 +371,10 @@ static void central_gradient(const Orc *o, const double *q, int nx, int ny, int 
 static void fstar(Orc *o, Level *Lv, const double *g, double *Fs)
 {
     const int nx = Lv->nx, ny = Lv->ny;
+    ORC_PAR_FOR
     for (int c = 0; c < nx * ny; c++) Lv->D[c] = divergence_of(o, g + 8 * c);
     const double coef = 0.5 * o->P.alpha * o->P.alpha * o->P.r;
+    ORC_PAR_FOR
     for (int y = 0; y < ny; y++)
         for (int x = 0; x < nx; x++) {
             double gr[2];
@@ -379,6 +390,7 @@ static void step_of_iterate(Orc *o, Level *Lv, int fine, const double *g, const 
     const int n = Lv->nx * Lv->ny;
     fstar(o, Lv, g, Lv->F);
     if (Ft) for (int c = 0; c < 2 * n; c++) Lv->F[c] += Ft[c];
+    ORC_PAR_FOR
     for (int c = 0; c < 8 * n; c++) Lv->gin[c] = g[c] - (Lv->r ? Lv->r[c] : 0.0);
     elastic_step(o, Lv, fine, Lv->gin, Lv->F, gout);
 }
@@ -396,6 +408,7 @@ static void multigrid(Orc *o, int l, const double *Ft)
     /* pre-smoothing, eq. MG:smoother */
     for (int k = 0; k < o->P.K; k++) {
         step_of_iterate(o, Lv, fine, Lv->g, Ft, Lv->gout);
+        ORC_PAR_FOR
         for (int c = 0; c < 8 * n; c++) Lv->g[c] = (1.0 - gam) * Lv->g[c] + gam * Lv->gout[c];
     }
     if (l > 0) {
@@ -414,6 +427,7 @@ static void multigrid(Orc *o, int l, const double *Ft)
         Lc->hist_valid = 0;
         multigrid(o, l - 1, NULL);
         /* prolongation P = R^T (copy of the coarse value to its four cells) */
+        ORC_PAR_FOR
         for (int y = 0; y < Lv->ny; y++)
             for (int x = 0; x < Lv->nx; x++) {
                 int pc = (y / 2) * Lc->nx + (x / 2);
@@ -426,16 +440,19 @@ static void multigrid(Orc *o, int l, const double *Ft)
     for (int k = 0; k < o->P.K; k++) {
         step_of_iterate(o, Lv, fine, Lv->g, Ft, Lv->gout);
         if (fine && k == o->P.K - 1) {
-            double res = 0.0, gn = 0.0;
+            double res = 0.0, gn = 0.0, sq = 0.0;
             for (int c = 0; c < 8 * n; c++) {
                 double a = absmax_nan_inf(Lv->g[c] - Lv->gout[c]);
                 double b = absmax_nan_inf(Lv->g[c]);
                 if (a > res) res = a;
                 if (b > gn) gn = b;
+                sq += (Lv->g[c] - Lv->gout[c]) * (Lv->g[c] - Lv->gout[c]);
             }
             o->last_res = res;
             o->last_gnorm = gn;
+            o->last_res_l2 = sqrt(sq); /* the 2-norm of the same residual */
         }
+        ORC_PAR_FOR
         for (int c = 0; c < 8 * n; c++) Lv->g[c] = (1.0 - gam) * Lv->g[c] + gam * Lv->gout[c];
     }
 }
@@ -452,6 +469,7 @@ static void explicit_source(Orc *o)
 {
     const int n = o->P.nx * o->P.ny;
     const double a = o->P.alpha / o->h, r = o->P.r;
+    ORC_PAR_FOR
     for (int c = 0; c < n; c++)
         o->sexp[c] = o->P.dt * o->src[c] - a * ((1.0 - r) * (o->D1[c] - o->D2[c]) - r * o->D1[c]);
 }
@@ -469,6 +487,7 @@ static double full_source(const Orc *o, int c)
 static void explicit_force(Orc *o)
 {
     const int nx = o->P.nx, ny = o->P.ny;
+    ORC_PAR_FOR
     for (int y = 0; y < ny; y++)
         for (int x = 0; x < nx; x++) {
             int c = y * nx + x;
@@ -526,6 +545,7 @@ static void flow_step(Orc *o)
 {
     const int nx = o->P.nx, ny = o->P.ny, n = nx * ny;
     const double om = o->omega;
+    ORC_PAR_FOR
     for (int c = 0; c < n; c++) {
         double sp = full_source(o, c);
         double sum = 0.0;
@@ -537,10 +557,12 @@ static void flow_step(Orc *o)
             o->fs[9 * c + i] = o->f[9 * c + i] - om * (o->f[9 * c + i] - feq) + S; /* eq. pressure:collision */
         }
     }
+    ORC_PAR_FOR
     for (int y = 0; y < ny; y++)
         for (int x = 0; x < nx; x++)
             for (int i = 0; i < 9; i++) o->fn[9 * (y * nx + x) + i] = pull_flow(o, x, y, i);
     double *tmp = o->f; o->f = o->fn; o->fn = tmp;
+    ORC_PAR_FOR
     for (int c = 0; c < n; c++) { o->D2[c] = o->D1[c]; o->D1[c] = o->Dt[c]; }
     o->nstep += 1;
     o->t = o->P.dt * (double)o->nstep;
@@ -589,6 +611,7 @@ static int elastic_solve(Orc *o)
         if (ne >= o->P.ne_max) { o->notconv_steps++; status = -4; break; }
     }
     o->last_ne = ne;
+    ORC_PAR_FOR
     for (int c = 0; c < n; c++) o->Dt[c] = divergence_of(o, Lf->g + 8 * c);
     o->solved = 1;
     return status;
@@ -616,6 +639,19 @@ static int validate(const orc_params *p, const orc_side s[4])
 }
 
 void orc_destroy(void *h);
+
+/* Threads of the per-cell loops (1 = serial, the default); results do not
+ * depend on it. */
+void orc_set_threads(int n) { orc_threads = n > 0 ? n : 1; }
+int orc_get_threads(void) { return orc_threads; }
+int orc_openmp(void)
+{
+#ifdef _OPENMP
+    return 1;
+#else
+    return 0;
+#endif
+}
 
 void *orc_create(const orc_params *p, const orc_side sides[4])
 {
@@ -794,6 +830,7 @@ typedef struct {
     long nstep;
     double t;
     double omega, om_s, om_d, kap_lattice;
+    double last_res_l2;
 } orc_stats;
 
 int orc_stats_get(void *h, orc_stats *s)
@@ -810,6 +847,7 @@ int orc_stats_get(void *h, orc_stats *s)
     s->om_s = o->om_s;
     s->om_d = o->om_d;
     s->kap_lattice = o->kap;
+    s->last_res_l2 = o->last_res_l2;
     return 0;
 }
 

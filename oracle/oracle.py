@@ -46,7 +46,7 @@ class _Stats(C.Structure):
     _fields_ = [("last_ne", C.c_int), ("last_res", C.c_double), ("total_cycles", C.c_long),
                 ("notconv_steps", C.c_int), ("diverged", C.c_int), ("nstep", C.c_long),
                 ("t", C.c_double), ("omega", C.c_double), ("om_s", C.c_double),
-                ("om_d", C.c_double), ("kap_lattice", C.c_double)]
+                ("om_d", C.c_double), ("kap_lattice", C.c_double), ("last_res_l2", C.c_double)]
 
 
 def build(force: bool = False) -> str:
@@ -59,7 +59,10 @@ def build(force: bool = False) -> str:
         tmp = _LIB + f".{os.getpid()}.tmp"
         cmd = ["gcc", "-std=c99", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
                "-shared", "-o", tmp, _SRC, "-lm"]
-        subprocess.run(cmd, check=True)
+        # OpenMP for the per-cell loops (orc_set_threads); without it the
+        # pragmas are ignored and the oracle runs on one thread
+        if subprocess.run(cmd[:-1] + ["-fopenmp", "-lm"], capture_output=True).returncode != 0:
+            subprocess.run(cmd, check=True)
         os.replace(tmp, _LIB)
         return _LIB
 
@@ -89,6 +92,9 @@ def _load():
         lib.orc_plain_pseudo_step.argtypes = [C.c_void_p]
         for name in ("orc_get_g", "orc_set_g", "orc_get_f", "orc_set_f"):
             getattr(lib, name).argtypes = [C.c_void_p, P]
+        lib.orc_set_threads.argtypes = [C.c_int]
+        lib.orc_get_threads.restype = C.c_int
+        lib.orc_openmp.restype = C.c_int
         _lib = lib
     return _lib
 
@@ -105,6 +111,20 @@ def collide_cell(lam_hat: float, mu_hat: float, g, F) -> np.ndarray:
     out = np.zeros(8)
     lib.orc_collide_cell(lam_hat, mu_hat, _ptr(g), _ptr(F), _ptr(out))
     return out
+
+
+def set_threads(n: int) -> int:
+    """Threads of the oracle's per-cell loops (1 = serial, the default; the
+    results are bitwise the same for every count).  Returns the count in use;
+    it stays 1 when the oracle was built without OpenMP."""
+    lib = _load()
+    lib.orc_set_threads(int(n))
+    return int(lib.orc_get_threads()) if openmp_enabled() else 1
+
+
+def openmp_enabled() -> bool:
+    """Whether the oracle library was built with OpenMP."""
+    return bool(_load().orc_openmp())
 
 
 def inverse_table() -> np.ndarray:
