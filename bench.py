@@ -87,14 +87,14 @@ def step_model(params, n, fp64):
       finest residual + restriction: the same inputs, 5 coarse moments per 4 cells out;
       coarse smoothing: 5 moments and 5 of r in, 5 moments out (+ prolongation);
       coarse residual + restriction: 10 in, 5 coarse out per 4 cells;
-      coarsest level: as coarse smoothing (FP32 on the FP32 path, FP64 with
-        BIOT_COARSEST_FP64=1);
+      coarsest level: as coarse smoothing (FP64 on the FP32 path, FP32 with
+        the option BIOT_OPT_COARSEST_STORAGE);
       flow step: 9 f in and out, m_s, D(t - dt) (FP64) and the previous history
         difference in, D(t) (FP64), the new difference and F~ out.
     Returns (cell-sweeps per step, bytes per step)."""
     L, K, ne = params["levels"], params["K"], params["ne_fixed"]
     esz = 8 if fp64 else 4
-    c64 = os.environ.get("BIOT_COARSEST_FP64", "0") == "1"  # as the library reads it
+    c64 = coarsest_fp64(params)
     cell_sweeps = 0.0
     nbytes = 0.0
     for l in range(L - 1, -1, -1):  # finest first
@@ -116,6 +116,25 @@ def step_model(params, n, fp64):
     fe = 8 if fp64 else 4
     nbytes += fine_cells * (9 * fe * 2 + fe + 8 + fe + 8 + fe + 2 * fe)
     return cell_sweeps, nbytes
+
+
+OPT_COARSEST_STORAGE = 1  # biot_params.options flag of include/biot.h
+
+
+def coarsest_fp64(params):
+    """Whether the FP32 path runs the coarsest multigrid level in FP64 (the
+    default; FP32 with the option BIOT_OPT_COARSEST_STORAGE)."""
+    return not (int(params.get("options", 0)) & OPT_COARSEST_STORAGE)
+
+
+def precision_label(params, fp64):
+    """What the run computes in, from the parameters the library was given."""
+    if fp64:
+        return "fp64 storage and arithmetic"
+    cells = params["nx"] * params["ny"]
+    return ("fp32 moments and collisions; fp64 residual norms, coupling accumulators and "
+            + ("coarsest level" if coarsest_fp64(params) else "no level (coarsest level fp32)")
+            + ("; fp64 solve at t = 0" if cells >= 2048 * 2048 else ""))
 
 
 def measured_fp64_peak(torch):
@@ -184,61 +203,109 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def oracle_sample_step(keep=None):
-    """The oracle (single-threaded FP64 C) on one physical step of the same workload,
-    restricted to a 512-cell-wide strip: the problem does not depend on x, so every
-    cell does the same work as in the full grid.  Returns (seconds, cells); with a
-    dict ``keep``, also stores the oracle's eta and p after the step there."""
+def oracle_strip():
+    """The oracle on the benchmark workload restricted to a 512-cell-wide strip:
+    the problem does not depend on x, so every cell does the same work as in
+    the full grid.  Returns (oracle, cells)."""
     from oracle import oracle as O
     from paper_2409_11382_gb300 import workloads as W
     params, _, _ = W.terzaghi_4097(precision=W.FP64)
     strip = dict(params, nx=512, lx=512 / 4096)
-    o = O.Oracle(strip, W.top_load_sides(512, W.uniform_load(512)))
-    o.step(0)  # elastic solve at t = 0 (untimed set-up)
+    return O.Oracle(strip, W.top_load_sides(512, W.uniform_load(512))), 512 * params["ny"]
+
+
+def timed_oracle_step(o, threads):
+    """Seconds of one physical step (flow step + elastic solve) of the oracle
+    on ``threads`` host threads, and the thread count it actually used."""
+    from oracle import oracle as O
+    used = O.set_threads(threads)
     t0 = time.perf_counter()
-    o.step(1)  # one Biot step: flow step + elastic solve
-    dt = time.perf_counter() - t0
-    if keep is not None:
-        keep["eta"], keep["p"] = o.read_u()[0], o.read_p()[0]
-    o.close()
-    return dt, 512 * params["ny"]
+    o.step(1)
+    return time.perf_counter() - t0, used
 
 
-def accuracy_vs_oracle(oracle_fields, n, precision=None):
-    """L-infinity and L2 relative errors of eta and p of the GPU path after one step
-    of the benchmark problem against the oracle's strip (x-independent problem)."""
+GOLDEN_STRIP = os.path.join(ROOT, "tests", "golden", "terzaghi_4096_strip_fp64.npz")
+
+
+def accuracy_vs_oracle(oracle_fields, n, params_over=None, precision=None):
+    """L-infinity and L2 relative errors of eta and p of the GPU path against the
+    FP64 oracle on the benchmark problem, which does not depend on x: after 1,
+    10 and 100 steps against the oracle's stored column (tests/golden, written
+    by the oracle on a 512-column strip of the same problem), every GPU column
+    compared.  Without the stored columns: after 1 step against the live strip
+    in ``oracle_fields``."""
     from paper_2409_11382_gb300 import biot, workloads as W
     params, sides, _ = W.terzaghi_4097(n=n, precision=W.FP32 if precision is None else precision)
+    params = dict(params, **(params_over or {}))
+
+    def errs(eta, p, eta_o, p_o):
+        out = {}
+        for name, g, o in (("eta", eta, eta_o), ("p", p, p_o)):
+            d = g - o
+            out[f"{name}_linf_rel"] = float(np.abs(d).max() / np.abs(o).max())
+            out[f"{name}_l2_rel"] = float(np.sqrt((d * d).sum() / (o * o * np.ones_like(g)).sum()))
+        return out
+
+    if n == 4096 and os.path.exists(GOLDEN_STRIP):
+        gold = np.load(GOLDEN_STRIP)
+        per_step = {}
+        done = 0
+        with biot.Solver(params, sides) as s:
+            for k, steps in enumerate(gold["steps"]):
+                s.step(int(steps) - done)
+                done = int(steps)
+                eta, t = s.read_u()
+                p, _ = s.read_p()
+                assert abs(t - gold["t"][k]) < 1e-12
+                per_step[str(int(steps))] = errs(eta, p, gold["eta"][k][:, :, None], gold["p"][k][:, None])
+        out = dict(per_step[str(int(gold["steps"][-1]))])
+        out["per_step"] = per_step
+        out["how"] = (f"after {int(gold['steps'][-1])} steps (also 1 and 10 in per_step), all {n} columns vs the "
+                      "FP64 oracle's column of the same x-independent problem (512-column strip)")
+        return out
     with biot.Solver(params, sides) as s:
         s.step(1)
         eta, _ = s.read_u()
         p, _ = s.read_p()
-    out = {}
-    for name, g, o in (("eta", eta[:, :, :512], oracle_fields["eta"]), ("p", p[:, :512], oracle_fields["p"])):
-        out[f"{name}_linf_rel"] = float(np.abs(g - o).max() / np.abs(o).max())
-        out[f"{name}_l2_rel"] = float(np.linalg.norm(g - o) / np.linalg.norm(o))
+    out = errs(eta[:, :, :512], p[:, :512], oracle_fields["eta"], oracle_fields["p"])
     out["how"] = "after 1 step, first 512 columns vs the FP64 oracle on a 512-column strip"
     return out
 
 
 def cpu_baseline_entry(keep=None):
-    secs, cells = oracle_sample_step(keep)
-    return {"value": cells / secs / 1e6, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+    """The oracle timed on this host's cores: one step on every core (OpenMP over
+    the cells; bitwise the single-thread result), then one on one core."""
+    nproc = os.cpu_count() or 1
+    o, cells = oracle_strip()
+    o.step(0)  # elastic solve at t = 0 (untimed set-up)
+    secs_n, used = timed_oracle_step(o, nproc)
+    if keep is not None:
+        keep["eta"], keep["p"] = o.read_u()[0], o.read_p()[0]
+    secs_1, _ = timed_oracle_step(o, 1)
+    o.close()
+    return {"value": cells / secs_n / 1e6, "unit": "MLUPS", "cores": used, "kind": "oracle", "nproc": nproc,
             "sample": f"1 physical step of the same problem on a 512x4096-cell strip "
-                      f"(x-independent solution, same per-cell work), {secs:.1f} s, FP64, 1 thread"}
+                      f"(x-independent solution, same per-cell work), {secs_n:.1f} s, FP64, "
+                      f"OpenMP over cells on {used} threads",
+            "single_thread": {"value": cells / secs_1 / 1e6, "unit": "MLUPS", "cores": 1,
+                              "sample": f"the next step of the same strip on 1 thread, {secs_1:.1f} s"}}
 
 
 def run_reference(args):
     rank, world, _ = dist_info()
     if rank != 0:
         return 0
+    nproc = os.cpu_count() or 1
+    o, cells = oracle_strip()
+    o.step(0)  # elastic solve at t = 0 (untimed set-up)
+    used = 1
     for _ in range(args.warmup):
-        oracle_sample_step()
+        timed_oracle_step(o, nproc)
     t = []
-    cells = 0
     for _ in range(args.steps):
-        secs, cells = oracle_sample_step()
+        secs, used = timed_oracle_step(o, nproc)
         t.append(secs)
+    o.close()
     total = sum(t)
     value = cells * args.steps / total / 1e6
     line = {
@@ -248,10 +315,13 @@ def run_reference(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "cells": "4096x4096", "levels": 10, "ne_fixed": 3, "K": 4, "gamma": 0.75,
-                   "precision": "fp64 (the oracle)", "parallelism": "replicas1"},
-        "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+                   "precision": "fp64 (the oracle)", "parallelism": "replicas1",
+                   "ms_per_step_extrapolated": True,
+                   "ms_per_step_from": "the timed 512x4096-cell strip, scaled by cells to 4096x4096",
+                   "timed_cells_per_step": cells, "host_threads": used, "nproc": nproc},
+        "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": used, "kind": "oracle", "nproc": nproc,
                          "sample": "each step: 1 physical step of the workload restricted to a 512x4096-cell "
-                                   "strip (x-independent solution, same per-cell work)"},
+                                   "strip (x-independent solution, same per-cell work), OpenMP over cells"},
         "e2e": {"value": value, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         "note": "ms_per_step extrapolated linearly from the strip to 4096x4096 cells",
     }
@@ -294,6 +364,8 @@ def run_ours(args):
         torch.distributed.barrier()
     fp64 = args.precision == "fp64"
     params, sides, _ = W.terzaghi_4097(n=args.n, precision=W.FP64 if fp64 else W.FP32)
+    if args.coarsest == "fp32":
+        params = dict(params, options=int(params.get("options", 0)) | OPT_COARSEST_STORAGE)
     nx, ny = params["nx"], params["ny"]
     cells = nx * ny
     stream = torch.cuda.current_stream()
@@ -373,10 +445,13 @@ def run_ours(args):
     value = world * cells * args.steps / (ms / 1e3) / 1e6
     peak, peak_kind = measured_peaks()
     cpu_base, accuracy = None, None
-    if not args.no_cpu_baseline and args.n == 4096:
+    if args.n == 4096:
         fields = {}
-        cpu_base = cpu_baseline_entry(fields)
-        accuracy = accuracy_vs_oracle(fields, args.n, W.FP64 if fp64 else W.FP32)
+        if not args.no_cpu_baseline:
+            cpu_base = cpu_baseline_entry(fields)
+        if fields or os.path.exists(GOLDEN_STRIP):
+            accuracy = accuracy_vs_oracle(fields, args.n, {"options": params.get("options", 0)},
+                                          W.FP64 if fp64 else W.FP32)
     # finest-level smoothing sweep, fixed V-cycle count: the 5 moments that carry
     # state (the ghost moments 12, 21, 22 are elided) in and out, F~ in, with FP32
     # storage also the 2 low parts of the first moments in and out; the
@@ -414,8 +489,7 @@ def run_ours(args):
         "config": {"workload": f"terzaghi_{args.n + 1}x{args.n + 1}_{args.precision}",
                    "cells": f"{nx}x{ny}", "levels": params["levels"],
                    "ne_fixed": params["ne_fixed"], "K": params["K"], "gamma": params["gamma"],
-                   "precision": "fp64 storage and arithmetic" if fp64 else
-                                "fp32 populations; fp64 residual norms, coarsest level, coupling",
+                   "precision": precision_label(params, fp64),
                    "l2": f"state ({st['device_bytes'] / 1e9:.1f} GB) larger than L2; no flush needed",
                    "parallelism": f"replicas{world}",
                    "autotuned_strip_rows": tuned},
@@ -660,7 +734,9 @@ def main():
     ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32",
                     help="single: the FP32 path (default) or the plain FP64 path")
     ap.add_argument("--instances", type=int, default=64, help="batched: number of instances")
-    ap.add_argument("--requests", type=int, default=48, help="served: number of requests")
+    ap.add_argument("--coarsest", choices=["fp64", "fp32"], default="fp64",
+                    help="single, FP32 path: precision of the coarsest multigrid level")
+    ap.add_argument("--requests", type=int, default=200, help="served: number of requests")
     ap.add_argument("--mean-service", type=float, default=0.05, help="served: assumed mean service time (s)")
     ap.add_argument("--budget-gb", type=float, default=16.0, help="served: device-memory budget")
     ap.add_argument("--max-resident", type=int, default=16, help="served: resident-instance limit")

@@ -54,20 +54,34 @@ extern "C" {
 
 /* ---- storage precision of the populations --------------------------------- */
 #define BIOT_FP64 0  /* all populations and arithmetic in FP64 (parity path) */
-#define BIOT_FP32 1  /* FP32 elastic state and collisions on every multigrid level, the
+#define BIOT_FP32 1  /* FP32 elastic state and collisions on every multigrid level but
+                        the coarsest, which is FP64 (Alg. 4 with l = 1); the
                         displacement moments of the finest level kept as double-float
                         (two FP32 planes); FP64 for residual norms and the divergence /
-                        pressure accumulations of the coupling (the environment variable
-                        BIOT_COARSEST_FP64=1 makes the coarsest level FP64).  The
-                        solve at t = 0, which starts from a zero iterate, runs on a
-                        temporary FP64 copy of the problem for grids of at least
-                        2048^2 cells (its state then rounded into FP32 storage), and
-                        with double-float coarse levels on smaller grids */
+                        pressure accumulations of the coupling.  The solve at t = 0,
+                        which starts from a zero iterate, runs on a temporary FP64 copy
+                        of the problem for grids of at least 2048^2 cells (its state
+                        then rounded into FP32 storage), and with double-float coarse
+                        levels on smaller grids.  biot_params.options changes each of
+                        these choices */
 #define BIOT_FP32_COARSE64 2  /* BIOT_FP32 on the finest level (elastic state and flow
                                  populations), FP64 on every coarser multigrid level:
                                  the coarse-grid corrections are not rounded to FP32 */
 /* In every precision the elastic state is stored as the MRT moments of the
  * populations (an exact change of basis, eqs. moments / moments:stress). */
+
+/* ---- options of the FP32 paths (biot_params.options, bit flags) ------------
+ * 0 selects the defaults described at BIOT_FP32.  They change rounding only:
+ * the scheme, its iteration counts and its fixed point are the same.
+ * BIOT_OPT_COLD_FP64 / _COLD_FP32 and BIOT_OPT_COARSE_LO_ALL / _OFF exclude
+ * each other; the options are ignored by BIOT_FP64. */
+#define BIOT_OPT_COARSEST_STORAGE 1   /* the coarsest level in FP32 like the other coarse
+                                         levels (faster on small instances) */
+#define BIOT_OPT_COLD_FP64        2   /* the solve at t = 0 on an FP64 copy on every grid */
+#define BIOT_OPT_COLD_FP32        4   /* ... on no grid (FP32 with double-float coarse levels) */
+#define BIOT_OPT_COARSE_LO_ALL    8   /* double-float first moments on the FP32 coarse levels
+                                         in every solve (default: in an FP32 solve at t = 0) */
+#define BIOT_OPT_COARSE_LO_OFF   16   /* ... in no solve */
 
 /* ---- boundary condition types (§3.6) --------------------------------------- */
 #define BIOT_PERIODIC  0  /* wrap-around streaming; must be set on both opposite sides
@@ -110,7 +124,8 @@ typedef struct biot_params {
                           max|g - ELASTIC_STEP(g)| <= tol * max(1, max|g|) (ne_fixed <= 0) */
     int    ne_max;     /* cap on V-cycles per step in tolerance mode */
     int    ne_fixed;   /* > 0: exactly this many V-cycles per step, MG(ne_fixed, K) */
-    int    precision;  /* BIOT_FP64 or BIOT_FP32 */
+    int    precision;  /* BIOT_FP64, BIOT_FP32 or BIOT_FP32_COARSE64 */
+    int    options;    /* BIOT_OPT_* flags (0: defaults) */
 } biot_params;
 
 /* Boundary data of one side.  Profiles are sampled at the 2n+1 arc positions
@@ -128,7 +143,8 @@ typedef struct biot_side {
 
 typedef struct biot_stats {
     int     last_ne;        /* V-cycles of the last elastic solve */
-    double  last_res;       /* residual measured in its last smoothing sweep */
+    double  last_res;       /* residual max|g - ELASTIC_STEP(g)| over the populations of the finest
+                               level, measured in its last smoothing sweep (FP64) */
     long    total_cycles;   /* V-cycles since creation */
     int     notconv_steps;  /* steps that hit ne_max */
     int     diverged;       /* 1 once a non-finite residual was met */
@@ -138,6 +154,9 @@ typedef struct biot_stats {
     double  omega_s, omega_d; /* elastic relaxation rates, Tab. moments */
     long    kernel_launches;  /* kernels launched since creation */
     size_t  device_bytes;     /* device memory held */
+    double  last_res_l2;      /* (sum over cells and populations of (g - ELASTIC_STEP(g))^2)^(1/2) of the
+                                 sweep that measured last_res, summed in FP64 (fixed V-cycle counts
+                                 leave out the ghost moments 12, 21, 22, as in last_res) */
 } biot_stats;
 
 typedef struct biot_ctx *biot_handle;
@@ -377,7 +396,13 @@ BIOT_API int biot_server_destroy(biot_server s);
  *    from different host threads whose GPU work overlaps (e.g. two instances on
  *    two streams) race on it: serialise them.
  *  - Like biot_read_u it may first run the pending elastic solve of the instance
- *    and returns after the values are in *eta (2 x nx x ny, host memory). */
+ *    and returns after the values are in *eta (2 x nx x ny, host memory).  The
+ *    one solve that would allocate -- the solve at t = 0 of an FP32 instance
+ *    that runs it on an FP64 copy (grids of at least 2048^2 cells, or
+ *    BIOT_OPT_COLD_FP64) -- is refused with BIOT_ERR_INVALID_ARG: step the
+ *    instance or read it once with biot_read_u first.
+ *  - The instance's device must be the current device (BIOT_ERR_INVALID_ARG
+ *    otherwise); the array of that device is used. */
 #define BIOT_NOALLOC_MAX_CELLS 262144
 BIOT_API int biot_read_u_noalloc(biot_handle h, double *eta, double *t_out);
 

@@ -19,6 +19,8 @@ LIB_PATH = os.path.join(_HERE, "libbiot_gb300.so")
 OK, ERR_INVALID_ARG, ERR_OOM, ERR_DIVERGED, ERR_NOT_CONVERGED, ERR_CUDA, ERR_TIMEOUT, ERR_NO_DEVICE = (
     0, -1, -2, -3, -4, -5, -6, -7)
 FP64, FP32, FP32_COARSE64 = 0, 1, 2
+# biot_params.options (include/biot.h)
+OPT_COARSEST_STORAGE, OPT_COLD_FP64, OPT_COLD_FP32, OPT_COARSE_LO_ALL, OPT_COARSE_LO_OFF = 1, 2, 4, 8, 16
 PERIODIC, SYMMETRY, DIRICHLET, NEUMANN = 0, 1, 2, 3
 BOTTOM, RIGHT, TOP, LEFT = 0, 1, 2, 3
 
@@ -51,7 +53,7 @@ class biot_params(C.Structure):
                 ("c0", C.c_double), ("kappa", C.c_double), ("dt", C.c_double),
                 ("r_coupling", C.c_double), ("mg_levels", C.c_int), ("K", C.c_int),
                 ("gamma", C.c_double), ("tol", C.c_double), ("ne_max", C.c_int),
-                ("ne_fixed", C.c_int), ("precision", C.c_int)]
+                ("ne_fixed", C.c_int), ("precision", C.c_int), ("options", C.c_int)]
 
 
 class biot_side(C.Structure):
@@ -75,7 +77,7 @@ class biot_stats(C.Structure):
                 ("notconv_steps", C.c_int), ("diverged", C.c_int), ("nstep", C.c_long),
                 ("t", C.c_double), ("omega", C.c_double), ("omega_s", C.c_double),
                 ("omega_d", C.c_double), ("kernel_launches", C.c_long),
-                ("device_bytes", C.c_size_t)]
+                ("device_bytes", C.c_size_t), ("last_res_l2", C.c_double)]
 
 
 _lib = None
@@ -169,6 +171,7 @@ def _fill_params(p: "biot_params", params: dict) -> "biot_params":
     p.gamma, p.tol = float(params["gamma"]), float(params["tol"])
     p.ne_max, p.ne_fixed = int(params["ne_max"]), int(params["ne_fixed"])
     p.precision = int(params.get("precision", FP64))
+    p.options = int(params.get("options", 0))
     return p
 
 

@@ -12,6 +12,10 @@ namespace biot {
 enum { SIDE_BOTTOM = 0, SIDE_RIGHT = 1, SIDE_TOP = 2, SIDE_LEFT = 3 };
 enum { BC_PERIODIC = 0, BC_SYMMETRY = 1, BC_DIRICHLET = 2, BC_NEUMANN = 3 };
 enum { SWEEP_SMOOTH = 0, SWEEP_RESTRICT = 1 };
+// Residual words of a measured sweep: [0] max|g - g**| and [1] max|g| over the
+// populations as ordered FP64 bits (atomicMax), [2] the FP64 sum of (g - g**)^2
+// over every population of every cell (atomicAdd of a double).
+constexpr int RES_WORDS = 3;
 
 // One elastic sweep on one multigrid level: either the under-relaxed smoother
 // of eq. MG:smoother, g <- (1-gamma) g + gamma ELASTIC_STEP(g - r, F~ + F_*(g)),
@@ -39,7 +43,7 @@ struct SweepArgs {
     double lm;                   // lambda^ + mu^
     double coef_fstar;           // alpha^2 r / 2 (self-dependence force)
     double c0h;                  // c0 * h (lattice traction per unit traction)
-    unsigned long long *resmax;  // [2] ordered bits of max|g - g**| and max|g|, or nullptr
+    unsigned long long *resmax;  // [RES_WORDS] max|g - g**|, max|g| (ordered bits), sum (g - g**)^2 (double), or nullptr
     int rows;                    // strip height of the launch (0: the default choice)
     int ghosts;                  // 1: load and store the ghost moments 12, 21, 22 (tolerance mode)
     // the same coefficients, evaluated once on the host in the storage type:
@@ -195,18 +199,8 @@ cudaError_t launch_sweep_batch(int variant, const BatchParams<T, TC> &P, cudaStr
 template <typename T, typename TC> int sweep_slots(int variant);
 constexpr int SWEEP_STRIP_COLS = 124;
 
-// Largest strip height of a sweep launch (rows); the environment variable
-// BIOT_SWEEP_MAX_ROWS overrides it.
-inline int sweep_rows_cap()
-{
-    static int cap = 0;
-    if (!cap) {
-        const char *e = getenv("BIOT_SWEEP_MAX_ROWS");
-        const int v = e ? atoi(e) : 0;
-        cap = v >= 2 ? v : 32;
-    }
-    return cap;
-}
+// Largest strip height of a sweep launch (rows) unless biot_autotune chose one.
+inline int sweep_rows_cap() { return 32; }
 
 // Rows per strip of a sweep over nx x ny cells given `slots` resident CTAs:
 // the grid fills whole waves of slots, with the first wave count whose strips

@@ -80,31 +80,21 @@ constexpr int MAX_LEVELS = 16;
 // corrections are displacement-sized: in the solve at t = 0, which starts from a
 // zero iterate (a cold start); a warm-started step's corrections are of the
 // size of the change over one time step.  Default: the cold-start solve only;
-// BIOT_COARSE_LO=1 takes them in every solve, BIOT_COARSE_LO=0 never (both for
-// comparisons).
+// BIOT_OPT_COARSE_LO_ALL takes them in every solve, BIOT_OPT_COARSE_LO_OFF never.
 enum { COARSE_LO_OFF = 0, COARSE_LO_COLD = 1, COARSE_LO_ALL = 2 };
-int coarse_lo_mode()
+int coarse_lo_mode(const biot_params *p)
 {
-    static int v = -1;
-    if (v < 0) {
-        const char *e = getenv("BIOT_COARSE_LO");
-        v = !e ? COARSE_LO_COLD : (e[0] == '0' ? COARSE_LO_OFF : (e[0] == '1' ? COARSE_LO_ALL : COARSE_LO_COLD));
-    }
-    return v;
+    if (p->options & BIOT_OPT_COARSE_LO_ALL) return COARSE_LO_ALL;
+    if (p->options & BIOT_OPT_COARSE_LO_OFF) return COARSE_LO_OFF;
+    return COARSE_LO_COLD;
 }
 
-// Precision of the coarsest level of the FP32 path: FP32 like the other coarse
-// levels (default; its corrections are the smoothest error components, and the
-// solve from a zero iterate has the FP64 cold start or double-float coarse
-// levels), or FP64 with BIOT_COARSEST_FP64=1, for comparisons.
-bool coarsest_fp64()
+// Precision of the coarsest level of the FP32 path: FP64 (default; Alg. 4 with
+// l = 1 is the FP64 part of the mixed-precision multigrid), or FP32 like the
+// other coarse levels with BIOT_OPT_COARSEST_STORAGE.
+bool coarsest_fp64(const biot_params *p)
 {
-    static int v = -1;
-    if (v < 0) {
-        const char *e = getenv("BIOT_COARSEST_FP64");
-        v = (e && e[0] == '1') ? 1 : 0;
-    }
-    return v != 0;
+    return (p->options & BIOT_OPT_COARSEST_STORAGE) == 0;
 }
 
 struct Level {
@@ -153,8 +143,8 @@ struct biot_ctx {
     cudaEvent_t aready[2] = {nullptr, nullptr}, acopied[2] = {nullptr, nullptr};
     bool ainflight[2] = {false, false};
     int aslot = 0;
-    unsigned long long *resmax = nullptr;      // device [2]
-    unsigned long long *resmax_host = nullptr; // pinned [2]
+    unsigned long long *resmax = nullptr;      // device [RES_WORDS]
+    unsigned long long *resmax_host = nullptr; // pinned [RES_WORDS]
     // device-side stopping test (tolerance mode inside graphs)
     StopState *stop = nullptr;                 // device
     StopState *stop_host = nullptr;            // pinned mirror, copied at the end of each step
@@ -172,6 +162,7 @@ struct biot_ctx {
     // statistics
     int last_ne = 0;
     double last_res = 0;
+    double last_res_l2 = 0;  // sqrt of the FP64 sum of squared residuals of that sweep
     long total_cycles = 0;
     int notconv_steps = 0;
     int diverged = 0;
@@ -199,6 +190,7 @@ struct biot_ctx {
     // mirrors are lent from the server's arena for the same reason.
     cudaMemPool_t pool = nullptr;
     bool host_lent = false;
+    int device = -1;  // the CUDA device current at biot_create (owns every buffer)
 };
 
 namespace {
@@ -206,7 +198,7 @@ namespace {
 // What a server lends an instance it creates (see biot_ctx::pool).
 struct Lend {
     cudaMemPool_t pool;
-    unsigned long long *resmax_host;  // 2 values
+    unsigned long long *resmax_host;  // RES_WORDS values
     StopState *stop_host;
 };
 
@@ -253,6 +245,13 @@ int check_params(const biot_params *p, const biot_side *s)
     if (p->ne_fixed <= 0 && (p->ne_max < 1 || !(p->tol > 0))) return fail(BIOT_ERR_INVALID_ARG, "tolerance mode needs tol > 0 and ne_max >= 1");
     if (p->precision != BIOT_FP64 && p->precision != BIOT_FP32 && p->precision != BIOT_FP32_COARSE64)
         return fail(BIOT_ERR_INVALID_ARG, "unknown precision");
+    constexpr int known = BIOT_OPT_COARSEST_STORAGE | BIOT_OPT_COLD_FP64 | BIOT_OPT_COLD_FP32 |
+                          BIOT_OPT_COARSE_LO_ALL | BIOT_OPT_COARSE_LO_OFF;
+    if (p->options & ~known) return fail(BIOT_ERR_INVALID_ARG, "unknown option flag");
+    if ((p->options & BIOT_OPT_COLD_FP64) && (p->options & BIOT_OPT_COLD_FP32))
+        return fail(BIOT_ERR_INVALID_ARG, "BIOT_OPT_COLD_FP64 and BIOT_OPT_COLD_FP32 exclude each other");
+    if ((p->options & BIOT_OPT_COARSE_LO_ALL) && (p->options & BIOT_OPT_COARSE_LO_OFF))
+        return fail(BIOT_ERR_INVALID_ARG, "BIOT_OPT_COARSE_LO_ALL and BIOT_OPT_COARSE_LO_OFF exclude each other");
     for (int i = 0; i < 4; i++) {
         if (s[i].eta_type < BIOT_PERIODIC || s[i].eta_type > BIOT_NEUMANN || s[i].p_type < BIOT_PERIODIC || s[i].p_type > BIOT_NEUMANN)
             return fail(BIOT_ERR_INVALID_ARG, "unknown boundary type");
@@ -344,18 +343,16 @@ int set_profiles_staged(biot_ctx *h, int side, const double *eta, const double *
 // rounding a cold start leaves behind grows with the grid: at 4096^2 it is the
 // largest part of the pressure error after the first steps (1.1e-5 against 4e-6
 // with the FP64 cold start), on grids up to 1024^2 it stays far below the 1e-5
-// target.  So the FP64 cold start applies from BIOT_COLD_FP64_MIN_CELLS cells
-// (default 2048^2; 0 = always, a negative value = never).  Smaller grids, and
-// large ones without room for the FP64 copy, solve with double-float coarse
-// levels instead (coarse_lo_mode).
-bool cold_fp64_for(long long cells)
+// target.  So the FP64 cold start applies from 2048^2 cells (BIOT_OPT_COLD_FP64:
+// every grid, BIOT_OPT_COLD_FP32: none).  Smaller grids, and large ones without
+// room for the FP64 copy, solve with double-float coarse levels instead
+// (coarse_lo_mode).
+constexpr long long COLD_FP64_MIN_CELLS = 2048LL * 2048LL;
+bool cold_fp64_for(const biot_params *p)
 {
-    static long long v = -2;
-    if (v == -2) {
-        const char *e = getenv("BIOT_COLD_FP64_MIN_CELLS");
-        v = e ? atoll(e) : 2048LL * 2048LL;
-    }
-    return v >= 0 && cells >= v;
+    if (p->options & BIOT_OPT_COLD_FP64) return true;
+    if (p->options & BIOT_OPT_COLD_FP32) return false;
+    return (long long)p->nx * p->ny >= COLD_FP64_MIN_CELLS;
 }
 
 // Whether the sweeps of level l use the double-float first moments: always on
@@ -364,7 +361,7 @@ bool level_lo(const biot_ctx *h, int l, bool cold)
 {
     if (!h->lv[l].glo[0]) return false;
     if (l == h->L - 1) return true;
-    const int m = coarse_lo_mode();
+    const int m = coarse_lo_mode(&h->P);
     return m == COARSE_LO_ALL || (m == COARSE_LO_COLD && cold);
 }
 
@@ -537,10 +534,12 @@ int read_residual(biot_ctx *h)
             return fail(BIOT_ERR_DIVERGED, "non-finite pseudo-time residual: the coupled iteration diverged");
         }
     }
-    double res, gn;
+    double res, gn, sq;
     std::memcpy(&res, &h->resmax_host[0], sizeof(double));
     std::memcpy(&gn, &h->resmax_host[1], sizeof(double));
+    std::memcpy(&sq, &h->resmax_host[2], sizeof(double));
     h->last_res = res;
+    h->last_res_l2 = std::sqrt(sq);
     h->pending_res = false;
     if (!std::isfinite(res)) {
         h->diverged = 1;
@@ -672,7 +671,7 @@ int elastic_solve(biot_ctx *h)
     for (;;) {
         const bool measure = !fixed || (ne + 1 == h->P.ne_fixed);
         h->measure_cycle = measure;
-        if (measure) CUDA_TRY(cudaMemsetAsync(h->resmax, 0, 2 * sizeof(unsigned long long), h->stream));
+        if (measure) CUDA_TRY(cudaMemsetAsync(h->resmax, 0, RES_WORDS * sizeof(unsigned long long), h->stream));
         if ((rc = vcycle(h, h->L - 1, false))) return rc;
         ne++;
         h->total_cycles++;
@@ -680,13 +679,13 @@ int elastic_solve(biot_ctx *h)
             if (ne >= h->P.ne_fixed) {
                 // (a batched step issues this copy after its merged sweeps)
                 if (!h->rec)
-                    CUDA_TRY(cudaMemcpyAsync(h->resmax_host, h->resmax, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, h->stream));
+                    CUDA_TRY(cudaMemcpyAsync(h->resmax_host, h->resmax, RES_WORDS * sizeof(unsigned long long), cudaMemcpyDeviceToHost, h->stream));
                 h->pending_res = true;
                 break;
             }
             continue;
         }
-        CUDA_TRY(cudaMemcpyAsync(h->resmax_host, h->resmax, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, h->stream));
+        CUDA_TRY(cudaMemcpyAsync(h->resmax_host, h->resmax, RES_WORDS * sizeof(unsigned long long), cudaMemcpyDeviceToHost, h->stream));
         if ((rc = read_residual(h))) return rc;
         double gn;
         std::memcpy(&gn, &h->resmax_host[1], sizeof(double));
@@ -734,7 +733,7 @@ int elastic_solve_device_loop(biot_ctx *h)
     CUDA_TRY(cudaGraphConditionalHandleCreate(&cond, cg, 0, cudaGraphCondAssignDefault));
     // first V-cycle of the step
     h->measure_cycle = true;
-    CUDA_TRY(cudaMemsetAsync(h->resmax, 0, 2 * sizeof(unsigned long long), h->stream));
+    CUDA_TRY(cudaMemsetAsync(h->resmax, 0, RES_WORDS * sizeof(unsigned long long), h->stream));
     if ((rc = vcycle(h, h->L - 1, false))) return rc;
     if ((rc = stop_test(h, 1, cond))) return rc;
     // WHILE node after it
@@ -751,7 +750,7 @@ int elastic_solve_device_loop(biot_ctx *h)
     cudaStream_t main = h->stream;
     h->stream = h->aux_stream;
     rc = BIOT_OK;
-    cudaError_t e = cudaMemsetAsync(h->resmax, 0, 2 * sizeof(unsigned long long), h->stream);
+    cudaError_t e = cudaMemsetAsync(h->resmax, 0, RES_WORDS * sizeof(unsigned long long), h->stream);
     if (e != cudaSuccess) rc = fail(BIOT_ERR_CUDA, std::string("cudaMemsetAsync: ") + cudaGetErrorString(e));
     if (!rc) rc = vcycle(h, h->L - 1, false);
     if (!rc) rc = stop_test(h, 0, cond);
@@ -762,7 +761,7 @@ int elastic_solve_device_loop(biot_ctx *h)
     if (e != cudaSuccess) return fail(BIOT_ERR_CUDA, std::string("cudaStreamEndCapture (loop body): ") + cudaGetErrorString(e));
     CUDA_TRY(cudaStreamUpdateCaptureDependencies(h->stream, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
     // counters and the last residual back to the host once per step
-    CUDA_TRY(cudaMemcpyAsync(h->resmax_host, h->resmax, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(cudaMemcpyAsync(h->resmax_host, h->resmax, RES_WORDS * sizeof(unsigned long long), cudaMemcpyDeviceToHost, h->stream));
     CUDA_TRY(cudaMemcpyAsync(h->stop_host, h->stop, sizeof(StopState), cudaMemcpyDeviceToHost, h->stream));
     h->pending_res = true;
     h->pending_stop = true;
@@ -1119,10 +1118,15 @@ int create_instance(const biot_params *p, const biot_side sides[4], biot_handle 
     }
     biot_ctx *h = new (std::nothrow) biot_ctx();
     if (!h) return fail(BIOT_ERR_OOM, "host allocation failed");
+    if (cudaGetDevice(&h->device) != cudaSuccess) {
+        cudaGetLastError();
+        delete h;
+        return fail(BIOT_ERR_CUDA, "cudaGetDevice failed");
+    }
     h->P = *p;
     h->L = p->mg_levels;
     h->fp32 = p->precision != BIOT_FP64;  // finest level and flow populations in FP32
-    h->cold64 = h->fp32 && cold_fp64_for((long long)p->nx * p->ny);
+    h->cold64 = h->fp32 && cold_fp64_for(p);
     h->h = p->lx / p->nx;
     h->lam = p->c0 * p->lambda;
     h->mu = p->c0 * p->mu;
@@ -1157,13 +1161,13 @@ int create_instance(const biot_params *p, const biot_side sides[4], biot_handle 
         Lv.nx = p->nx >> shift;
         Lv.ny = p->ny >> shift;
         Lv.np = (size_t)Lv.nx * Lv.ny;
-        // FP64: the FP64 path; the coarsest level with BIOT_COARSEST_FP64=1; with
-        // BIOT_FP32_COARSE64 every level below the finest
-        Lv.fp64 = !h->fp32 || (l == 0 && h->L > 1 && coarsest_fp64()) || (p->precision == BIOT_FP32_COARSE64 && l < h->L - 1);
+        // FP64: the FP64 path; the coarsest level below a finer one unless
+        // BIOT_OPT_COARSEST_STORAGE; with BIOT_FP32_COARSE64 every level below the finest
+        Lv.fp64 = !h->fp32 || (l == 0 && h->L > 1 && coarsest_fp64(p)) || (p->precision == BIOT_FP32_COARSE64 && l < h->L - 1);
         const size_t esz = Lv.fp64 ? sizeof(double) : sizeof(float);
         TRY_RC(dev_alloc(h, &Lv.g[0], 8 * Lv.np * esz));
         TRY_RC(dev_alloc(h, &Lv.g[1], 8 * Lv.np * esz));
-        if (!Lv.fp64 && (l == h->L - 1 || coarse_lo_mode() != COARSE_LO_OFF)) {  // double-float displacement moments
+        if (!Lv.fp64 && (l == h->L - 1 || coarse_lo_mode(p) != COARSE_LO_OFF)) {  // double-float displacement moments
             TRY_RC(dev_alloc(h, &Lv.glo[0], 2 * Lv.np * esz));
             TRY_RC(dev_alloc(h, &Lv.glo[1], 2 * Lv.np * esz));
         }
@@ -1182,9 +1186,9 @@ int create_instance(const biot_params *p, const biot_side sides[4], biot_handle 
     TRY_RC(dev_alloc(h, &h->dB[0], np * tsz));
     TRY_RC(dev_alloc(h, &h->dB[1], np * tsz));
     TRY_RC(dev_alloc(h, (void **)&h->SE, np * sizeof(double)));
-    TRY_RC(dev_alloc(h, (void **)&h->resmax, 2 * sizeof(unsigned long long)));
+    TRY_RC(dev_alloc(h, (void **)&h->resmax, RES_WORDS * sizeof(unsigned long long)));
     TRY_RC(dev_alloc(h, (void **)&h->stop, sizeof(StopState)));
-    if (!h->host_lent && (cudaMallocHost((void **)&h->resmax_host, 2 * sizeof(unsigned long long)) != cudaSuccess ||
+    if (!h->host_lent && (cudaMallocHost((void **)&h->resmax_host, RES_WORDS * sizeof(unsigned long long)) != cudaSuccess ||
                           cudaMallocHost((void **)&h->stop_host, sizeof(StopState)) != cudaSuccess)) {
         cudaGetLastError();
         release(h);
@@ -1383,6 +1387,7 @@ int biot_stats_get(biot_handle h, biot_stats *o)
     int rc = finish_pending(h);
     o->last_ne = h->last_ne;
     o->last_res = h->last_res;
+    o->last_res_l2 = h->last_res_l2;
     o->total_cycles = h->total_cycles;
     o->notconv_steps = h->notconv_steps;
     o->diverged = h->diverged;
@@ -1436,12 +1441,10 @@ static __device__ __align__(256) double g_noalloc_eta[2 * (size_t)BIOT_NOALLOC_M
 std::mutex g_noalloc_mu;
 double *g_noalloc_addr[NOALLOC_MAX_DEVICES] = {};
 
-// Device address of the staging array on the current device, looked up once
-// per device with that device current.
-int noalloc_scratch(double **out)
+// Device address of the staging array on device dev, looked up once per device
+// with that device current (the caller has checked that it is).
+int noalloc_scratch(int dev, double **out)
 {
-    int dev = -1;
-    CUDA_TRY(cudaGetDevice(&dev));
     if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return fail(BIOT_ERR_INVALID_ARG, "device ordinal out of range for the static read-out array");
     std::lock_guard<std::mutex> lock(g_noalloc_mu);
     if (!g_noalloc_addr[dev]) {
@@ -1465,8 +1468,18 @@ extern "C" int biot_read_u_noalloc(biot_handle h, double *eta, double *t_out)
         return fail(BIOT_ERR_INVALID_ARG, "biot_read_u_noalloc: the grid has " + std::to_string(np) +
                                               " cells, more than the static read-out array holds (" +
                                               std::to_string(BIOT_NOALLOC_MAX_CELLS) + "); use biot_read_u");
+    int cur = -1;
+    CUDA_TRY(cudaGetDevice(&cur));
+    if (cur != h->device)
+        return fail(BIOT_ERR_INVALID_ARG, "biot_read_u_noalloc: the instance lives on device " + std::to_string(h->device) +
+                                              " but device " + std::to_string(cur) + " is current; make it current first");
+    // the solve at t = 0 of a large FP32 instance runs on an FP64 copy that
+    // biot_create allocates: not on this path
+    if (h->cold64 && h->nstep == 0 && !h->solved)
+        return fail(BIOT_ERR_INVALID_ARG, "biot_read_u_noalloc: the pending solve at t = 0 of this instance allocates "
+                                          "an FP64 copy; step it (biot_step) or read it with biot_read_u first");
     double *scratch = nullptr;
-    int rc = noalloc_scratch(&scratch);
+    int rc = noalloc_scratch(h->device, &scratch);
     if (rc) return rc;
     if ((rc = ensure_initialized(h))) return rc;
     if (!h->solved) {  // as biot_read_u: a step that hit ne_max still reads out
@@ -1497,19 +1510,10 @@ extern "C" int biot_read_u_noalloc(biot_handle h, double *eta, double *t_out)
 // ============================================================================
 namespace {
 
-// In a batch, levels of at most this many cells run as tiles (default 128^2,
-// whose rows would fill only 128 of the 248 columns of two strips; the
-// environment variable BIOT_BATCH_TILE_MAX_CELLS overrides it).
-long batch_tile_max_cells()
-{
-    static long v = -1;
-    if (v < 0) {
-        const char *e = getenv("BIOT_BATCH_TILE_MAX_CELLS");
-        v = e ? atol(e) : 128L * 128L;
-        if (v < 0) v = 0;
-    }
-    return v;
-}
+// In a batch, levels of at most this many cells run as tiles: a 128^2 level's
+// rows would fill only 128 of the 248 columns of two strips.
+constexpr long BATCH_TILE_MAX_CELLS = 128L * 128L;
+long batch_tile_max_cells() { return BATCH_TILE_MAX_CELLS; }
 
 // One sweep of the static schedule of an instance.
 struct PlanOp {
@@ -1823,7 +1827,7 @@ int batch_capture(biot_batch_s *b, int par)
     }
     for (int i = 0; i < n && !rc; i++) {
         biot_ctx *h = b->inst[i];
-        cudaError_t e = cudaMemcpyAsync(h->resmax_host, h->resmax, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, b->stream);
+        cudaError_t e = cudaMemcpyAsync(h->resmax_host, h->resmax, RES_WORDS * sizeof(unsigned long long), cudaMemcpyDeviceToHost, b->stream);
         if (e != cudaSuccess) rc = fail(BIOT_ERR_CUDA, std::string("cudaMemcpyAsync: ") + cudaGetErrorString(e));
     }
     cudaGraph_t g = nullptr;
@@ -2055,11 +2059,11 @@ size_t estimate_bytes(const biot_params *p, const biot_side *sides)
     for (int l = 0; l < p->mg_levels; l++) {
         const int shift = p->mg_levels - 1 - l;
         const size_t nx = (size_t)(p->nx >> shift), ny = (size_t)(p->ny >> shift), n = nx * ny;
-        const bool fp64 = !fp32 || (l == 0 && p->mg_levels > 1 && coarsest_fp64()) ||
+        const bool fp64 = !fp32 || (l == 0 && p->mg_levels > 1 && coarsest_fp64(p)) ||
                           (p->precision == BIOT_FP32_COARSE64 && l < p->mg_levels - 1);
         const size_t esz = fp64 ? 8 : 4;
         b += 2 * 8 * n * esz;
-        if (!fp64 && (l == p->mg_levels - 1 || coarse_lo_mode() != COARSE_LO_OFF)) b += 2 * 2 * n * esz;
+        if (!fp64 && (l == p->mg_levels - 1 || coarse_lo_mode(p) != COARSE_LO_OFF)) b += 2 * 2 * n * esz;
         if (l < p->mg_levels - 1) b += 8 * n * esz;
         for (int s = 0; s < 4; s++)
             if (sides && sides[s].eta_type == BIOT_DIRICHLET) b += 3 * ((s == BIOT_BOTTOM || s == BIOT_TOP) ? nx : ny) * esz;
@@ -2117,7 +2121,7 @@ struct biot_server_s {
     unsigned char *host_arena = nullptr;
     std::vector<int> free_slots;  // worker thread only
     static constexpr size_t SLOT_BYTES = 256;
-    static_assert(2 * sizeof(unsigned long long) + sizeof(StopState) <= SLOT_BYTES, "arena slot");
+    static_assert(RES_WORDS * sizeof(unsigned long long) + sizeof(StopState) <= SLOT_BYTES, "arena slot");
     double now() const { return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count(); }
 };
 
@@ -2182,7 +2186,7 @@ void server_loop(biot_server_s *S)
                 S->free_slots.pop_back();
                 unsigned char *slot = S->host_arena + (size_t)r->host_slot * biot_server_s::SLOT_BYTES;
                 const Lend lend{S->pool, reinterpret_cast<unsigned long long *>(slot),
-                                reinterpret_cast<StopState *>(slot + 2 * sizeof(unsigned long long))};
+                                reinterpret_cast<StopState *>(slot + RES_WORDS * sizeof(unsigned long long))};
                 rc = create_instance(&r->P, r->sides, &h, &lend);
             } else {
                 rc = create_instance(&r->P, r->sides, &h, nullptr);
@@ -2345,7 +2349,7 @@ int biot_server_submit(biot_server S, const biot_params *p, const biot_side side
     r.P = *p;
     r.target = (long)std::floor(T / p->dt + 0.5);
     r.bytes = estimate_bytes(p, sides);
-    if (p->precision != BIOT_FP64 && cold_fp64_for((long long)p->nx * p->ny)) {
+    if (p->precision != BIOT_FP64 && cold_fp64_for(p)) {
         biot_params p64 = *p;
         p64.precision = BIOT_FP64;
         r.shadow = estimate_bytes(&p64, sides);

@@ -132,6 +132,19 @@ __device__ __forceinline__ T pop_absmax(const T (&m)[8])
     return r;
 }
 
+// Sum of the squared populations of a moment vector, sum_k g_k^2 =
+// 1/2 sum_p (S_p^2 + A_p^2), in the storage type.
+template <typename T>
+__device__ __forceinline__ T pop_sumsq(const T (&m)[8])
+{
+    T S[4], A[4];
+    moments_to_pairs(m, S, A);
+    T r = T(0);
+#pragma unroll
+    for (int p = 0; p < 4; p++) r += S[p] * S[p] + A[p] * A[p];
+    return T(0.5) * r;
+}
+
 // Lattice traction term eps * varsigma of eq. BC:traction for the incoming
 // direction (cx, cy) at a wall, per unit of c0 h (the left-wall values are the
 // paper's; the other walls follow by rotating the square).

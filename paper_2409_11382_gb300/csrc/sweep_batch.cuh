@@ -31,7 +31,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 7 : 1)
     k_sweep_batch(const __grid_constant__ BatchParams<T, TC> P)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ double red[2][NT / 32];
+    __shared__ double red[3][NT / 32];
     const int j = batch_job(P, blockIdx.x);
     const int local = blockIdx.x - P.start[j], sx = P.sx[j];
     sweep_strip<T, TC, NT, KIND, LO, RESTRICT>(P.job[j], local % sx, local / sx, P.ty[j], smem_raw, red);
@@ -43,7 +43,7 @@ __global__ void __launch_bounds__(TileShape<TX, TY>::NT)
     k_sweep_tile_batch(const __grid_constant__ BatchParams<T, TC> P)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ double red[2][TileShape<TX, TY>::NT / 32];
+    __shared__ double red[3][TileShape<TX, TY>::NT / 32];
     const int j = batch_job(P, blockIdx.x);
     const int local = blockIdx.x - P.start[j], sx = P.sx[j];
     tile_body<T, TC, TX, TY, KIND, LO, RESTRICT>(P.job[j], local % sx, local / sx, smem_raw, red);

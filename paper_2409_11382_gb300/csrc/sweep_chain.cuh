@@ -17,7 +17,7 @@ __global__ void __launch_bounds__(TileShape<SWEEP_CHAIN_MAX, SWEEP_CHAIN_MAX>::N
 {
     constexpr int TX = SWEEP_CHAIN_MAX, TY = SWEEP_CHAIN_MAX;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ double red[2][TileShape<TX, TY>::NT / 32];
+    __shared__ double red[3][TileShape<TX, TY>::NT / 32];
     __shared__ SweepArgs<T, TC> a;
     if (threadIdx.x == 0) a = a0;
     __syncthreads();

@@ -584,7 +584,7 @@ __device__ __forceinline__ void residual_cell(const SweepArgs<T, TC> &a, const R
 // of both the single-instance kernel and the batched work-list kernel.
 template <typename T, typename TC, int NT, int KIND, bool LO, bool RESTRICT>
 __device__ __forceinline__ void sweep_strip(const SweepArgs<T, TC> &a, int bx, int by, int TY, unsigned char *smem_raw,
-                                            double (&red)[2][NT / 32])
+                                            double (&red)[3][NT / 32])
 {
     using L = RingLayout<KIND, LO>;
     constexpr int W = NT, RV = L::RV;
@@ -636,6 +636,7 @@ __device__ __forceinline__ void sweep_strip(const SweepArgs<T, TC> &a, int bx, i
     __syncthreads();
 
     T rmax = T(0), gmax = T(0);
+    double rsum = 0.0;  // FP64 sum of the squared population residuals (measured sweeps)
     T acc[8];
 #pragma unroll
     for (int k = 0; k < 8; k++) acc[k] = T(0);
@@ -680,6 +681,7 @@ __device__ __forceinline__ void sweep_strip(const SweepArgs<T, TC> &a, int bx, i
                 if (a.resmax) {
                     rmax = fmax(rmax, pop_absmax(d));
                     gmax = fmax(gmax, pop_absmax(gcur));
+                    rsum += (double)pop_sumsq(d);
                 }
             }
         }
@@ -716,21 +718,25 @@ __device__ __forceinline__ void sweep_strip(const SweepArgs<T, TC> &a, int bx, i
         for (int o = 16; o > 0; o >>= 1) {
             rmax = fmax(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
             gmax = fmax(gmax, __shfl_xor_sync(0xffffffffu, gmax, o));
+            rsum += __shfl_xor_sync(0xffffffffu, rsum, o);
         }
         const int warp = t >> 5, lane = t & 31;
         if (lane == 0) {
             red[0][warp] = (double)rmax;
             red[1][warp] = (double)gmax;
+            red[2][warp] = rsum;
         }
         __syncthreads();
         if (t == 0) {
-            double r0 = 0.0, g0 = 0.0;
+            double r0 = 0.0, g0 = 0.0, q0 = 0.0;
             for (int w = 0; w < NT / 32; w++) {
                 r0 = fmax(r0, red[0][w]);
                 g0 = fmax(g0, red[1][w]);
+                q0 += red[2][w];
             }
             atomicMax(&a.resmax[0], (unsigned long long)__double_as_longlong(r0));
             atomicMax(&a.resmax[1], (unsigned long long)__double_as_longlong(g0));
+            atomicAdd(reinterpret_cast<double *>(&a.resmax[2]), q0);
         }
     }
 }
@@ -739,7 +745,7 @@ template <typename T, typename TC, int NT, int KIND, bool LO, bool RESTRICT>
 __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 6 : 1) k_sweep_mom(const SweepArgs<T, TC> a, int TY)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ double red[2][NT / 32];
+    __shared__ double red[3][NT / 32];
     sweep_strip<T, TC, NT, KIND, LO, RESTRICT>(a, blockIdx.x, blockIdx.y, TY, smem_raw, red);
 }
 
@@ -766,7 +772,7 @@ constexpr size_t tile_smem_bytes()
 
 template <typename T, typename TC, int TX, int TY, int KIND, bool LO, bool RESTRICT>
 __device__ __forceinline__ void tile_body(const SweepArgs<T, TC> &a, int bx, int by, unsigned char *smem_raw,
-                                          double (&red)[2][TileShape<TX, TY>::NT / 32])
+                                          double (&red)[3][TileShape<TX, TY>::NT / 32])
 {
     using L = RingLayout<KIND, LO>;
     using S = TileShape<TX, TY>;
@@ -798,6 +804,7 @@ __device__ __forceinline__ void tile_body(const SweepArgs<T, TC> &a, int bx, int
     __syncthreads();
 
     T rmax = T(0), gmax = T(0);
+    double rsum = 0.0;
     const bool writes = live && c >= 2 && c < W - 2 && rrow >= 2 && rrow < R - 2 && x < nx && y < ny;
     T d[8];
 #pragma unroll
@@ -830,6 +837,7 @@ __device__ __forceinline__ void tile_body(const SweepArgs<T, TC> &a, int bx, int
             if (a.resmax) {
                 rmax = pop_absmax(d);
                 gmax = pop_absmax(gcur);
+                rsum = (double)pop_sumsq(d);
             }
         } else {
             const int i = (rrow - 2) * TX + (c - 2);
@@ -862,21 +870,25 @@ __device__ __forceinline__ void tile_body(const SweepArgs<T, TC> &a, int bx, int
         for (int o = 16; o > 0; o >>= 1) {
             rmax = fmax(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
             gmax = fmax(gmax, __shfl_xor_sync(0xffffffffu, gmax, o));
+            rsum += __shfl_xor_sync(0xffffffffu, rsum, o);
         }
         const int warp = tid >> 5, lane = tid & 31;
         if (lane == 0) {
             red[0][warp] = (double)rmax;
             red[1][warp] = (double)gmax;
+            red[2][warp] = rsum;
         }
         __syncthreads();
         if (tid == 0) {
-            double r0 = 0.0, g0 = 0.0;
+            double r0 = 0.0, g0 = 0.0, q0 = 0.0;
             for (int w = 0; w < NT / 32; w++) {
                 r0 = fmax(r0, red[0][w]);
                 g0 = fmax(g0, red[1][w]);
+                q0 += red[2][w];
             }
             atomicMax(&a.resmax[0], (unsigned long long)__double_as_longlong(r0));
             atomicMax(&a.resmax[1], (unsigned long long)__double_as_longlong(g0));
+            atomicAdd(reinterpret_cast<double *>(&a.resmax[2]), q0);
         }
     }
 }
@@ -885,7 +897,7 @@ template <typename T, typename TC, int TX, int TY, int KIND, bool LO, bool RESTR
 __global__ void __launch_bounds__(TileShape<TX, TY>::NT) k_sweep_tile(const SweepArgs<T, TC> a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ double red[2][TileShape<TX, TY>::NT / 32];
+    __shared__ double red[3][TileShape<TX, TY>::NT / 32];
     tile_body<T, TC, TX, TY, KIND, LO, RESTRICT>(a, blockIdx.x, blockIdx.y, smem_raw, red);
 }
 
@@ -897,18 +909,8 @@ template <> struct TileFor<double> { static constexpr int X = 8, Y = 2; };
 static_assert(TileFor<float>::X == 32 && TileFor<float>::Y == 8 && TileFor<double>::X == 8 && TileFor<double>::Y == 2,
               "tile shapes shared with the host planner (sweep_tile_shape)");
 
-// Levels of at most this many cells use the tile sweep (default 256^2; the
-// environment variable BIOT_SWEEP_TILE_MAX_CELLS overrides it, 0 disables).
-inline long sweep_tile_max_cells()
-{
-    static long v = -1;
-    if (v < 0) {
-        const char *e = getenv("BIOT_SWEEP_TILE_MAX_CELLS");
-        v = e ? atol(e) : SWEEP_TILE_CELLS;
-        if (v < 0) v = 0;
-    }
-    return v;
-}
+// Levels of at most this many cells use the tile sweep.
+inline long sweep_tile_max_cells() { return SWEEP_TILE_CELLS; }
 
 template <typename T, typename TC, int KIND, bool LO, bool RESTRICT>
 cudaError_t launch_tile(const SweepArgs<T, TC> &a, cudaStream_t s)

@@ -28,11 +28,13 @@ def test_step_model_terzaghi_4096_fp32():
     fine = cells[-1]
     restrict_fine = (5 + 2 + 2) * 4 + 5 * 4 / 4
     coarse = 0.0
-    for l in range(L - 1):  # every coarse level in FP32, the coarsest included
-        prol = 5 * 4 / 4 / (2 * K) if l > 0 else 0.0
-        coarse += ne * 2 * K * cells[l] * ((5 * 2 + 5) * 4 + prol)
+    for l in range(L - 1):  # coarse levels in FP32, the coarsest (l = 0) in FP64
+        e = 8 if l == 0 else 4
+        ec = 8 if l == 1 else 4  # the storage of the next coarser level (prolongation, restriction)
+        prol = 5 * ec / 4 / (2 * K) if l > 0 else 0.0
+        coarse += ne * 2 * K * cells[l] * ((5 * 2 + 5) * e + prol)
         if l > 0:
-            coarse += ne * cells[l] * ((5 + 5) * 4 + 5 * 4 / 4)
+            coarse += ne * cells[l] * ((5 + 5) * e + 5 * ec / 4)
     # flow: 9 f in and out, m_s, D(t - dt) (FP64), previous difference in;
     # D(t) (FP64), new difference, F~ (2) out
     flow = fine * (9 * 4 * 2 + 4 + 8 + 4 + 8 + 4 + 2 * 4)
@@ -42,13 +44,19 @@ def test_step_model_terzaghi_4096_fp32():
     assert nb / fine == pytest.approx(2312, abs=1.0)
 
 
-def test_step_model_follows_the_coarsest_precision_switch(monkeypatch):
+def test_step_model_follows_the_coarsest_precision_option():
     p, _, _ = W.terzaghi_4097()
-    _, nb32 = bench.step_model(p, 4096, fp64=False)
-    monkeypatch.setenv("BIOT_COARSEST_FP64", "1")
     _, nb64 = bench.step_model(p, 4096, fp64=False)
+    _, nb32 = bench.step_model(dict(p, options=bench.OPT_COARSEST_STORAGE), 4096, fp64=False)
     # the 8^2 level's bytes double and its prolongation into 16^2 doubles
     assert 0 < nb64 - nb32 < 1e-5 * nb32
+
+
+def test_precision_label_states_what_runs():
+    p, _, _ = W.terzaghi_4097()
+    assert "coarsest level" in bench.precision_label(p, False)
+    assert "coarsest level fp32" in bench.precision_label(dict(p, options=bench.OPT_COARSEST_STORAGE), False)
+    assert bench.precision_label(p, True) == "fp64 storage and arithmetic"
 
 
 def test_step_model_fp64_has_no_low_parts():

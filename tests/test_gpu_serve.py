@@ -1,6 +1,8 @@
 """Serving (biot_server_*): requests that arrive while others run are admitted
 as memory and slots free up, their steps overlap on the GPU, and each result is
-the same as the request solved alone (same kernels and arguments: bitwise)."""
+the same as the request solved alone (same kernels and arguments: bitwise) and
+within the FP32 tolerance (1e-5 relative L-infinity of eta and p) of the FP64
+oracle -- checked for one request of every size in the mix."""
 import time
 
 import numpy as np
@@ -9,7 +11,14 @@ import pytest
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
+from oracle import oracle as O  # noqa: E402
 from paper_2409_11382_gb300 import biot, workloads as W  # noqa: E402
+
+TOL32 = 1e-5
+
+
+def rel(a, b):
+    return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -51,6 +60,20 @@ def test_served_results_equal_solo_runs_and_overlap():
         (eta_a, t_a), p_a = alone(p, s, T)
         assert t == pytest.approx(t_a)
         assert np.array_equal(eta, eta_a) and np.array_equal(pr, p_a)
+    # one served result of every size against the FP64 oracle
+    seen = set()
+    for (arrival, p, s, T), (eta, pr, t) in zip(reqs, results):
+        if p["nx"] in seen:
+            continue
+        seen.add(p["nx"])
+        o = O.Oracle(dict(p, precision=W.FP64), s)
+        o.solve_to(T)
+        eta_o, t_o = o.read_u()
+        p_o, _ = o.read_p()
+        o.close()
+        assert t == pytest.approx(t_o)
+        assert rel(eta, eta_o) < TOL32 and rel(pr, p_o) < TOL32, (p["nx"], rel(eta, eta_o), rel(pr, p_o))
+    assert len(seen) >= 2
 
 
 def test_request_larger_than_budget_is_rejected():
