@@ -633,6 +633,7 @@ int cold_start_fp64(biot_ctx *h)
         h->notconv_steps += s->notconv_steps;
         h->last_ne = s->last_ne;
         h->last_res = s->last_res;
+        h->last_res_l2 = s->last_res_l2;
         h->initialized = true;
         h->solved = true;
         h->pending_res = false;
@@ -2068,7 +2069,7 @@ size_t estimate_bytes(const biot_params *p, const biot_side *sides)
         for (int s = 0; s < 4; s++)
             if (sides && sides[s].eta_type == BIOT_DIRICHLET) b += 3 * ((s == BIOT_BOTTOM || s == BIOT_TOP) ? nx : ny) * esz;
     }
-    b += (2 * 9 + 2 + 2) * np * tsz + 3 * np * 8 + 16 + sizeof(StopState);
+    b += (2 * 9 + 2 + 2) * np * tsz + 3 * np * 8 + RES_WORDS * sizeof(unsigned long long) + sizeof(StopState);
     for (int s = 0; s < 4; s++) {
         const size_t m = 2 * (size_t)((s == BIOT_BOTTOM || s == BIOT_TOP) ? p->nx : p->ny) + 1;
         if (sides && sides[s].eta_profile) b += 2 * m * 8;

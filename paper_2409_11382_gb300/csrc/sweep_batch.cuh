@@ -26,15 +26,15 @@ __device__ __forceinline__ int batch_job(const BatchParams<T, TC> &P, int b)
 // jobs of one launch may belong to different instances and different multigrid
 // levels of one storage kind).  The arguments are read from the launch's
 // parameter block, which lives in constant memory.
-template <typename T, typename TC, int NT, int KIND, bool LO, bool RESTRICT>
-__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 7 : 1)
+template <typename T, typename TC, int NT, int CPT, int KIND, bool LO, bool RESTRICT>
+__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 896 / (NT * CPT) : 1)
     k_sweep_batch(const __grid_constant__ BatchParams<T, TC> P)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double red[3][NT / 32];
     const int j = batch_job(P, blockIdx.x);
     const int local = blockIdx.x - P.start[j], sx = P.sx[j];
-    sweep_strip<T, TC, NT, KIND, LO, RESTRICT>(P.job[j], local % sx, local / sx, P.ty[j], smem_raw, red);
+    sweep_strip<T, TC, NT, CPT, KIND, LO, RESTRICT>(P.job[j], local % sx, local / sx, P.ty[j], smem_raw, red);
 }
 
 // Batched form: CTA b processes work item b, a tile of the sweep of its job.
@@ -71,12 +71,12 @@ cudaError_t launch_tile_batch(const BatchParams<T, TC> &P, cudaStream_t s)
 // first use).
 template <typename T, typename TC, int KIND, bool LO, bool RESTRICT>
 struct BatchKernel {
-    static constexpr size_t smem = rows_smem_bytes<T, KIND, LO, SWEEP_NT>();
+    static constexpr size_t smem = rows_smem_bytes<T, KIND, LO, SWEEP_NT * SWEEP_CPT>();
     static int slots()
     {
         static int n = 0;
         if (!n) {
-            auto k = k_sweep_batch<T, TC, SWEEP_NT, KIND, LO, RESTRICT>;
+            auto k = k_sweep_batch<T, TC, SWEEP_NT, SWEEP_CPT, KIND, LO, RESTRICT>;
             if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
             int dev = 0, sms = 0, per_sm = 0;
             if (cudaGetDevice(&dev) != cudaSuccess) return 0;
@@ -95,7 +95,7 @@ cudaError_t launch_batch_v(const BatchParams<T, TC> &P, cudaStream_t s)
     const int n = P.start[P.njobs];
     if (n <= 0) return cudaSuccess;
     if (!BK::slots()) return cudaErrorInvalidConfiguration;
-    k_sweep_batch<T, TC, SWEEP_NT, KIND, LO, RESTRICT><<<n, SWEEP_NT, BK::smem, s>>>(P);
+    k_sweep_batch<T, TC, SWEEP_NT, SWEEP_CPT, KIND, LO, RESTRICT><<<n, SWEEP_NT, BK::smem, s>>>(P);
     return cudaGetLastError();
 }
 

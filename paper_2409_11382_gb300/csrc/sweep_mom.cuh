@@ -581,13 +581,18 @@ __device__ __forceinline__ void residual_cell(const SweepArgs<T, TC> &a, const R
 }
 
 // One strip (column block bx, row block by of TY rows) of one sweep; the body
-// of both the single-instance kernel and the batched work-list kernel.
-template <typename T, typename TC, int NT, int KIND, bool LO, bool RESTRICT>
+// of both the single-instance kernel and the batched work-list kernel.  The CTA
+// has NT threads and a window of W = NT * CPT columns: thread t owns the ring
+// columns t, t + NT, ..., so every plane access of a warp stays on consecutive
+// words, and the per-row work that does not depend on the column -- ring slots,
+// loop control, barriers, row predicates -- is shared by the thread's CPT cells.
+template <typename T, typename TC, int NT, int CPT, int KIND, bool LO, bool RESTRICT>
 __device__ __forceinline__ void sweep_strip(const SweepArgs<T, TC> &a, int bx, int by, int TY, unsigned char *smem_raw,
                                             double (&red)[3][NT / 32])
 {
     using L = RingLayout<KIND, LO>;
-    constexpr int W = NT, RV = L::RV;
+    constexpr int W = NT * CPT, RV = L::RV;
+    static_assert(NT % 32 == 0 && NT % 2 == 0, "whole warps; even column offsets keep restriction pairs in one warp");
     Rings<T, W, KIND, LO> rg;
     rg.carve(smem_raw, 3);
 
@@ -596,26 +601,40 @@ __device__ __forceinline__ void sweep_strip(const SweepArgs<T, TC> &a, int bx, i
     const bool perx = a.bc[SIDE_LEFT] == BC_PERIODIC;
     const bool pery = a.bc[SIDE_BOTTOM] == BC_PERIODIC;
     const int t = threadIdx.x;
-    const int x0 = bx * (NT - 4), y0 = by * TY;
+    const int x0 = bx * (W - 4), y0 = by * TY;
     const int y1 = min(y0 + TY, ny);
 
-    const int x = x0 - 2 + t;  // this thread's column (ring column t)
-    const bool loads = perx || x < nx + 2;                           // a real, wrapped or ghost column
-    const bool collides = t >= 1 && t < NT - 1 && (perx || (x >= 0 && x < nx));
-    const bool writes = t >= 2 && t < NT - 2 && x < nx;
-    const bool wall_col = !perx && (x == 0 || x == nx - 1);
+    // this thread's columns x[j] = x0 - 2 + c[j], ring columns c[j] = t + j NT
+    int xj[CPT], cj[CPT];
+    bool loads[CPT], collides[CPT], writes[CPT], wall_col[CPT];
+#pragma unroll
+    for (int j = 0; j < CPT; j++) {
+        cj[j] = t + j * NT;
+        xj[j] = x0 - 2 + cj[j];
+        loads[j] = perx || xj[j] < nx + 2;  // a real, wrapped or ghost column
+        collides[j] = cj[j] >= 1 && cj[j] < W - 1 && (perx || (xj[j] >= 0 && xj[j] < nx));
+        writes[j] = cj[j] >= 2 && cj[j] < W - 2 && xj[j] < nx;
+        wall_col[j] = !perx && (xj[j] == 0 || xj[j] == nx - 1);
+    }
 
     auto row_ok = [&](int y) { return pery || (y >= 0 && y < ny); };
 
-    T pv[RV];
+    T pv[CPT][RV];
     auto fetch_row = [&](int y) {
-        if (loads) fetch_cell<T, TC, KIND, LO, RV>(a, x, y, NP, perx, pery, pv);
+#pragma unroll
+        for (int j = 0; j < CPT; j++)
+            if (loads[j]) fetch_cell<T, TC, KIND, LO, RV>(a, xj[j], y, NP, perx, pery, pv[j]);
     };
     auto store_row = [&](int s) {
-        if (loads) store_cell<T, W, KIND, LO, RV>(rg, s, t, pv);
+#pragma unroll
+        for (int j = 0; j < CPT; j++)
+            if (loads[j]) store_cell<T, W, KIND, LO, RV>(rg, s, cj[j], pv[j]);
     };
     auto collide_row = [&](int y, int sm, int s, int sp) {
-        if (collides && row_ok(y)) collide_cell<T, TC, KIND, LO, W>(a, rg, sm, s, sp, t);
+        if (!row_ok(y)) return;
+#pragma unroll
+        for (int j = 0; j < CPT; j++)
+            if (collides[j]) collide_cell<T, TC, KIND, LO, W>(a, rg, sm, s, sp, cj[j]);
     };
 
     // ring slots: rows y0-2, y0-1, y0 in slots 0, 1, 2; row r in slot (r - y0 + 2) % 3
@@ -637,9 +656,11 @@ __device__ __forceinline__ void sweep_strip(const SweepArgs<T, TC> &a, int bx, i
 
     T rmax = T(0), gmax = T(0);
     double rsum = 0.0;  // FP64 sum of the squared population residuals (measured sweeps)
-    T acc[8];
+    T acc[CPT][8];
 #pragma unroll
-    for (int k = 0; k < 8; k++) acc[k] = T(0);
+    for (int j = 0; j < CPT; j++)
+#pragma unroll
+        for (int k = 0; k < 8; k++) acc[j][k] = T(0);
     const T gam = a.k_gam;
     // slots of rows y-1, y, y+1 (row y+2 reuses the slot of row y-1)
     int sa = 1, sb = 2, sc = 0;
@@ -651,58 +672,62 @@ __device__ __forceinline__ void sweep_strip(const SweepArgs<T, TC> &a, int bx, i
         collide_row(y + 1, sb, sc, sa);
         __syncthreads();   // (E)
         const int sl[3] = {sa, sb, sc};
-        T d[8];
+        const bool wall_row = !pery && (y == 0 || y == ny - 1);
 #pragma unroll
-        for (int k = 0; k < 8; k++) d[k] = T(0);
-        if (writes) {
-            const OwnCell<T> own = own_cell<T, W, KIND, LO>(rg, sb, t);
-            const T(&gcur)[8] = own.g;
-            const bool wall = wall_col || (!pery && (y == 0 || y == ny - 1));
-            if (wall) residual_cell<T, TC, KIND, LO, W, true>(a, rg, x, y, sl, t, perx, pery, own, d);
-            else residual_cell<T, TC, KIND, LO, W, false>(a, rg, x, y, sl, t, perx, pery, own, d);
-            if (!RESTRICT) {
-                const size_t idx = (size_t)y * nx + x;
-                T *go = a.gout + idx;
+        for (int j = 0; j < CPT; j++) {
+            const int x = xj[j], c = cj[j];
+            T d[8];
 #pragma unroll
-                for (int k = 2; k < (kind_ghosts(KIND) ? 8 : 5); k++) go[k * NP] = gcur[k] - gam * d[k];
-                // first moments: (hi + lo) - gamma d, renormalised into hi + lo with LO
-                if constexpr (LO) {
+            for (int k = 0; k < 8; k++) d[k] = T(0);
+            if (writes[j]) {
+                const OwnCell<T> own = own_cell<T, W, KIND, LO>(rg, sb, c);
+                const T(&gcur)[8] = own.g;
+                if (wall_col[j] || wall_row) residual_cell<T, TC, KIND, LO, W, true>(a, rg, x, y, sl, c, perx, pery, own, d);
+                else residual_cell<T, TC, KIND, LO, W, false>(a, rg, x, y, sl, c, perx, pery, own, d);
+                if (!RESTRICT) {
+                    const size_t idx = (size_t)y * nx + x;
+                    T *go = a.gout + idx;
 #pragma unroll
-                    for (int k = 0; k < 2; k++) {
-                        T hi, lw;
-                        two_sum(gcur[k], own.lo[k] - gam * d[k], hi, lw);
-                        go[k * NP] = hi;
-                        a.glo_out[k * NP + idx] = lw;
+                    for (int k = 2; k < (kind_ghosts(KIND) ? 8 : 5); k++) go[k * NP] = gcur[k] - gam * d[k];
+                    // first moments: (hi + lo) - gamma d, renormalised into hi + lo with LO
+                    if constexpr (LO) {
+#pragma unroll
+                        for (int k = 0; k < 2; k++) {
+                            T hi, lw;
+                            two_sum(gcur[k], own.lo[k] - gam * d[k], hi, lw);
+                            go[k * NP] = hi;
+                            a.glo_out[k * NP + idx] = lw;
+                        }
+                    } else {
+#pragma unroll
+                        for (int k = 0; k < 2; k++) go[k * NP] = gcur[k] - gam * d[k];
                     }
-                } else {
-#pragma unroll
-                    for (int k = 0; k < 2; k++) go[k * NP] = gcur[k] - gam * d[k];
-                }
-                if (a.resmax) {
-                    rmax = fmax(rmax, pop_absmax(d));
-                    gmax = fmax(gmax, pop_absmax(gcur));
-                    rsum += (double)pop_sumsq(d);
+                    if (a.resmax) {
+                        rmax = fmax(rmax, pop_absmax(d));
+                        gmax = fmax(gmax, pop_absmax(gcur));
+                        rsum += (double)pop_sumsq(d);
+                    }
                 }
             }
-        }
-        if (RESTRICT) {
-            // full-sum restriction of eq. MG:restriction: pair rows, then columns
-            // (columns x, x+1 with x even sit in lanes t, t+1 of one warp)
-            const bool odd = ((y - y0) & 1) != 0;
+            if (RESTRICT) {
+                // full-sum restriction of eq. MG:restriction: pair rows, then columns
+                // (columns x, x+1 with x even sit in lanes t, t+1 of one warp)
+                const bool odd = ((y - y0) & 1) != 0;
 #pragma unroll
-            for (int k = 0; k < 8; k++) acc[k] = odd ? acc[k] + d[k] : d[k];
-            if (odd) {
-                TC tot[8];
+                for (int k = 0; k < 8; k++) acc[j][k] = odd ? acc[j][k] + d[k] : d[k];
+                if (odd) {
+                    TC tot[8];
 #pragma unroll
-                for (int k = 0; k < 8; k++) {
-                    const TC mine = (TC)acc[k];
-                    tot[k] = mine + __shfl_down_sync(0xffffffffu, mine, 1);
-                }
-                if (writes && (x & 1) == 0) {
-                    const size_t NPc = NP >> 2;
-                    const size_t cidx = (size_t)(y >> 1) * (nx >> 1) + (x >> 1);
+                    for (int k = 0; k < 8; k++) {
+                        const TC mine = (TC)acc[j][k];
+                        tot[k] = mine + __shfl_down_sync(0xffffffffu, mine, 1);
+                    }
+                    if (writes[j] && (x & 1) == 0) {
+                        const size_t NPc = NP >> 2;
+                        const size_t cidx = (size_t)(y >> 1) * (nx >> 1) + (x >> 1);
 #pragma unroll
-                    for (int k = 0; k < (kind_ghosts(KIND) ? 8 : 5); k++) a.rc[k * NPc + cidx] = tot[k];
+                        for (int k = 0; k < (kind_ghosts(KIND) ? 8 : 5); k++) a.rc[k * NPc + cidx] = tot[k];
+                    }
                 }
             }
         }
@@ -713,7 +738,7 @@ __device__ __forceinline__ void sweep_strip(const SweepArgs<T, TC> &a, int bx, i
     }
 
     if (!RESTRICT && a.resmax) {
-        // warp-shuffle then block reduction of the two maxima, one atomic per CTA
+        // warp-shuffle then block reduction of the two maxima and the sum, one atomic each per CTA
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             rmax = fmax(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
@@ -741,12 +766,12 @@ __device__ __forceinline__ void sweep_strip(const SweepArgs<T, TC> &a, int bx, i
     }
 }
 
-template <typename T, typename TC, int NT, int KIND, bool LO, bool RESTRICT>
-__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 6 : 1) k_sweep_mom(const SweepArgs<T, TC> a, int TY)
+template <typename T, typename TC, int NT, int CPT, int KIND, bool LO, bool RESTRICT>
+__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 768 / (NT * CPT) : 1) k_sweep_mom(const SweepArgs<T, TC> a, int TY)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double red[3][NT / 32];
-    sweep_strip<T, TC, NT, KIND, LO, RESTRICT>(a, blockIdx.x, blockIdx.y, TY, smem_raw, red);
+    sweep_strip<T, TC, NT, CPT, KIND, LO, RESTRICT>(a, blockIdx.x, blockIdx.y, TY, smem_raw, red);
 }
 
 // ---------------------------------------------------------------------------
@@ -929,18 +954,19 @@ cudaError_t launch_tile(const SweepArgs<T, TC> &a, cudaStream_t s)
     return cudaGetLastError();
 }
 
-constexpr int SWEEP_NT = 128;
-static_assert(SWEEP_NT - 4 == SWEEP_STRIP_COLS, "strip geometry shared with the host planner");
+// Strip sweep launch shape: SWEEP_NT threads, SWEEP_CPT cells of a row per thread.
+constexpr int SWEEP_NT = 128, SWEEP_CPT = 1;
+static_assert(SWEEP_NT * SWEEP_CPT - 4 == SWEEP_STRIP_COLS, "strip geometry shared with the host planner");
 
 template <typename T, typename TC, int KIND, bool LO, bool RESTRICT>
 struct SweepKernel {
-    static constexpr size_t smem = rows_smem_bytes<T, KIND, LO, SWEEP_NT>();
+    static constexpr size_t smem = rows_smem_bytes<T, KIND, LO, SWEEP_NT * SWEEP_CPT>();
     // kernel attributes and resident CTAs per device (set up on first use)
     static int slots()
     {
         static int n = 0;
         if (!n) {
-            auto k1 = k_sweep_mom<T, TC, SWEEP_NT, KIND, LO, RESTRICT>;
+            auto k1 = k_sweep_mom<T, TC, SWEEP_NT, SWEEP_CPT, KIND, LO, RESTRICT>;
             if (cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
             int dev = 0, sms = 0, per_sm = 0;
             if (cudaGetDevice(&dev) != cudaSuccess) return 0;
@@ -960,8 +986,8 @@ cudaError_t launch_rows(const SweepArgs<T, TC> &a, cudaStream_t s)
     const int slots = SK::slots();
     if (!slots) return cudaGetLastError() != cudaSuccess ? cudaErrorUnknown : cudaErrorInvalidConfiguration;
     int ty = a.rows > 0 ? a.rows + (a.rows & 1) : sweep_strip_rows(a.nx, a.ny, slots);
-    dim3 grid((a.nx + SWEEP_NT - 5) / (SWEEP_NT - 4), (a.ny + ty - 1) / ty);
-    k_sweep_mom<T, TC, SWEEP_NT, KIND, LO, RESTRICT><<<grid, SWEEP_NT, SK::smem, s>>>(a, ty);
+    dim3 grid((a.nx + SWEEP_STRIP_COLS - 1) / SWEEP_STRIP_COLS, (a.ny + ty - 1) / ty);
+    k_sweep_mom<T, TC, SWEEP_NT, SWEEP_CPT, KIND, LO, RESTRICT><<<grid, SWEEP_NT, SK::smem, s>>>(a, ty);
     return cudaGetLastError();
 }
 
