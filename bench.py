@@ -118,7 +118,7 @@ def step_model(params, n, fp64):
     return cell_sweeps, nbytes
 
 
-OPT_COARSEST_STORAGE = 1  # biot_params.options flag of include/biot.h
+OPT_COARSEST_STORAGE, OPT_COLD_FP64, OPT_COLD_FP32 = 1, 2, 4  # biot_params.options flags of include/biot.h
 
 
 def coarsest_fp64(params):
@@ -132,9 +132,11 @@ def precision_label(params, fp64):
     if fp64:
         return "fp64 storage and arithmetic"
     cells = params["nx"] * params["ny"]
+    opt = int(params.get("options", 0))
+    cold64 = bool(opt & OPT_COLD_FP64) or (cells >= 2048 * 2048 and not opt & OPT_COLD_FP32)
     return ("fp32 moments and collisions; fp64 residual norms, coupling accumulators and "
             + ("coarsest level" if coarsest_fp64(params) else "no level (coarsest level fp32)")
-            + ("; fp64 solve at t = 0" if cells >= 2048 * 2048 else ""))
+            + ("; fp64 solve at t = 0" if cold64 else ""))
 
 
 def measured_fp64_peak(torch):
@@ -366,6 +368,8 @@ def run_ours(args):
     params, sides, _ = W.terzaghi_4097(n=args.n, precision=W.FP64 if fp64 else W.FP32)
     if args.coarsest == "fp32":
         params = dict(params, options=int(params.get("options", 0)) | OPT_COARSEST_STORAGE)
+    if args.cold != "auto":
+        params = dict(params, options=int(params.get("options", 0)) | (OPT_COLD_FP64 if args.cold == "fp64" else OPT_COLD_FP32))
     nx, ny = params["nx"], params["ny"]
     cells = nx * ny
     stream = torch.cuda.current_stream()
@@ -736,6 +740,8 @@ def main():
     ap.add_argument("--instances", type=int, default=64, help="batched: number of instances")
     ap.add_argument("--coarsest", choices=["fp64", "fp32"], default="fp64",
                     help="single, FP32 path: precision of the coarsest multigrid level")
+    ap.add_argument("--cold", choices=["auto", "fp64", "fp32"], default="auto",
+                    help="single, FP32 path: the solve at t = 0 on an FP64 copy (auto: from 2048^2 cells)")
     ap.add_argument("--requests", type=int, default=200, help="served: number of requests")
     ap.add_argument("--mean-service", type=float, default=0.05, help="served: assumed mean service time (s)")
     ap.add_argument("--budget-gb", type=float, default=16.0, help="served: device-memory budget")
