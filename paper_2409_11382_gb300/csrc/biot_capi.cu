@@ -2498,7 +2498,7 @@ extern "C" int biot_autotune(biot_handle h, int *rows_out, double *ms_out, int m
         release(c);
         return fail(BIOT_ERR_CUDA, "cudaEventCreate failed");
     }
-    static const int cand[] = {4, 8, 16, 24, 32, 48, 64, 96};
+    static const int fixed_cand[] = {4, 8, 16, 24, 32, 48, 64, 96};
     int status = BIOT_OK;
     for (int l = 0; l < h->L && !status; l++) {
         Level &Lv = h->lv[l];
@@ -2508,7 +2508,21 @@ extern "C" int biot_autotune(biot_handle h, int *rows_out, double *ms_out, int m
             double best_ms = 1e30;
             // tile-sized levels are not launched as strips: nothing to choose
             const bool strips = (long)Lv.nx * Lv.ny > (long)256 * 256;
-            for (int k = 0; strips && k < (int)(sizeof(cand) / sizeof(cand[0])) && !status; k++) {
+            // candidates: fixed heights, and the heights whose strips fill exactly
+            // 1, 2 or 3 waves of resident CTAs (tall strips repeat fewer halo rows)
+            std::vector<int> cand(std::begin(fixed_cand), std::end(fixed_cand));
+            const int slots = strips ? tkind_slots(level_tkind(h, l), level_variant(h, l, mode) & ~SWEEP_V_TILE) : 0;
+            const int sx = (Lv.nx + SWEEP_STRIP_COLS - 1) / SWEEP_STRIP_COLS;
+            for (int w = 1; w <= 3 && slots > 0; w++) {
+                const int nsy = w * slots / sx;
+                if (nsy < 1) continue;
+                int ty = (Lv.ny + nsy - 1) / nsy;
+                ty += ty & 1;
+                if ((Lv.ny + ty - 1) / ty * sx <= w * slots) cand.push_back(ty);
+            }
+            std::sort(cand.begin(), cand.end());
+            cand.erase(std::unique(cand.begin(), cand.end()), cand.end());
+            for (size_t k = 0; strips && k < cand.size() && !status; k++) {
                 if (cand[k] > Lv.ny) break;
                 c->lv[l].rows[mode] = cand[k];
                 for (int w = 0; w < 2 && !status; w++) status = sweep(c, l, mode, false, false, false);
@@ -2525,6 +2539,7 @@ extern "C" int biot_autotune(biot_handle h, int *rows_out, double *ms_out, int m
                     best_ms = ms / reps;
                     best = cand[k];
                 }
+                c->lv[l].rows[mode] = 0;
             }
             Lv.rows[mode] = best;
             if (rows_out && l < max_levels) rows_out[2 * l + mode] = best;

@@ -34,7 +34,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 896 / (NT * CPT) : 1)
     __shared__ double red[3][NT / 32];
     const int j = batch_job(P, blockIdx.x);
     const int local = blockIdx.x - P.start[j], sx = P.sx[j];
-    sweep_strip<T, TC, NT, CPT, KIND, LO, RESTRICT>(P.job[j], local % sx, local / sx, P.ty[j], smem_raw, red);
+    sweep_strip_any<T, TC, NT, CPT, KIND, LO, RESTRICT, FETCH_DYN>(P.job[j], local % sx, local / sx, P.ty[j], smem_raw, red);
 }
 
 // Batched form: CTA b processes work item b, a tile of the sweep of its job.

@@ -177,22 +177,32 @@ __device__ __forceinline__ void two_sum(T a, T b, T &s, T &e)
     e = (a - (s - bb)) + (b - bb);
 }
 
+// How a sweep's loads form the iterate: from the arguments at run time
+// (a.zero_init, a.gc), or fixed at compile time -- the stored iterate, the
+// stored iterate plus the prolongated coarse correction, or zero.
+enum { FETCH_DYN = 0, FETCH_PLAIN = 1, FETCH_PROL = 2, FETCH_ZERO = 3 };
+
 // Raw values of cell (gx, gy): moments of the iterate (+ prolongated coarse
 // correction; with LO its first moments go to the low parts), F~ (FINE) or r
 // (COARSE), low parts (LO).  Ghost cells of a non-periodic wall read the
 // adjacent cell: only their m_s is used (even extension of the divergence).
-template <typename T, typename TC, int KIND, bool LO, int RV>
+// INB: the caller guarantees 0 <= gx < nx and 0 <= gy < ny.
+template <typename T, typename TC, int KIND, bool LO, int RV, int FM = FETCH_DYN, bool INB = false>
 __device__ __forceinline__ void fetch_cell(const SweepArgs<T, TC> &a, int gx, int gy, size_t NP, bool perx, bool pery,
                                            T (&v)[RV])
 {
     using L = RingLayout<KIND, LO>;
-    if (perx) gx = wrapi(gx, a.nx);
-    if (pery) gy = wrapi(gy, a.ny);
-    gx = clampi(gx, a.nx);
-    gy = clampi(gy, a.ny);
+    if constexpr (!INB) {
+        if (perx) gx = wrapi(gx, a.nx);
+        if (pery) gy = wrapi(gy, a.ny);
+        gx = clampi(gx, a.nx);
+        gy = clampi(gy, a.ny);
+    }
     const size_t idx = (size_t)gy * a.nx + gx;
     constexpr int NM = kind_ghosts(KIND) ? 8 : 5;  // moment planes loaded
-    if (a.zero_init) {
+    const bool zero = FM == FETCH_ZERO || (FM == FETCH_DYN && a.zero_init);
+    const bool prol = FM == FETCH_PROL || (FM == FETCH_DYN && a.gc != nullptr);
+    if (zero) {
 #pragma unroll
         for (int k = 0; k < 8; k++) v[k] = T(0);
     } else {
@@ -211,10 +221,10 @@ __device__ __forceinline__ void fetch_cell(const SweepArgs<T, TC> &a, int gx, in
         for (int k = 0; k < 5; k++) v[L::XV + k] = r[k * NP];
     }
     if constexpr (LO) {
-        v[L::LOV] = a.zero_init ? T(0) : a.glo[idx];
-        v[L::LOV + 1] = a.zero_init ? T(0) : a.glo[NP + idx];
+        v[L::LOV] = zero ? T(0) : a.glo[idx];
+        v[L::LOV + 1] = zero ? T(0) : a.glo[NP + idx];
     }
-    if (a.gc) {
+    if (prol) {
         const size_t NPc = NP >> 2;
         const size_t cidx = (size_t)(gy >> 1) * (a.nx >> 1) + (gx >> 1);
         if constexpr (LO) {
@@ -586,7 +596,10 @@ __device__ __forceinline__ void residual_cell(const SweepArgs<T, TC> &a, const R
 // columns t, t + NT, ..., so every plane access of a warp stays on consecutive
 // words, and the per-row work that does not depend on the column -- ring slots,
 // loop control, barriers, row predicates -- is shared by the thread's CPT cells.
-template <typename T, typename TC, int NT, int CPT, int KIND, bool LO, bool RESTRICT>
+// INT: the CTA's whole window -- columns x0-2 .. x0+W-3, rows y0-2 .. y1+2 --
+// lies inside the grid (sweep_strip_interior), so no cell of it is a wall cell
+// or reads a ghost or wrapped source: no clamping, no wall rules, no row tests.
+template <typename T, typename TC, int NT, int CPT, int KIND, bool LO, bool RESTRICT, int FM, bool INT>
 __device__ __forceinline__ void sweep_strip(const SweepArgs<T, TC> &a, int bx, int by, int TY, unsigned char *smem_raw,
                                             double (&red)[3][NT / 32])
 {
@@ -611,19 +624,26 @@ __device__ __forceinline__ void sweep_strip(const SweepArgs<T, TC> &a, int bx, i
     for (int j = 0; j < CPT; j++) {
         cj[j] = t + j * NT;
         xj[j] = x0 - 2 + cj[j];
-        loads[j] = perx || xj[j] < nx + 2;  // a real, wrapped or ghost column
-        collides[j] = cj[j] >= 1 && cj[j] < W - 1 && (perx || (xj[j] >= 0 && xj[j] < nx));
-        writes[j] = cj[j] >= 2 && cj[j] < W - 2 && xj[j] < nx;
-        wall_col[j] = !perx && (xj[j] == 0 || xj[j] == nx - 1);
+        if constexpr (INT) {
+            loads[j] = true;
+            collides[j] = cj[j] >= 1 && cj[j] < W - 1;
+            writes[j] = cj[j] >= 2 && cj[j] < W - 2;
+            wall_col[j] = false;
+        } else {
+            loads[j] = perx || xj[j] < nx + 2;  // a real, wrapped or ghost column
+            collides[j] = cj[j] >= 1 && cj[j] < W - 1 && (perx || (xj[j] >= 0 && xj[j] < nx));
+            writes[j] = cj[j] >= 2 && cj[j] < W - 2 && xj[j] < nx;
+            wall_col[j] = !perx && (xj[j] == 0 || xj[j] == nx - 1);
+        }
     }
 
-    auto row_ok = [&](int y) { return pery || (y >= 0 && y < ny); };
+    auto row_ok = [&](int y) { return INT || pery || (y >= 0 && y < ny); };
 
     T pv[CPT][RV];
     auto fetch_row = [&](int y) {
 #pragma unroll
         for (int j = 0; j < CPT; j++)
-            if (loads[j]) fetch_cell<T, TC, KIND, LO, RV>(a, xj[j], y, NP, perx, pery, pv[j]);
+            if (loads[j]) fetch_cell<T, TC, KIND, LO, RV, FM, INT>(a, xj[j], y, NP, perx, pery, pv[j]);
     };
     auto store_row = [&](int s) {
 #pragma unroll
@@ -672,7 +692,7 @@ __device__ __forceinline__ void sweep_strip(const SweepArgs<T, TC> &a, int bx, i
         collide_row(y + 1, sb, sc, sa);
         __syncthreads();   // (E)
         const int sl[3] = {sa, sb, sc};
-        const bool wall_row = !pery && (y == 0 || y == ny - 1);
+        const bool wall_row = !INT && !pery && (y == 0 || y == ny - 1);
 #pragma unroll
         for (int j = 0; j < CPT; j++) {
             const int x = xj[j], c = cj[j];
@@ -682,7 +702,7 @@ __device__ __forceinline__ void sweep_strip(const SweepArgs<T, TC> &a, int bx, i
             if (writes[j]) {
                 const OwnCell<T> own = own_cell<T, W, KIND, LO>(rg, sb, c);
                 const T(&gcur)[8] = own.g;
-                if (wall_col[j] || wall_row) residual_cell<T, TC, KIND, LO, W, true>(a, rg, x, y, sl, c, perx, pery, own, d);
+                if (!INT && (wall_col[j] || wall_row)) residual_cell<T, TC, KIND, LO, W, true>(a, rg, x, y, sl, c, perx, pery, own, d);
                 else residual_cell<T, TC, KIND, LO, W, false>(a, rg, x, y, sl, c, perx, pery, own, d);
                 if (!RESTRICT) {
                     const size_t idx = (size_t)y * nx + x;
@@ -766,12 +786,31 @@ __device__ __forceinline__ void sweep_strip(const SweepArgs<T, TC> &a, int bx, i
     }
 }
 
-template <typename T, typename TC, int NT, int CPT, int KIND, bool LO, bool RESTRICT>
+// Whether strip (bx, by) of TY rows lies inside the grid with its whole window
+// (the INT form of sweep_strip applies).
+template <int W>
+__device__ __forceinline__ bool sweep_strip_interior(int nx, int ny, int bx, int by, int TY)
+{
+    const int x0 = bx * (W - 4), y0 = by * TY, y1 = min(y0 + TY, ny);
+    return x0 >= 2 && x0 + W - 3 <= nx - 1 && y0 >= 2 && y1 + 2 <= ny - 1;
+}
+
+template <typename T, typename TC, int NT, int CPT, int KIND, bool LO, bool RESTRICT, int FM>
+__device__ __forceinline__ void sweep_strip_any(const SweepArgs<T, TC> &a, int bx, int by, int TY, unsigned char *smem_raw,
+                                                double (&red)[3][NT / 32])
+{
+    if (sweep_strip_interior<NT * CPT>(a.nx, a.ny, bx, by, TY))
+        sweep_strip<T, TC, NT, CPT, KIND, LO, RESTRICT, FM, true>(a, bx, by, TY, smem_raw, red);
+    else
+        sweep_strip<T, TC, NT, CPT, KIND, LO, RESTRICT, FM, false>(a, bx, by, TY, smem_raw, red);
+}
+
+template <typename T, typename TC, int NT, int CPT, int KIND, bool LO, bool RESTRICT, int FM>
 __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 768 / (NT * CPT) : 1) k_sweep_mom(const SweepArgs<T, TC> a, int TY)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double red[3][NT / 32];
-    sweep_strip<T, TC, NT, CPT, KIND, LO, RESTRICT>(a, blockIdx.x, blockIdx.y, TY, smem_raw, red);
+    sweep_strip_any<T, TC, NT, CPT, KIND, LO, RESTRICT, FM>(a, blockIdx.x, blockIdx.y, TY, smem_raw, red);
 }
 
 // ---------------------------------------------------------------------------
@@ -961,17 +1000,21 @@ static_assert(SWEEP_NT * SWEEP_CPT - 4 == SWEEP_STRIP_COLS, "strip geometry shar
 template <typename T, typename TC, int KIND, bool LO, bool RESTRICT>
 struct SweepKernel {
     static constexpr size_t smem = rows_smem_bytes<T, KIND, LO, SWEEP_NT * SWEEP_CPT>();
-    // kernel attributes and resident CTAs per device (set up on first use)
+    template <int FM>
+    static constexpr auto kernel() { return k_sweep_mom<T, TC, SWEEP_NT, SWEEP_CPT, KIND, LO, RESTRICT, FM>; }
+    // kernel attributes and resident CTAs per device (set up on first use); the
+    // fetch forms share one shape, and the plain form's occupancy stands for all
     static int slots()
     {
         static int n = 0;
         if (!n) {
-            auto k1 = k_sweep_mom<T, TC, SWEEP_NT, SWEEP_CPT, KIND, LO, RESTRICT>;
-            if (cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
+            for (auto k : {kernel<FETCH_PLAIN>(), kernel<FETCH_PROL>(), kernel<FETCH_ZERO>()})
+                if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
             int dev = 0, sms = 0, per_sm = 0;
             if (cudaGetDevice(&dev) != cudaSuccess) return 0;
             if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
-            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k1, SWEEP_NT, smem) != cudaSuccess) return 0;
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel<FETCH_PLAIN>(), SWEEP_NT, smem) != cudaSuccess)
+                return 0;
             n = sms * (per_sm > 0 ? per_sm : 1);
         }
         return n;
@@ -987,7 +1030,13 @@ cudaError_t launch_rows(const SweepArgs<T, TC> &a, cudaStream_t s)
     if (!slots) return cudaGetLastError() != cudaSuccess ? cudaErrorUnknown : cudaErrorInvalidConfiguration;
     int ty = a.rows > 0 ? a.rows + (a.rows & 1) : sweep_strip_rows(a.nx, a.ny, slots);
     dim3 grid((a.nx + SWEEP_STRIP_COLS - 1) / SWEEP_STRIP_COLS, (a.ny + ty - 1) / ty);
-    k_sweep_mom<T, TC, SWEEP_NT, SWEEP_CPT, KIND, LO, RESTRICT><<<grid, SWEEP_NT, SK::smem, s>>>(a, ty);
+    // the fetch form is fixed per launch (a restriction sweep never starts from
+    // zero or takes a correction)
+    auto k = a.zero_init && !RESTRICT ? SK::template kernel<FETCH_ZERO>()
+           : a.gc && !RESTRICT         ? SK::template kernel<FETCH_PROL>()
+                                       : SK::template kernel<FETCH_PLAIN>();
+    if (RESTRICT && (a.zero_init || a.gc)) return cudaErrorInvalidValue;
+    k<<<grid, SWEEP_NT, SK::smem, s>>>(a, ty);
     return cudaGetLastError();
 }
 
