@@ -76,7 +76,10 @@ def profiled_traffic_per_cell(path=PROFILE):
     return profiled_per_cell("traffic_bytes_per_cell", path)
 
 
-def step_model(params, n, fp64):
+DEV_PRECISIONS = {"fp32dev16": 3, "fp32devbf16": 4}  # BIOT_FP32_DEV16, BIOT_FP32_DEVBF16 of include/biot.h
+
+
+def step_model(params, n, fp64, dev=False):
     """Sweeps and algorithmic bytes of one physical step with fixed V-cycle counts
     (N_E V-cycles of 2K smoothing sweeps and one residual + restriction sweep per
     level, 2K sweeps on the coarsest level, then the fused flow step).  Per cell
@@ -91,6 +94,9 @@ def step_model(params, n, fp64):
         the option BIOT_OPT_COARSEST_STORAGE);
       flow step: 9 f in and out, m_s, D(t - dt) (FP64) and the previous history
         difference in, D(t) (FP64), the new difference and F~ out.
+    With the 16-bit deviation store (dev) the finest level's m_11, m_s, m_d move
+    as 2-byte values; the last finest sweep of a solve also writes them in FP32
+    (3 planes, once per solve).
     Returns (cell-sweeps per step, bytes per step)."""
     L, K, ne = params["levels"], params["K"], params["ne_fixed"]
     esz = 8 if fp64 else 4
@@ -106,12 +112,15 @@ def step_model(params, n, fp64):
         nlo = 2 if (fine and not fp64) else 0
         xin = 2 if fine else 5  # F~ or r
         prol = 5 * ec / 4.0 / (2 * K) if l > 0 else 0.0  # correction from level l - 1
-        smooth = ((5 + nlo) * 2 + xin) * e + prol
+        nst = 3 if (fine and dev) else 0  # moments in the 2-byte store
+        smooth = ((5 - nst + nlo) * 2 + xin) * e + nst * 2 * 2 + prol
         cell_sweeps += ne * 2 * K * c
         nbytes += ne * 2 * K * c * smooth
+        if fine and dev:
+            nbytes += c * 3 * e  # the FP32 copy of the last sweep of the solve
         if l > 0:
             cell_sweeps += ne * c
-            nbytes += ne * c * ((5 + nlo + xin) * e + 5 * ec / 4.0)
+            nbytes += ne * c * ((5 - nst + nlo + xin) * e + nst * 2 + 5 * ec / 4.0)
     fine_cells = float(n * n)
     fe = 8 if fp64 else 4
     nbytes += fine_cells * (9 * fe * 2 + fe + 8 + fe + 8 + fe + 2 * fe)
@@ -131,12 +140,14 @@ def precision_label(params, fp64):
     """What the run computes in, from the parameters the library was given."""
     if fp64:
         return "fp64 storage and arithmetic"
+    prec = int(params.get("precision", 1))
+    store = {3: "; finest m_11, m_s, m_d stored as fp16 deviation", 4: "; finest m_11, m_s, m_d stored as bf16 deviation"}.get(prec, "")
     cells = params["nx"] * params["ny"]
     opt = int(params.get("options", 0))
     cold64 = bool(opt & OPT_COLD_FP64) or (cells >= 2048 * 2048 and not opt & OPT_COLD_FP32)
     return ("fp32 moments and collisions; fp64 residual norms, coupling accumulators and "
             + ("coarsest level" if coarsest_fp64(params) else "no level (coarsest level fp32)")
-            + ("; fp64 solve at t = 0" if cold64 else ""))
+            + ("; fp64 solve at t = 0" if cold64 else "") + store)
 
 
 def measured_fp64_peak(torch):
@@ -365,7 +376,8 @@ def run_ours(args):
     if world > 1:
         torch.distributed.barrier()
     fp64 = args.precision == "fp64"
-    params, sides, _ = W.terzaghi_4097(n=args.n, precision=W.FP64 if fp64 else W.FP32)
+    dev = args.precision in DEV_PRECISIONS
+    params, sides, _ = W.terzaghi_4097(n=args.n, precision=W.FP64 if fp64 else DEV_PRECISIONS.get(args.precision, W.FP32))
     if args.coarsest == "fp32":
         params = dict(params, options=int(params.get("options", 0)) | OPT_COARSEST_STORAGE)
     if args.cold != "auto":
@@ -454,8 +466,7 @@ def run_ours(args):
         if not args.no_cpu_baseline:
             cpu_base = cpu_baseline_entry(fields)
         if fields or os.path.exists(GOLDEN_STRIP):
-            accuracy = accuracy_vs_oracle(fields, args.n, {"options": params.get("options", 0)},
-                                          W.FP64 if fp64 else W.FP32)
+            accuracy = accuracy_vs_oracle(fields, args.n, {"options": params.get("options", 0)}, params["precision"])
     # finest-level smoothing sweep, fixed V-cycle count: the 5 moments that carry
     # state (the ghost moments 12, 21, 22 are elided) in and out, F~ in, with FP32
     # storage also the 2 low parts of the first moments in and out; the
@@ -463,7 +474,8 @@ def run_ours(args):
     nm = 5 if params["ne_fixed"] > 0 else 8
     esz = 8.0 if fp64 else 4.0
     nlo = 0 if fp64 else 2
-    bytes_per_cell = ((nm + nlo) * 2 + 2) * esz + nm * esz / 4.0 / (2 * params["K"])
+    nst = 3 if dev else 0  # m_11, m_s, m_d as 2-byte values
+    bytes_per_cell = ((nm - nst + nlo) * 2 + 2) * esz + nst * 2 * 2 + nm * esz / 4.0 / (2 * params["K"])
     avg_sweep_ms = sweep_ms / max(sweep_n, 1)
     achieved = bytes_per_cell * cells / (avg_sweep_ms / 1e3) / 1e9
     traffic_pc = profiled_traffic_per_cell(PROFILE64 if fp64 else PROFILE)
@@ -490,6 +502,7 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64" if fp64 else "f32", "data": "synthetic",
+        "storage": args.precision,
         "config": {"workload": f"terzaghi_{args.n + 1}x{args.n + 1}_{args.precision}",
                    "cells": f"{nx}x{ny}", "levels": params["levels"],
                    "ne_fixed": params["ne_fixed"], "K": params["K"], "gamma": params["gamma"],
@@ -510,7 +523,7 @@ def run_ours(args):
     if roofline_other is not None:
         line["roofline_hbm"] = roofline_other
     if params["ne_fixed"] > 0:
-        sweeps, nb = step_model(params, args.n, fp64)
+        sweeps, nb = step_model(params, args.n, fp64, dev)
         t_step = ms / args.steps / 1e3
         line["step"] = {"mlups_sweep": world * sweeps / t_step / 1e6,
                         "algorithmic_bytes_per_step": nb, "achieved_gbs": nb / t_step / 1e9,
@@ -559,6 +572,8 @@ def run_batched(args):
     _barrier(world)
     # weak scaling: every rank advances its own 64 seeded instances
     probs = W.batched_instances(count=args.instances, seed=2409 + 7919 * rank)
+    if args.precision in DEV_PRECISIONS:
+        probs = [(dict(p, precision=DEV_PRECISIONS[args.precision]), s) for p, s in probs]
     cells = sum(p["nx"] * p["ny"] for p, _ in probs)
     b = biot.Batch(probs)
     b.step(args.warmup)
@@ -620,9 +635,20 @@ def run_batched(args):
     b.close()
     accuracy = oracle_errors([(probs[i], got[i]) for i in small], total_steps) if rank == 0 else None
     value = world * cells * args.steps / secs / 1e6
+    # step-level roofline: the algorithmic bytes of every instance's step (the
+    # per-sweep model of step_model) over the measured time per step
+    dev = args.precision in DEV_PRECISIONS
+    step_bytes = sum(step_model(p, p["nx"], False, dev)[1] for p, _ in probs)
+    peak, peak_kind = measured_peaks()
+    achieved = world * step_bytes / (secs / args.steps) / 1e9
+    roofline = {"kernel": "whole batched step (every phase launch and the flow steps)", "bound": "hbm",
+                "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "peak_kind": f"{peak_kind} copy bandwidth (burst)", "bytes_per_step": step_bytes, "traffic": None}
     line = {"metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
+            "roofline": roofline,
             "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "storage": args.precision if args.precision in DEV_PRECISIONS else "fp32",
             "config": {"workload": "batched_64_instances_64-512_fp32", "instances": len(probs),
                        "cells_total": cells, "ne_fixed": 3, "K": 4,
                        "l2": "state of all instances larger than L2; no flush needed",
@@ -735,8 +761,9 @@ def main():
     ap.add_argument("--no-tune", action="store_true", help="skip biot_autotune (default launch shapes)")
     ap.add_argument("--n", type=int, default=4096, help="cells per side (4096 = the benchmark workload)")
     ap.add_argument("--workload", choices=["single", "batched", "served"], default="single")
-    ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32",
-                    help="single: the FP32 path (default) or the plain FP64 path")
+    ap.add_argument("--precision", choices=["fp32", "fp64"] + sorted(DEV_PRECISIONS), default="fp32",
+                    help="single: the FP32 path (default), the plain FP64 path, or the FP32 path with the "
+                         "16-bit deviation store; batched: fp32 or a deviation store")
     ap.add_argument("--instances", type=int, default=64, help="batched: number of instances")
     ap.add_argument("--coarsest", choices=["fp64", "fp32"], default="fp64",
                     help="single, FP32 path: precision of the coarsest multigrid level")

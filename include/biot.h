@@ -67,6 +67,13 @@ extern "C" {
 #define BIOT_FP32_COARSE64 2  /* BIOT_FP32 on the finest level (elastic state and flow
                                  populations), FP64 on every coarser multigrid level:
                                  the coarse-grid corrections are not rounded to FP32 */
+#define BIOT_FP32_DEV16   3  /* BIOT_FP32, with the finest level's m_11, m_s, m_d -- the
+                                 elastic state's deviation from its equilibrium (Tab. moments:
+                                 their equilibria are zero) -- stored as IEEE FP16 values times a
+                                 power of two fixed at creation from the boundary data, and
+                                 collided in FP32.  Needs ne_fixed > 0 (the ghost moments 12, 21,
+                                 22 are not stored) */
+#define BIOT_FP32_DEVBF16 4  /* the same with bfloat16 storage */
 /* In every precision the elastic state is stored as the MRT moments of the
  * populations (an exact change of basis, eqs. moments / moments:stress). */
 
@@ -124,7 +131,7 @@ typedef struct biot_params {
                           max|g - ELASTIC_STEP(g)| <= tol * max(1, max|g|) (ne_fixed <= 0) */
     int    ne_max;     /* cap on V-cycles per step in tolerance mode */
     int    ne_fixed;   /* > 0: exactly this many V-cycles per step, MG(ne_fixed, K) */
-    int    precision;  /* BIOT_FP64, BIOT_FP32 or BIOT_FP32_COARSE64 */
+    int    precision;  /* BIOT_FP64, BIOT_FP32, BIOT_FP32_COARSE64, BIOT_FP32_DEV16 or BIOT_FP32_DEVBF16 */
     int    options;    /* BIOT_OPT_* flags (0: defaults) */
 } biot_params;
 

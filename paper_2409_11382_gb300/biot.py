@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(_HERE, "libbiot_gb300.so")
 
 OK, ERR_INVALID_ARG, ERR_OOM, ERR_DIVERGED, ERR_NOT_CONVERGED, ERR_CUDA, ERR_TIMEOUT, ERR_NO_DEVICE = (
     0, -1, -2, -3, -4, -5, -6, -7)
-FP64, FP32, FP32_COARSE64 = 0, 1, 2
+FP64, FP32, FP32_COARSE64, FP32_DEV16, FP32_DEVBF16 = 0, 1, 2, 3, 4
 # biot_params.options (include/biot.h)
 OPT_COARSEST_STORAGE, OPT_COLD_FP64, OPT_COLD_FP32, OPT_COARSE_LO_ALL, OPT_COARSE_LO_OFF = 1, 2, 4, 8, 16
 PERIODIC, SYMMETRY, DIRICHLET, NEUMANN = 0, 1, 2, 3

@@ -56,6 +56,16 @@ struct SweepArgs {
     T k_hd;   // (1 - om_d) / 4
     T k_h22;  // -1 / (4 (12 lm + 4))
     T k_gam;  // gamma
+    // 16-bit deviation store of the finest FP32 level (BIOT_FP32_DEV16 / _DEVBF16):
+    // the moments m_11, m_s, m_d -- the state's deviation from the equilibrium
+    // values of Tab. moments, which are zero for them -- held as 16-bit values
+    // times the power of two dsc; everything else as in FP32
+    int dev;           // 0: none, 1: FP16, 2: BF16
+    const void *gd;    // 3 planes (m_11, m_s, m_d) of the iterate, or nullptr
+    void *gd_out;      // 3 planes of the smoothed iterate (SMOOTH), or nullptr
+    float dsc, dinv;   // scale of the stored values and its inverse
+    int dev_full;      // 1: also store m_11, m_s, m_d in FP32 (planes 2-4 of gout), for
+                       // the flow step and the read-outs: the last sweep of a solve
 };
 
 // One CTA's work item of a batched sweep launch: strip (bx, by) of TY rows of
@@ -65,7 +75,8 @@ struct SweepItem {
 };
 
 // Storage kind of a sweep launch (bit flags).
-enum { SWEEP_V_COARSE = 1, SWEEP_V_LO = 2, SWEEP_V_RESTRICT = 4, SWEEP_V_NOGHOST = 8, SWEEP_V_TILE = 16 };
+enum { SWEEP_V_COARSE = 1, SWEEP_V_LO = 2, SWEEP_V_RESTRICT = 4, SWEEP_V_NOGHOST = 8, SWEEP_V_TILE = 16,
+       SWEEP_V_DEV16 = 32, SWEEP_V_DEVBF16 = 64 };
 // Tile sweeps: levels of at most SWEEP_TILE_CELLS cells (single instance); tile
 // shape per storage type.  The fused flow step works on FLOW_TILE_X x FLOW_TILE_Y tiles.
 constexpr long SWEEP_TILE_CELLS = 256L * 256L;
@@ -238,5 +249,17 @@ struct NarrowArgs {
 };
 cudaError_t launch_narrow_state(const NarrowArgs &a, cudaStream_t s);
 template <typename T> cudaError_t launch_init(const InitArgs<T> &a, cudaStream_t s);
+
+// The 16-bit deviation store written from the FP32 moment planes 2-4 (m_11,
+// m_s, m_d): after the initial state, the FP64 cold start's hand-over and a
+// checkpoint load.  dev: 1 FP16, 2 BF16.
+struct DevEncodeArgs {
+    size_t np;
+    const float *g;  // planes 2-4 of an FP32 moment buffer (8 planes of np)
+    void *gd;        // 3 planes of 16-bit values
+    float dsc;
+    int dev;
+};
+cudaError_t launch_dev_encode(const DevEncodeArgs &a, cudaStream_t s);
 
 }  // namespace biot

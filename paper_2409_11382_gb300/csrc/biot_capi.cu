@@ -104,6 +104,7 @@ struct Level {
     int rows[2] = {0, 0};  // strip height per sweep mode chosen by biot_autotune (0: default)
     void *g[2] = {nullptr, nullptr};
     void *glo[2] = {nullptr, nullptr};  // low parts of m_10, m_01 (finest FP32 level)
+    void *gd[2] = {nullptr, nullptr};   // 16-bit deviation store: m_11, m_s, m_d (finest level, dev > 0)
     int cur = 0;
     void *r = nullptr;
     void *H[4] = {nullptr, nullptr, nullptr, nullptr};
@@ -126,6 +127,8 @@ struct biot_ctx {
     double h = 0, lam = 0, mu = 0, kap = 0, omega = 0, om_s = 0, om_d = 0, lm = 0;
     int L = 0;
     bool fp32 = false;  // FP32 state (finest and middle levels)
+    int dev = 0;        // finest level's deviation store: 0 none, 1 FP16, 2 BF16
+    float dsc = 1.f, dinv = 1.f;  // its scale (a power of two) and inverse
     Level lv[MAX_LEVELS];
     void *f[2]{};
     int fcur = 0;
@@ -243,8 +246,11 @@ int check_params(const biot_params *p, const biot_side *s)
     if (p->K < 1) return fail(BIOT_ERR_INVALID_ARG, "K must be >= 1");
     if (!(p->gamma > 0 && p->gamma <= 1)) return fail(BIOT_ERR_INVALID_ARG, "gamma must lie in (0, 1]");
     if (p->ne_fixed <= 0 && (p->ne_max < 1 || !(p->tol > 0))) return fail(BIOT_ERR_INVALID_ARG, "tolerance mode needs tol > 0 and ne_max >= 1");
-    if (p->precision != BIOT_FP64 && p->precision != BIOT_FP32 && p->precision != BIOT_FP32_COARSE64)
+    if (p->precision != BIOT_FP64 && p->precision != BIOT_FP32 && p->precision != BIOT_FP32_COARSE64 &&
+        p->precision != BIOT_FP32_DEV16 && p->precision != BIOT_FP32_DEVBF16)
         return fail(BIOT_ERR_INVALID_ARG, "unknown precision");
+    if ((p->precision == BIOT_FP32_DEV16 || p->precision == BIOT_FP32_DEVBF16) && p->ne_fixed <= 0)
+        return fail(BIOT_ERR_INVALID_ARG, "the 16-bit deviation store needs a fixed number of V-cycles (ne_fixed > 0)");
     constexpr int known = BIOT_OPT_COARSEST_STORAGE | BIOT_OPT_COLD_FP64 | BIOT_OPT_COLD_FP32 |
                           BIOT_OPT_COARSE_LO_ALL | BIOT_OPT_COARSE_LO_OFF;
     if (p->options & ~known) return fail(BIOT_ERR_INVALID_ARG, "unknown option flag");
@@ -407,12 +413,20 @@ int sweep_typed(biot_ctx *h, int l, int mode, bool zero_init, bool prolong, bool
         a.k_h22 = T(0.25 * k22);
     }
     a.k_gam = T(a.gamma);
+    if (fine && h->dev) {
+        a.dev = h->dev;
+        a.gd = Lv.gd[Lv.cur];
+        a.gd_out = mode == SWEEP_SMOOTH ? Lv.gd[1 - Lv.cur] : nullptr;
+        a.dsc = h->dsc;
+        a.dinv = h->dinv;
+        a.dev_full = (mode == SWEEP_SMOOTH && want_res) ? 1 : 0;  // the last sweep of the solve
+    }
 
     if (h->rec) {
         SweepJob j{};
         j.tkind = sizeof(T) == 8 ? 0 : (sizeof(TC) == 8 ? 1 : 2);
         j.variant = (fine ? 0 : SWEEP_V_COARSE) | (a.glo ? SWEEP_V_LO : 0) | (mode == SWEEP_RESTRICT ? SWEEP_V_RESTRICT : 0) |
-                    (a.ghosts ? 0 : SWEEP_V_NOGHOST);
+                    (a.ghosts ? 0 : SWEEP_V_NOGHOST) | (a.dev == 1 ? SWEEP_V_DEV16 : a.dev == 2 ? SWEEP_V_DEVBF16 : 0);
         j.level = l;
         job_args<T, TC>(j) = a;
         h->rec->push_back(j);
@@ -554,6 +568,7 @@ int elastic_solve_device_loop(biot_ctx *h);
 int elastic_solve(biot_ctx *h);
 int ensure_initialized(biot_ctx *h);
 int finish_pending(biot_ctx *h);
+int dev_encode(biot_ctx *h);
 void release(biot_ctx *h);
 size_t estimate_bytes(const biot_params *p, const biot_side *sides);
 
@@ -625,7 +640,8 @@ int cold_start_fp64(biot_ctx *h)
         a.ft32 = static_cast<float *>(h->Ft);
         if (!a.glo32) rc = fail(BIOT_ERR_CUDA, "FP32 instance without double-float first moments");
         else if (launch_narrow_state(a, h->stream) != cudaSuccess) rc = fail(BIOT_ERR_CUDA, "state hand-over launch failed");
-        else if (cudaStreamSynchronize(h->stream) != cudaSuccess) rc = fail(BIOT_ERR_CUDA, "state hand-over failed");
+        else if ((rc = dev_encode(h))) {
+        } else if (cudaStreamSynchronize(h->stream) != cudaSuccess) rc = fail(BIOT_ERR_CUDA, "state hand-over failed");
     }
     if (!rc) {
         h->launches += s->launches + 1;
@@ -823,6 +839,22 @@ int flow_typed(biot_ctx *h)
     return BIOT_OK;
 }
 
+// The finest level's deviation store from its FP32 planes 2-4 (no-op without one).
+int dev_encode(biot_ctx *h)
+{
+    if (!h->dev) return BIOT_OK;
+    Level &Lf = h->lv[h->L - 1];
+    DevEncodeArgs e{};
+    e.np = (size_t)h->P.nx * h->P.ny;
+    e.g = static_cast<const float *>(Lf.g[Lf.cur]);
+    e.gd = Lf.gd[Lf.cur];
+    e.dsc = h->dsc;
+    e.dev = h->dev;
+    CUDA_TRY(launch_dev_encode(e, h->stream));
+    h->launches++;
+    return BIOT_OK;
+}
+
 template <typename T>
 int init_typed(biot_ctx *h)
 {
@@ -839,6 +871,8 @@ int init_typed(biot_ctx *h)
     a.c0h2 = h->P.c0 * h->h * h->h;
     CUDA_TRY(launch_init<T>(a, h->stream));
     h->launches++;
+    int rc = dev_encode(h);
+    if (rc) return rc;
     h->initialized = true;
     return BIOT_OK;
 }
@@ -1127,6 +1161,7 @@ int create_instance(const biot_params *p, const biot_side sides[4], biot_handle 
     h->P = *p;
     h->L = p->mg_levels;
     h->fp32 = p->precision != BIOT_FP64;  // finest level and flow populations in FP32
+    h->dev = p->precision == BIOT_FP32_DEV16 ? 1 : p->precision == BIOT_FP32_DEVBF16 ? 2 : 0;
     h->cold64 = h->fp32 && cold_fp64_for(p);
     h->h = p->lx / p->nx;
     h->lam = p->c0 * p->lambda;
@@ -1139,6 +1174,25 @@ int create_instance(const biot_params *p, const biot_side sides[4], biot_handle 
     for (int i = 0; i < 4; i++) {
         h->bc_eta[i] = sides[i].eta_type;
         h->bc_p[i] = sides[i].p_type;
+    }
+    if (h->dev) {
+        // scale of the deviation store: the lattice stress c0 h sigma_ref of the
+        // largest boundary traction (or of the stress lambda + 2 mu times the
+        // largest boundary displacement over the domain size), taken to about 1,
+        // so that FP16's normal range covers several decades on both sides
+        double sref = 0.0;
+        for (int i = 0; i < 4; i++) {
+            if (!sides[i].eta_profile) continue;
+            const size_t m = 2 * (size_t)((i == BIOT_BOTTOM || i == BIOT_TOP) ? p->nx : p->ny) + 1;
+            double mx = 0.0;
+            for (size_t k = 0; k < 2 * m; k++) mx = std::max(mx, std::fabs(sides[i].eta_profile[k]));
+            if (sides[i].eta_type == BIOT_NEUMANN) sref = std::max(sref, mx);
+            else if (sides[i].eta_type == BIOT_DIRICHLET) sref = std::max(sref, (p->lambda + 2.0 * p->mu) * mx / std::max(p->lx, p->ly));
+        }
+        if (!(sref > 0.0) || !std::isfinite(sref)) sref = 1.0;
+        const int e = std::max(-60, std::min(60, (int)std::lround(-std::log2(p->c0 * h->h * sref))));
+        h->dsc = std::ldexp(1.0f, e);
+        h->dinv = std::ldexp(1.0f, -e);
     }
     if (cudaStreamCreateWithFlags(&h->own_stream, cudaStreamNonBlocking) != cudaSuccess) {
         cudaGetLastError();
@@ -1173,6 +1227,10 @@ int create_instance(const biot_params *p, const biot_side sides[4], biot_handle 
             TRY_RC(dev_alloc(h, &Lv.glo[1], 2 * Lv.np * esz));
         }
         if (l < h->L - 1) TRY_RC(dev_alloc(h, &Lv.r, 8 * Lv.np * esz));
+        if (l == h->L - 1 && h->dev) {  // 16-bit m_11, m_s, m_d
+            TRY_RC(dev_alloc(h, &Lv.gd[0], 3 * Lv.np * 2));
+            TRY_RC(dev_alloc(h, &Lv.gd[1], 3 * Lv.np * 2));
+        }
         for (int s = 0; s < 4; s++) {
             if (h->bc_eta[s] != BIOT_DIRICHLET) continue;
             const int n = (s == BIOT_BOTTOM || s == BIOT_TOP) ? Lv.nx : Lv.ny;
@@ -1555,7 +1613,7 @@ int level_variant(const biot_ctx *h, int l, int mode)
     const bool tile = (long)h->lv[l].nx * h->lv[l].ny <= batch_tile_max_cells() || h->lv[l].fp64;
     return (fine ? 0 : SWEEP_V_COARSE) | (level_lo(h, l, false) ? SWEEP_V_LO : 0) |
            (mode == SWEEP_RESTRICT ? SWEEP_V_RESTRICT : 0) | (h->P.ne_fixed > 0 ? SWEEP_V_NOGHOST : 0) |
-           (tile ? SWEEP_V_TILE : 0);
+           (tile ? SWEEP_V_TILE : 0) | (fine && h->dev == 1 ? SWEEP_V_DEV16 : 0) | (fine && h->dev == 2 ? SWEEP_V_DEVBF16 : 0);
 }
 
 // Strip heights of one batched launch (levels of nx x ny cells): the fewest whole
@@ -2066,6 +2124,8 @@ size_t estimate_bytes(const biot_params *p, const biot_side *sides)
         b += 2 * 8 * n * esz;
         if (!fp64 && (l == p->mg_levels - 1 || coarse_lo_mode(p) != COARSE_LO_OFF)) b += 2 * 2 * n * esz;
         if (l < p->mg_levels - 1) b += 8 * n * esz;
+        if (l == p->mg_levels - 1 && (p->precision == BIOT_FP32_DEV16 || p->precision == BIOT_FP32_DEVBF16))
+            b += 2 * 3 * n * 2;
         for (int s = 0; s < 4; s++)
             if (sides && sides[s].eta_type == BIOT_DIRICHLET) b += 3 * ((s == BIOT_BOTTOM || s == BIOT_TOP) ? nx : ny) * esz;
     }
@@ -2589,6 +2649,7 @@ std::vector<CkptPart> ckpt_parts(biot_ctx *h)
     v.push_back({h->f[h->fcur], 9 * np * tsz});
     v.push_back({Lf.g[Lf.cur], 8 * np * esz});
     if (Lf.glo[Lf.cur]) v.push_back({Lf.glo[Lf.cur], 2 * np * esz});
+    if (Lf.gd[Lf.cur]) v.push_back({Lf.gd[Lf.cur], 3 * np * 2});
     v.push_back({h->Ft, 2 * np * tsz});
     v.push_back({h->D1, np * sizeof(double)});
     v.push_back({h->D2, np * sizeof(double)});

@@ -16,6 +16,8 @@
 // c_s^2 = 1/3; scaling of §2.2 with L = h, T = dt, H = 1, eps = h.
 //
 #pragma once
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -173,5 +175,20 @@ __device__ __forceinline__ double dirichlet_term(const double *prof, int side, i
 }
 
 __device__ __forceinline__ double nan_to_inf(double v) { return (v == v) ? v : (double)INFINITY; }
+
+// 16-bit values of the deviation store: DEV 1 = IEEE FP16, 2 = BF16, rounded
+// to nearest on the way in.
+template <int DEV>
+__device__ __forceinline__ float dev_load(const void *p, size_t i)
+{
+    if constexpr (DEV == 1) return __half2float(static_cast<const __half *>(p)[i]);
+    else return __bfloat162float(static_cast<const __nv_bfloat16 *>(p)[i]);
+}
+template <int DEV>
+__device__ __forceinline__ void dev_store(void *p, size_t i, float v)
+{
+    if constexpr (DEV == 1) static_cast<__half *>(p)[i] = __float2half_rn(v);
+    else static_cast<__nv_bfloat16 *>(p)[i] = __float2bfloat16_rn(v);
+}
 
 }  // namespace biot

@@ -62,3 +62,25 @@ cudaError_t biot::launch_narrow_state(const biot::NarrowArgs &a, cudaStream_t s)
     k_narrow_state<<<blocks, 256, 0, s>>>(a);
     return cudaGetLastError();
 }
+
+// The deviation store encoded from FP32 planes 2-4 (see DevEncodeArgs).
+__global__ void __launch_bounds__(256) k_dev_encode(const biot::DevEncodeArgs a)
+{
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.np; i += (size_t)gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            const float v = a.g[(2 + k) * a.np + i] * a.dsc;
+            if (a.dev == 1) biot::dev_store<1>(a.gd, k * a.np + i, v);
+            else biot::dev_store<2>(a.gd, k * a.np + i, v);
+        }
+    }
+}
+
+cudaError_t biot::launch_dev_encode(const biot::DevEncodeArgs &a, cudaStream_t s)
+{
+    if (a.np == 0) return cudaSuccess;
+    if (a.dev != 1 && a.dev != 2) return cudaErrorInvalidValue;
+    const unsigned blocks = (unsigned)((a.np + 255) / 256 < 65536 ? (a.np + 255) / 256 : 65536);
+    k_dev_encode<<<blocks, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}

@@ -115,13 +115,15 @@ template <typename T, typename TC>
 cudaError_t launch_sweep_batch_impl(int v, const BatchParams<T, TC> &P, cudaStream_t s)
 {
     return dispatch_kind<T, TC, BatchRun>(v & SWEEP_V_COARSE, v & SWEEP_V_LO, v & SWEEP_V_RESTRICT,
-                                         !(v & SWEEP_V_NOGHOST), (v & SWEEP_V_TILE) != 0, P, s);
+                                         !(v & SWEEP_V_NOGHOST), (v & SWEEP_V_DEV16) ? 1 : (v & SWEEP_V_DEVBF16) ? 2 : 0,
+                                         (v & SWEEP_V_TILE) != 0, P, s);
 }
 
 template <typename T, typename TC>
 int sweep_slots_impl(int v)
 {
-    return dispatch_kind<T, TC, SlotsRun>(v & SWEEP_V_COARSE, v & SWEEP_V_LO, v & SWEEP_V_RESTRICT, !(v & SWEEP_V_NOGHOST));
+    return dispatch_kind<T, TC, SlotsRun>(v & SWEEP_V_COARSE, v & SWEEP_V_LO, v & SWEEP_V_RESTRICT, !(v & SWEEP_V_NOGHOST),
+                                          (v & SWEEP_V_DEV16) ? 1 : (v & SWEEP_V_DEVBF16) ? 2 : 0);
 }
 
 }  // namespace biot

@@ -58,9 +58,13 @@ namespace biot {
 // independent of them, and only the residual norm contains them.  With fixed
 // V-cycle counts they are elided (the norm then covers the other five moments'
 // residuals); the tolerance mode keeps them for the paper's norm.
-enum { KIND_FINE = 0, KIND_COARSE = 1, KIND_NOGHOST = 2 };
+// KIND bits 2-3 (finest FP32 level without ghost moments only): m_11, m_s, m_d
+// come from and go to the 16-bit deviation store, FP16 (KIND_DEV16) or BF16
+// (KIND_DEVBF16).
+enum { KIND_FINE = 0, KIND_COARSE = 1, KIND_NOGHOST = 2, KIND_DEV16 = 4, KIND_DEVBF16 = 8 };
 __host__ __device__ constexpr bool kind_fine(int k) { return (k & 1) == 0; }
 __host__ __device__ constexpr bool kind_ghosts(int k) { return (k & KIND_NOGHOST) == 0; }
+__host__ __device__ constexpr int kind_dev(int k) { return (k & KIND_DEV16) ? 1 : (k & KIND_DEVBF16) ? 2 : 0; }
 
 template <typename T>
 struct alignas(4 * sizeof(T)) V4 {
@@ -202,13 +206,17 @@ __device__ __forceinline__ void fetch_cell(const SweepArgs<T, TC> &a, int gx, in
     constexpr int NM = kind_ghosts(KIND) ? 8 : 5;  // moment planes loaded
     const bool zero = FM == FETCH_ZERO || (FM == FETCH_DYN && a.zero_init);
     const bool prol = FM == FETCH_PROL || (FM == FETCH_DYN && a.gc != nullptr);
+    constexpr int DEV = kind_dev(KIND);
     if (zero) {
 #pragma unroll
         for (int k = 0; k < 8; k++) v[k] = T(0);
     } else {
         const T *g = a.g + idx;
 #pragma unroll
-        for (int k = 0; k < NM; k++) v[k] = g[k * NP];
+        for (int k = 0; k < NM; k++) {
+            if (DEV && k >= 2 && k <= 4) v[k] = T(dev_load<DEV>(a.gd, (k - 2) * NP + idx)) * T(a.dinv);
+            else v[k] = g[k * NP];
+        }
 #pragma unroll
         for (int k = NM; k < 8; k++) v[k] = T(0);
     }
@@ -590,6 +598,41 @@ __device__ __forceinline__ void residual_cell(const SweepArgs<T, TC> &a, const R
     if (!GH) d[5] = d[6] = d[7] = T(0);  // elided ghost moments (see KIND_NOGHOST)
 }
 
+// The smoothed iterate m - gamma d of the cell at idx (eq. MG:smoother in
+// moment space): the first moments as (hi + lo) - gamma d renormalised into hi +
+// lo with LO; m_11, m_s, m_d into the deviation store (and, in the last sweep of
+// a solve, also in FP32) when the level has one.
+template <typename T, typename TC, int KIND, bool LO>
+__device__ __forceinline__ void store_smoothed(const SweepArgs<T, TC> &a, size_t idx, size_t NP, const OwnCell<T> &own,
+                                               const T (&d)[8], T gam)
+{
+    constexpr int DEV = kind_dev(KIND);
+    const T(&gcur)[8] = own.g;
+    T *go = a.gout + idx;
+#pragma unroll
+    for (int k = 2; k < (kind_ghosts(KIND) ? 8 : 5); k++) {
+        const T v = gcur[k] - gam * d[k];
+        if (DEV && k <= 4) {
+            dev_store<DEV>(a.gd_out, (k - 2) * NP + idx, float(v * T(a.dsc)));
+            if (a.dev_full) go[k * NP] = v;
+        } else {
+            go[k * NP] = v;
+        }
+    }
+    if constexpr (LO) {
+#pragma unroll
+        for (int k = 0; k < 2; k++) {
+            T hi, lw;
+            two_sum(gcur[k], own.lo[k] - gam * d[k], hi, lw);
+            go[k * NP] = hi;
+            a.glo_out[k * NP + idx] = lw;
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < 2; k++) go[k * NP] = gcur[k] - gam * d[k];
+    }
+}
+
 // One strip (column block bx, row block by of TY rows) of one sweep; the body
 // of both the single-instance kernel and the batched work-list kernel.  The CTA
 // has NT threads and a window of W = NT * CPT columns: thread t owns the ring
@@ -705,23 +748,7 @@ __device__ __forceinline__ void sweep_strip(const SweepArgs<T, TC> &a, int bx, i
                 if (!INT && (wall_col[j] || wall_row)) residual_cell<T, TC, KIND, LO, W, true>(a, rg, x, y, sl, c, perx, pery, own, d);
                 else residual_cell<T, TC, KIND, LO, W, false>(a, rg, x, y, sl, c, perx, pery, own, d);
                 if (!RESTRICT) {
-                    const size_t idx = (size_t)y * nx + x;
-                    T *go = a.gout + idx;
-#pragma unroll
-                    for (int k = 2; k < (kind_ghosts(KIND) ? 8 : 5); k++) go[k * NP] = gcur[k] - gam * d[k];
-                    // first moments: (hi + lo) - gamma d, renormalised into hi + lo with LO
-                    if constexpr (LO) {
-#pragma unroll
-                        for (int k = 0; k < 2; k++) {
-                            T hi, lw;
-                            two_sum(gcur[k], own.lo[k] - gam * d[k], hi, lw);
-                            go[k * NP] = hi;
-                            a.glo_out[k * NP + idx] = lw;
-                        }
-                    } else {
-#pragma unroll
-                        for (int k = 0; k < 2; k++) go[k * NP] = gcur[k] - gam * d[k];
-                    }
+                    store_smoothed<T, TC, KIND, LO>(a, (size_t)y * nx + x, NP, own, d, gam);
                     if (a.resmax) {
                         rmax = fmax(rmax, pop_absmax(d));
                         gmax = fmax(gmax, pop_absmax(gcur));
@@ -881,23 +908,7 @@ __device__ __forceinline__ void tile_body(const SweepArgs<T, TC> &a, int bx, int
         if (wall) residual_cell<T, TC, KIND, LO, W, true>(a, rg, x, y, sl, c, perx, pery, own, d);
         else residual_cell<T, TC, KIND, LO, W, false>(a, rg, x, y, sl, c, perx, pery, own, d);
         if (!RESTRICT) {
-            const size_t idx = (size_t)y * nx + x;
-            T *go = a.gout + idx;
-            const T gam = a.k_gam;
-#pragma unroll
-            for (int k = 2; k < (kind_ghosts(KIND) ? 8 : 5); k++) go[k * NP] = gcur[k] - gam * d[k];
-            if constexpr (LO) {
-#pragma unroll
-                for (int k = 0; k < 2; k++) {
-                    T hi, lw;
-                    two_sum(gcur[k], own.lo[k] - gam * d[k], hi, lw);
-                    go[k * NP] = hi;
-                    a.glo_out[k * NP + idx] = lw;
-                }
-            } else {
-#pragma unroll
-                for (int k = 0; k < 2; k++) go[k * NP] = gcur[k] - gam * d[k];
-            }
+            store_smoothed<T, TC, KIND, LO>(a, (size_t)y * nx + x, NP, own, d, a.k_gam);
             if (a.resmax) {
                 rmax = pop_absmax(d);
                 gmax = pop_absmax(gcur);
@@ -1042,9 +1053,18 @@ cudaError_t launch_rows(const SweepArgs<T, TC> &a, cudaStream_t s)
 
 // Storage kind of a launch from the SWEEP_V_* flags / the arguments.
 template <typename T, typename TC, template <typename, typename, int, bool, bool> class F, typename... A>
-auto dispatch_kind(bool coarse, bool lo, bool rs, bool ghosts, A &&...args)
+auto dispatch_kind(bool coarse, bool lo, bool rs, bool ghosts, int dev, A &&...args)
 {
     const int g = ghosts ? 0 : KIND_NOGHOST;
+    if constexpr (sizeof(T) == 4) {  // the deviation store: finest FP32 level, low parts, no ghost moments
+        if (dev && !coarse && lo && !ghosts) {
+            if (dev == 1)
+                return rs ? F<T, TC, KIND_FINE | KIND_NOGHOST | KIND_DEV16, true, true>::run(args...)
+                          : F<T, TC, KIND_FINE | KIND_NOGHOST | KIND_DEV16, true, false>::run(args...);
+            return rs ? F<T, TC, KIND_FINE | KIND_NOGHOST | KIND_DEVBF16, true, true>::run(args...)
+                      : F<T, TC, KIND_FINE | KIND_NOGHOST | KIND_DEVBF16, true, false>::run(args...);
+        }
+    }
     if (coarse) {
         if constexpr (sizeof(T) == 4) {
             if (lo) {
@@ -1075,7 +1095,8 @@ struct RowsRun {
 template <typename T, typename TC>
 cudaError_t launch_sweep_mom_impl(const SweepArgs<T, TC> &a, cudaStream_t s)
 {
-    return dispatch_kind<T, TC, RowsRun>(a.Ft == nullptr, a.glo != nullptr, a.mode == SWEEP_RESTRICT, a.ghosts != 0, a, s);
+    return dispatch_kind<T, TC, RowsRun>(a.Ft == nullptr, a.glo != nullptr, a.mode == SWEEP_RESTRICT, a.ghosts != 0,
+                                         a.dev, a, s);
 }
 
 }  // namespace biot

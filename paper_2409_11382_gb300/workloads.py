@@ -24,7 +24,7 @@ import numpy as np
 
 PERIODIC, SYMMETRY, DIRICHLET, NEUMANN = 0, 1, 2, 3
 BOTTOM, RIGHT, TOP, LEFT = 0, 1, 2, 3
-FP64, FP32, FP32_COARSE64 = 0, 1, 2
+FP64, FP32, FP32_COARSE64, FP32_DEV16, FP32_DEVBF16 = 0, 1, 2, 3, 4
 
 
 def _params(n, *, lam, mu, alpha, c0, kappa, dt, levels, K=4, gamma=0.75, r=0.5,
