@@ -133,7 +133,23 @@ typedef struct biot_params {
     int    ne_fixed;   /* > 0: exactly this many V-cycles per step, MG(ne_fixed, K) */
     int    precision;  /* BIOT_FP64, BIOT_FP32, BIOT_FP32_COARSE64, BIOT_FP32_DEV16 or BIOT_FP32_DEVBF16 */
     int    options;    /* BIOT_OPT_* flags (0: defaults) */
+    /* Multigrid cycles and pressure gradient (0 everywhere: the paper's V-cycle
+     * of Alg. 4 and eq. pressure:gradient).  The paper leaves W- and F-cycles and
+     * full multigrid to future work (§5); they are built here as the usual
+     * definitions applied to Alg. 4's correction problem.  Batches take V-cycles
+     * only. */
+    int    cycle;      /* BIOT_CYCLE_V, BIOT_CYCLE_W (the coarse correction by two cycles
+                          in succession) or BIOT_CYCLE_F (by an F-cycle, then a V-cycle) */
+    int    fmg;        /* 1: the first cycle of every elastic solve is a full-multigrid
+                          cycle: the finest defect restricted level by level, the coarsest
+                          level solved, and each finer level started from the prolongated
+                          solution below it and given one cycle */
+    int    pgrad;      /* 0: eq. pressure:gradient (flux moment of f); 1: the central
+                          difference of eq. pressure:gradient:alternative (§3.4) */
 } biot_params;
+#define BIOT_CYCLE_V 0
+#define BIOT_CYCLE_W 1
+#define BIOT_CYCLE_F 2
 
 /* Boundary data of one side.  Profiles are sampled at the 2n+1 arc positions
  * k*h/2, k = 0..2n, along the side (n = nx for bottom/top, ny for left/right;

@@ -69,6 +69,9 @@ typedef struct {
     double gamma;           /* under-relaxation of eq. MG:smoother */
     double tol;             /* residual tolerance (used when ne_fixed <= 0) */
     int ne_max, ne_fixed;   /* cap on V-cycles; fixed V-cycle count when > 0 */
+    int cycle;              /* 0: V-cycle (Alg. 4); 1: W-cycle; 2: F-cycle (reading R20) */
+    int fmg;                /* 1: the first cycle of every elastic solve is a full-multigrid cycle (reading R21) */
+    int pgrad;              /* 0: eq. pressure:gradient; 1: eq. pressure:gradient:alternative (reading R22) */
 } orc_params;
 
 typedef struct {
@@ -102,6 +105,7 @@ typedef struct {
     double *f, *fs, *fn;       /* 9 per cell: pre-collision, post-collision, streamed */
     double *D1, *D2, *Dt;      /* D(t - dt), D(t - 2 dt), D(t) */
     double *sexp;              /* explicit part of s_eff^im in lattice units */
+    double *Pf;                /* sum_i f_i per cell (eq. pressure:gradient:alternative) */
     double *Ft;                /* explicit force F~ (2 per cell) */
     double *fbody, *src;       /* body force f (2 per cell) and source s (1 per cell), dimensional */
     double t;
@@ -397,9 +401,14 @@ static void step_of_iterate(Orc *o, Level *Lv, int fine, const double *g, const 
 
 static double absmax_nan_inf(double v) { return (v == v) ? fabs(v) : INFINITY; }
 
+enum { CYC_V = 0, CYC_W = 1, CYC_F = 2 };
+
 /* ELASTIC_MULTIGRID (Alg. 4) on level index l (0 = coarsest); the iterate
- * Lv->g is updated in place; Ft is NULL on coarse levels (zero explicit force). */
-static void multigrid(Orc *o, int l, const double *Ft)
+ * Lv->g is updated in place; Ft is NULL on coarse levels (zero explicit force).
+ * kind selects how the coarse-grid correction problem is solved (reading R20):
+ * by one cycle of Alg. 4 (V), by two in succession (W), or by an F-cycle
+ * followed by a V-cycle (F). */
+static void multigrid(Orc *o, int l, const double *Ft, int kind)
 {
     Level *Lv = &o->lv[l];
     const int fine = (l == o->L - 1);
@@ -425,7 +434,15 @@ static void multigrid(Orc *o, int l, const double *Ft)
         /* coarse-grid correction: ELASTIC_MULTIGRID(0, r^c, 0, f_*, l-1), homogeneous BCs */
         memset(Lc->g, 0, sizeof(double) * 8 * (size_t)(Lc->nx * Lc->ny));
         Lc->hist_valid = 0;
-        multigrid(o, l - 1, NULL);
+        if (kind == CYC_V) {
+            multigrid(o, l - 1, NULL, CYC_V);
+        } else if (kind == CYC_W) {
+            multigrid(o, l - 1, NULL, CYC_W);
+            multigrid(o, l - 1, NULL, CYC_W);
+        } else {
+            multigrid(o, l - 1, NULL, CYC_F);
+            multigrid(o, l - 1, NULL, CYC_V);
+        }
         /* prolongation P = R^T (copy of the coarse value to its four cells) */
         ORC_PAR_FOR
         for (int y = 0; y < Lv->ny; y++)
@@ -455,6 +472,71 @@ static void multigrid(Orc *o, int l, const double *Ft)
         ORC_PAR_FOR
         for (int c = 0; c < 8 * n; c++) Lv->g[c] = (1.0 - gam) * Lv->g[c] + gam * Lv->gout[c];
     }
+}
+
+/* Full-sum restriction (eq. MG:restriction) of the defect g - gout of level l
+ * into the right-hand side r of level l - 1. */
+static void restrict_defect(Orc *o, int l)
+{
+    Level *Lv = &o->lv[l], *Lc = &o->lv[l - 1];
+    memset(Lc->r, 0, sizeof(double) * 8 * (size_t)(Lc->nx * Lc->ny));
+    for (int y = 0; y < Lv->ny; y++)
+        for (int x = 0; x < Lv->nx; x++) {
+            int pc = (y / 2) * Lc->nx + (x / 2);
+            for (int k = 0; k < 8; k++)
+                Lc->r[8 * pc + k] += Lv->g[8 * (y * Lv->nx + x) + k] - Lv->gout[8 * (y * Lv->nx + x) + k];
+        }
+}
+
+/* Prolongation P = R^T of level l - 1's iterate into level l: the copy of each
+ * coarse value to its four cells, added to (add = 1) or replacing the iterate. */
+static void prolong_into(Orc *o, int l, int add)
+{
+    Level *Lv = &o->lv[l], *Lc = &o->lv[l - 1];
+    ORC_PAR_FOR
+    for (int y = 0; y < Lv->ny; y++)
+        for (int x = 0; x < Lv->nx; x++) {
+            int pc = (y / 2) * Lc->nx + (x / 2);
+            for (int k = 0; k < 8; k++) {
+                double v = Lc->g[8 * pc + k];
+                Lv->g[8 * (y * Lv->nx + x) + k] = add ? Lv->g[8 * (y * Lv->nx + x) + k] + v : v;
+            }
+        }
+}
+
+/* One full-multigrid cycle on the correction problem of the finest iterate
+ * (reading R21; nested iteration): the finest defect is restricted level by
+ * level -- each coarse level passing on the defect of its zero iterate, so every
+ * level holds the right-hand side of the cycle of Alg. 4 that would reach it --
+ * the coarsest level is solved by its 2K sweeps from zero, then each finer level
+ * starts from the prolongated solution of the level below and runs one cycle of
+ * the chosen kind, and the finest level takes the prolongated correction and
+ * one cycle. */
+static void fmg_cycle(Orc *o, const double *Ft, int kind)
+{
+    const int L = o->L;
+    if (L < 2) { multigrid(o, 0, Ft, kind); return; }
+    Level *Lf = &o->lv[L - 1];
+    step_of_iterate(o, Lf, 1, Lf->g, Ft, Lf->gout);
+    restrict_defect(o, L - 1);
+    for (int l = L - 2; l >= 1; l--) {
+        Level *Lv = &o->lv[l];
+        memset(Lv->g, 0, sizeof(double) * 8 * (size_t)(Lv->nx * Lv->ny));
+        Lv->hist_valid = 0;
+        step_of_iterate(o, Lv, 0, Lv->g, NULL, Lv->gout);
+        restrict_defect(o, l);
+    }
+    Level *L0 = &o->lv[0];
+    memset(L0->g, 0, sizeof(double) * 8 * (size_t)(L0->nx * L0->ny));
+    L0->hist_valid = 0;
+    multigrid(o, 0, NULL, CYC_V);
+    for (int l = 1; l <= L - 2; l++) {
+        prolong_into(o, l, 0);
+        o->lv[l].hist_valid = 0;
+        multigrid(o, l, NULL, kind);
+    }
+    prolong_into(o, L - 1, 1);
+    multigrid(o, L - 1, Ft, kind);
 }
 
 /* ---------------------------------------------------------------------------
@@ -487,16 +569,34 @@ static double full_source(const Orc *o, int c)
 static void explicit_force(Orc *o)
 {
     const int nx = o->P.nx, ny = o->P.ny;
+    if (o->P.pgrad) {  /* the zeroth moments, for eq. pressure:gradient:alternative */
+        ORC_PAR_FOR
+        for (int c = 0; c < nx * ny; c++) {
+            double sum = 0.0;
+            for (int i = 0; i < 9; i++) sum += o->f[9 * c + i];
+            o->Pf[c] = sum;
+        }
+    }
     ORC_PAR_FOR
     for (int y = 0; y < ny; y++)
         for (int x = 0; x < nx; x++) {
             int c = y * nx + x;
-            double jx = 0.0, jy = 0.0;
-            for (int i = 0; i < 9; i++) { jx += o->f[9 * c + i] * CX9[i]; jy += o->f[9 * c + i] * CY9[i]; }
-            double gs[2];
+            double gs[2], gpx, gpy;
             central_gradient(o, o->sexp, nx, ny, x, y, gs);
-            double gpx = -3.0 * o->omega * jx + 0.5 * gs[0];
-            double gpy = -3.0 * o->omega * jy + 0.5 * gs[1];
+            if (o->P.pgrad) {
+                /* reading R22: grad^c of p^ = sum f + s'/2 by the central difference of
+                 * eq. pressure:gradient:alternative, the iterate-dependent part of s'
+                 * kept in F_*(g) as with eq. pressure:gradient */
+                double gP[2];
+                central_gradient(o, o->Pf, nx, ny, x, y, gP);
+                gpx = gP[0] + 0.5 * gs[0];
+                gpy = gP[1] + 0.5 * gs[1];
+            } else {
+                double jx = 0.0, jy = 0.0;
+                for (int i = 0; i < 9; i++) { jx += o->f[9 * c + i] * CX9[i]; jy += o->f[9 * c + i] * CY9[i]; }
+                gpx = -3.0 * o->omega * jx + 0.5 * gs[0];
+                gpy = -3.0 * o->omega * jy + 0.5 * gs[1];
+            }
             o->Ft[2 * c + 0] = o->P.c0 * o->h * o->h * o->fbody[2 * c + 0] - o->P.alpha * o->h * gpx;
             o->Ft[2 * c + 1] = o->P.c0 * o->h * o->h * o->fbody[2 * c + 1] - o->P.alpha * o->h * gpy;
         }
@@ -601,7 +701,8 @@ static int elastic_solve(Orc *o)
     Lf->hist_valid = 0;
     int ne = 0, status = 0;
     for (;;) {
-        multigrid(o, o->L - 1, o->Ft);
+        if (ne == 0 && o->P.fmg) fmg_cycle(o, o->Ft, o->P.cycle);
+        else multigrid(o, o->L - 1, o->Ft, o->P.cycle);
         ne++;
         o->total_cycles++;
         if (!isfinite(o->last_res)) { o->diverged = 1; status = -3; break; }
@@ -629,6 +730,7 @@ static int validate(const orc_params *p, const orc_side s[4])
     if (!(p->lx > 0 && p->ly > 0) || fabs(p->lx / p->nx - p->ly / p->ny) > 1e-12 * (p->lx / p->nx)) return -1;
     if (!(p->c0 > 0 && p->kappa > 0 && p->dt > 0 && p->lambda + p->mu > 0 && p->mu > 0)) return -1;
     if (!(p->gamma > 0 && p->gamma <= 1) || p->r < 0 || p->r > 1) return -1;
+    if (p->cycle < 0 || p->cycle > 2 || (p->fmg != 0 && p->fmg != 1) || (p->pgrad != 0 && p->pgrad != 1)) return -1;
     for (int pair = 0; pair < 2; pair++) {
         int a = pair, b = pair + 2;
         if ((s[a].eta_type == ORC_PERIODIC) != (s[b].eta_type == ORC_PERIODIC)) return -1;
@@ -702,6 +804,7 @@ void *orc_create(const orc_params *p, const orc_side sides[4])
     o->D2 = (double *)calloc(n, sizeof(double));
     o->Dt = (double *)calloc(n, sizeof(double));
     o->sexp = (double *)calloc(n, sizeof(double));
+    o->Pf = (double *)calloc(n, sizeof(double));
     o->Ft = (double *)calloc(2 * n, sizeof(double));
     o->fbody = (double *)calloc(2 * n, sizeof(double));
     o->src = (double *)calloc(n, sizeof(double));
@@ -720,7 +823,7 @@ void orc_destroy(void *h)
     }
     for (int s = 0; s < 4; s++) { free(o->eta_prof[s]); free(o->p_prof[s]); }
     free(o->f); free(o->fs); free(o->fn); free(o->D1); free(o->D2); free(o->Dt);
-    free(o->sexp); free(o->Ft); free(o->fbody); free(o->src);
+    free(o->sexp); free(o->Pf); free(o->Ft); free(o->fbody); free(o->src);
     free(o);
 }
 
@@ -903,7 +1006,7 @@ double orc_vcycle(void *h, int reset_history)
 {
     Orc *o = (Orc *)h;
     if (reset_history) o->lv[o->L - 1].hist_valid = 0;
-    multigrid(o, o->L - 1, o->Ft);
+    multigrid(o, o->L - 1, o->Ft, o->P.cycle);
     return o->last_res;
 }
 

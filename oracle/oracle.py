@@ -34,7 +34,7 @@ class _Params(C.Structure):
                 ("c0", C.c_double), ("kappa", C.c_double), ("dt", C.c_double),
                 ("r", C.c_double), ("levels", C.c_int), ("K", C.c_int),
                 ("gamma", C.c_double), ("tol", C.c_double), ("ne_max", C.c_int),
-                ("ne_fixed", C.c_int)]
+                ("ne_fixed", C.c_int), ("cycle", C.c_int), ("fmg", C.c_int), ("pgrad", C.c_int)]
 
 
 class _Side(C.Structure):
@@ -148,7 +148,8 @@ class Oracle:
         self._lib = lib
         p = _Params()
         for name, _ in _Params._fields_:
-            setattr(p, name, params[name])
+            # cycle, fmg, pgrad default to the paper's V-cycle and eq. pressure:gradient
+            setattr(p, name, params[name] if name in params or name not in ("cycle", "fmg", "pgrad") else 0)
         self.nx, self.ny = params["nx"], params["ny"]
         self._keep = []
         arr = (_Side * 4)()

@@ -19,6 +19,7 @@ LIB_PATH = os.path.join(_HERE, "libbiot_gb300.so")
 OK, ERR_INVALID_ARG, ERR_OOM, ERR_DIVERGED, ERR_NOT_CONVERGED, ERR_CUDA, ERR_TIMEOUT, ERR_NO_DEVICE = (
     0, -1, -2, -3, -4, -5, -6, -7)
 FP64, FP32, FP32_COARSE64, FP32_DEV16, FP32_DEVBF16 = 0, 1, 2, 3, 4
+CYCLE_V, CYCLE_W, CYCLE_F = 0, 1, 2
 # biot_params.options (include/biot.h)
 OPT_COARSEST_STORAGE, OPT_COLD_FP64, OPT_COLD_FP32, OPT_COARSE_LO_ALL, OPT_COARSE_LO_OFF = 1, 2, 4, 8, 16
 PERIODIC, SYMMETRY, DIRICHLET, NEUMANN = 0, 1, 2, 3
@@ -53,7 +54,8 @@ class biot_params(C.Structure):
                 ("c0", C.c_double), ("kappa", C.c_double), ("dt", C.c_double),
                 ("r_coupling", C.c_double), ("mg_levels", C.c_int), ("K", C.c_int),
                 ("gamma", C.c_double), ("tol", C.c_double), ("ne_max", C.c_int),
-                ("ne_fixed", C.c_int), ("precision", C.c_int), ("options", C.c_int)]
+                ("ne_fixed", C.c_int), ("precision", C.c_int), ("options", C.c_int),
+                ("cycle", C.c_int), ("fmg", C.c_int), ("pgrad", C.c_int)]
 
 
 class biot_side(C.Structure):
@@ -172,6 +174,9 @@ def _fill_params(p: "biot_params", params: dict) -> "biot_params":
     p.ne_max, p.ne_fixed = int(params["ne_max"]), int(params["ne_fixed"])
     p.precision = int(params.get("precision", FP64))
     p.options = int(params.get("options", 0))
+    p.cycle = int(params.get("cycle", CYCLE_V))
+    p.fmg = int(params.get("fmg", 0))
+    p.pgrad = int(params.get("pgrad", 0))
     return p
 
 

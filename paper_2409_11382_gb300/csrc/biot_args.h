@@ -104,6 +104,8 @@ struct ForceArgs {
     int perx, pery;       // periodic in x / y
     double omega, alpha_h, c0h2;
     T k_m3w, k_mah;       // -3 omega and -alpha h in the storage type (host-evaluated)
+    int central;          // 1: grad of sum_i f_i by the central difference of
+                          //    eq. pressure:gradient:alternative instead of -3 omega sum_i f_i c_i
 };
 
 // Fused flow step (Alg. 3) and explicit force of the next time step: D(t) of

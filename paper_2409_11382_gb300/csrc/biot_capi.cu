@@ -254,6 +254,9 @@ int check_params(const biot_params *p, const biot_side *s)
     constexpr int known = BIOT_OPT_COARSEST_STORAGE | BIOT_OPT_COLD_FP64 | BIOT_OPT_COLD_FP32 |
                           BIOT_OPT_COARSE_LO_ALL | BIOT_OPT_COARSE_LO_OFF;
     if (p->options & ~known) return fail(BIOT_ERR_INVALID_ARG, "unknown option flag");
+    if (p->cycle < BIOT_CYCLE_V || p->cycle > BIOT_CYCLE_F) return fail(BIOT_ERR_INVALID_ARG, "unknown cycle");
+    if (p->fmg != 0 && p->fmg != 1) return fail(BIOT_ERR_INVALID_ARG, "fmg must be 0 or 1");
+    if (p->pgrad != 0 && p->pgrad != 1) return fail(BIOT_ERR_INVALID_ARG, "pgrad must be 0 or 1");
     if ((p->options & BIOT_OPT_COLD_FP64) && (p->options & BIOT_OPT_COLD_FP32))
         return fail(BIOT_ERR_INVALID_ARG, "BIOT_OPT_COLD_FP64 and BIOT_OPT_COLD_FP32 exclude each other");
     if ((p->options & BIOT_OPT_COARSE_LO_ALL) && (p->options & BIOT_OPT_COARSE_LO_OFF))
@@ -465,9 +468,13 @@ int sweep(biot_ctx *h, int l, int mode, bool zero_init, bool prolong, bool want_
     return sweep_typed<float, float>(h, l, mode, zero_init, prolong, want_res, chain);
 }
 
-// ELASTIC_MULTIGRID (Alg. 4) on level l; zero_start: the iterate is zero
-// (coarse-grid correction of a finer level).
-int vcycle(biot_ctx *h, int l, bool zero_start)
+// ELASTIC_MULTIGRID (Alg. 4) on level l.  zero_start: the iterate is zero
+// (coarse-grid correction of a finer level); prolong_first: the first sweep
+// adds the prolongated iterate of level l - 1 to it (the finer levels of a
+// full-multigrid cycle).  kind: how the coarse-grid correction problem is
+// solved -- one cycle of Alg. 4 (V), two in succession (W), or an F-cycle
+// followed by a V-cycle (F).
+int vcycle(biot_ctx *h, int l, bool zero_start, bool prolong_first = false, int kind = BIOT_CYCLE_V)
 {
     const int K = h->P.K;
     const bool fine = (l == h->L - 1);
@@ -475,18 +482,58 @@ int vcycle(biot_ctx *h, int l, bool zero_start)
     // the coarsest level's 2K sweeps, when it is a small FP64 level below the
     // finest, in one launch (a batch records them one by one)
     const Level &Lv = h->lv[l];
-    if (l == 0 && !fine && !h->rec && Lv.fp64 && Lv.nx <= SWEEP_CHAIN_MAX && Lv.ny <= SWEEP_CHAIN_MAX)
+    if (l == 0 && !fine && !h->rec && Lv.fp64 && Lv.nx <= SWEEP_CHAIN_MAX && Lv.ny <= SWEEP_CHAIN_MAX && !prolong_first)
         return sweep(h, 0, SWEEP_SMOOTH, zero_start, false, false, 2 * K);
     for (int k = 0; k < K; k++)
-        if ((rc = sweep(h, l, SWEEP_SMOOTH, zero_start && k == 0, false, false))) return rc;
+        if ((rc = sweep(h, l, SWEEP_SMOOTH, zero_start && k == 0, prolong_first && k == 0, false))) return rc;
     if (l > 0) {
         if ((rc = sweep(h, l, SWEEP_RESTRICT, false, false, false))) return rc;
         h->lv[l - 1].hist_valid = 0;
-        if ((rc = vcycle(h, l - 1, true))) return rc;
+        if (kind == BIOT_CYCLE_V) {
+            if ((rc = vcycle(h, l - 1, true))) return rc;
+        } else if (kind == BIOT_CYCLE_W) {
+            if ((rc = vcycle(h, l - 1, true, false, BIOT_CYCLE_W))) return rc;
+            if ((rc = vcycle(h, l - 1, false, false, BIOT_CYCLE_W))) return rc;
+        } else {
+            if ((rc = vcycle(h, l - 1, true, false, BIOT_CYCLE_F))) return rc;
+            if ((rc = vcycle(h, l - 1, false, false, BIOT_CYCLE_V))) return rc;
+        }
     }
     for (int k = 0; k < K; k++)
         if ((rc = sweep(h, l, SWEEP_SMOOTH, false, l > 0 && k == 0, fine && k == K - 1 && h->measure_cycle))) return rc;
     return BIOT_OK;
+}
+
+// One full-multigrid cycle on the finest level's correction problem (nested
+// iteration): the finest defect is restricted level by level (each coarse
+// level passes on the defect of its zero iterate), the coarsest level is
+// solved by its 2K sweeps from zero, every finer level starts from the
+// prolongated solution of the level below and gets one cycle, and the finest
+// level adds the prolongated correction and gets one cycle.
+int fmg_cycle(biot_ctx *h, int kind)
+{
+    const int L = h->L;
+    int rc;
+    if (L < 2) return vcycle(h, 0, false, false, kind);
+    if ((rc = sweep(h, L - 1, SWEEP_RESTRICT, false, false, false))) return rc;
+    for (int l = L - 2; l >= 1; l--) {
+        h->lv[l].hist_valid = 0;
+        if ((rc = sweep(h, l, SWEEP_RESTRICT, true, false, false))) return rc;
+    }
+    h->lv[0].hist_valid = 0;
+    if ((rc = vcycle(h, 0, true))) return rc;
+    for (int l = 1; l <= L - 2; l++) {
+        h->lv[l].hist_valid = 0;
+        if ((rc = vcycle(h, l, true, true, kind))) return rc;
+    }
+    return vcycle(h, L - 1, false, true, kind);
+}
+
+// The cycle of the elastic solve: the first one of a solve is a full-multigrid
+// cycle when fmg is set.
+int solve_cycle(biot_ctx *h, bool first)
+{
+    return (first && h->P.fmg) ? fmg_cycle(h, h->P.cycle) : vcycle(h, h->L - 1, false, false, h->P.cycle);
 }
 
 template <typename T>
@@ -525,6 +572,7 @@ int force_typed(biot_ctx *h)
     a.c0h2 = h->P.c0 * h->h * h->h;
     a.k_m3w = T(-3.0 * a.omega);
     a.k_mah = T(-a.alpha_h);
+    a.central = h->P.pgrad;
     CUDA_TRY(launch_force<T>(a, h->stream));
     h->launches++;
     return BIOT_OK;
@@ -689,7 +737,7 @@ int elastic_solve(biot_ctx *h)
         const bool measure = !fixed || (ne + 1 == h->P.ne_fixed);
         h->measure_cycle = measure;
         if (measure) CUDA_TRY(cudaMemsetAsync(h->resmax, 0, RES_WORDS * sizeof(unsigned long long), h->stream));
-        if ((rc = vcycle(h, h->L - 1, false))) return rc;
+        if ((rc = solve_cycle(h, ne == 0))) return rc;
         ne++;
         h->total_cycles++;
         if (fixed) {
@@ -751,7 +799,7 @@ int elastic_solve_device_loop(biot_ctx *h)
     // first V-cycle of the step
     h->measure_cycle = true;
     CUDA_TRY(cudaMemsetAsync(h->resmax, 0, RES_WORDS * sizeof(unsigned long long), h->stream));
-    if ((rc = vcycle(h, h->L - 1, false))) return rc;
+    if ((rc = solve_cycle(h, true))) return rc;
     if ((rc = stop_test(h, 1, cond))) return rc;
     // WHILE node after it
     CUDA_TRY(cudaStreamGetCaptureInfo(h->stream, &cs, nullptr, &cg, &deps, nullptr, &ndeps));
@@ -769,7 +817,7 @@ int elastic_solve_device_loop(biot_ctx *h)
     rc = BIOT_OK;
     cudaError_t e = cudaMemsetAsync(h->resmax, 0, RES_WORDS * sizeof(unsigned long long), h->stream);
     if (e != cudaSuccess) rc = fail(BIOT_ERR_CUDA, std::string("cudaMemsetAsync: ") + cudaGetErrorString(e));
-    if (!rc) rc = vcycle(h, h->L - 1, false);
+    if (!rc) rc = solve_cycle(h, false);
     if (!rc) rc = stop_test(h, 0, cond);
     h->stream = main;
     cudaGraph_t body_out = body;
@@ -832,7 +880,7 @@ int flow_typed(biot_ctx *h)
         h->launches++;
     }
     std::swap(h->D1, h->D2);  // D1 <- D(t), D2 <- D(t - dt)
-    h->ft_fresh = true;   // F~ of the next elastic solve is computed
+    h->ft_fresh = !h->P.pgrad;  // F~ of the next elastic solve is computed (eq. pressure:gradient)
     h->se_stale = true;   // the s'_exp buffer was used as scratch
     h->fcur ^= 1;
     h->nstep++;
@@ -1949,6 +1997,8 @@ int biot_batch_create(int count, const biot_params *params, const biot_side *sid
         if (params[i].ne_fixed <= 0) return fail(BIOT_ERR_INVALID_ARG, "batched instances need a fixed number of V-cycles (ne_fixed > 0)");
         if (params[i].K != params[0].K || params[i].ne_fixed != params[0].ne_fixed)
             return fail(BIOT_ERR_INVALID_ARG, "batched instances need equal K and ne_fixed");
+        if (params[i].cycle != BIOT_CYCLE_V || params[i].fmg)
+            return fail(BIOT_ERR_INVALID_ARG, "batched instances run V-cycles (cycle = BIOT_CYCLE_V, fmg = 0)");
     }
     biot_batch_s *b = new (std::nothrow) biot_batch_s();
     if (!b) return fail(BIOT_ERR_OOM, "host allocation failed");

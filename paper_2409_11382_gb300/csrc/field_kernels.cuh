@@ -52,8 +52,23 @@ __global__ void __launch_bounds__(256) k_force(const ForceArgs<T> a)
     const double sSE = se_at(a, x + 1, y - 1), sSW = se_at(a, x - 1, y - 1);
     const T gx_ = T(sE - sW) * T(1.0 / 3.0) + (T(sNE - sNW) + T(sSE - sSW)) * T(1.0 / 12.0);
     const T gy_ = T(sN - sS) * T(1.0 / 3.0) + (T(sNE - sSE) + T(sNW - sSW)) * T(1.0 / 12.0);
-    const T gpx = a.k_m3w * jx + T(0.5) * gx_;
-    const T gpy = a.k_m3w * jy + T(0.5) * gy_;
+    T gpx = a.k_m3w * jx + T(0.5) * gx_;
+    T gpy = a.k_m3w * jy + T(0.5) * gy_;
+    if (a.central) {
+        // eq. pressure:gradient:alternative for sum_i f_i: 3 sum_i w_i c_i P(x + c_i)
+        // (same stencil as grad^c s'_exp; ghosts of non-periodic walls are the
+        // adjacent cell, as for s'_exp)
+        auto P = [&](int xx, int yy) {
+            if (a.perx) xx = wrapi(xx, a.nx); else xx = clampi(xx, a.nx);
+            if (a.pery) yy = wrapi(yy, a.ny); else yy = clampi(yy, a.ny);
+            const T *q = a.f + (size_t)yy * a.nx + xx;
+            return ((q[0] + q[NP]) + (q[2 * NP] + q[3 * NP])) + ((q[4 * NP] + q[5 * NP]) + (q[6 * NP] + q[7 * NP])) + q[8 * NP];
+        };
+        const T pE = P(x + 1, y), pW = P(x - 1, y), pN = P(x, y + 1), pS = P(x, y - 1);
+        const T pNE = P(x + 1, y + 1), pNW = P(x - 1, y + 1), pSE = P(x + 1, y - 1), pSW = P(x - 1, y - 1);
+        gpx = (pE - pW) * T(1.0 / 3.0) + ((pNE + pSE) - (pNW + pSW)) * T(1.0 / 12.0) + T(0.5) * gx_;
+        gpy = (pN - pS) * T(1.0 / 3.0) + ((pNE + pNW) - (pSE + pSW)) * T(1.0 / 12.0) + T(0.5) * gy_;
+    }
     T fx = a.k_mah * gpx, fy = a.k_mah * gpy;
     if (a.fbody) {
         fx += T(a.c0h2 * a.fbody[idx]);

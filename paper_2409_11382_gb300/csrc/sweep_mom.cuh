@@ -184,7 +184,7 @@ __device__ __forceinline__ void two_sum(T a, T b, T &s, T &e)
 // How a sweep's loads form the iterate: from the arguments at run time
 // (a.zero_init, a.gc), or fixed at compile time -- the stored iterate, the
 // stored iterate plus the prolongated coarse correction, or zero.
-enum { FETCH_DYN = 0, FETCH_PLAIN = 1, FETCH_PROL = 2, FETCH_ZERO = 3 };
+enum { FETCH_DYN = 0, FETCH_PLAIN = 1, FETCH_PROL = 2, FETCH_ZERO = 3, FETCH_ZPROL = 4 };
 
 // Raw values of cell (gx, gy): moments of the iterate (+ prolongated coarse
 // correction; with LO its first moments go to the low parts), F~ (FINE) or r
@@ -204,8 +204,8 @@ __device__ __forceinline__ void fetch_cell(const SweepArgs<T, TC> &a, int gx, in
     }
     const size_t idx = (size_t)gy * a.nx + gx;
     constexpr int NM = kind_ghosts(KIND) ? 8 : 5;  // moment planes loaded
-    const bool zero = FM == FETCH_ZERO || (FM == FETCH_DYN && a.zero_init);
-    const bool prol = FM == FETCH_PROL || (FM == FETCH_DYN && a.gc != nullptr);
+    const bool zero = FM == FETCH_ZERO || FM == FETCH_ZPROL || (FM == FETCH_DYN && a.zero_init);
+    const bool prol = FM == FETCH_PROL || FM == FETCH_ZPROL || (FM == FETCH_DYN && a.gc != nullptr);
     constexpr int DEV = kind_dev(KIND);
     if (zero) {
 #pragma unroll
@@ -1019,7 +1019,7 @@ struct SweepKernel {
     {
         static int n = 0;
         if (!n) {
-            for (auto k : {kernel<FETCH_PLAIN>(), kernel<FETCH_PROL>(), kernel<FETCH_ZERO>()})
+            for (auto k : {kernel<FETCH_PLAIN>(), kernel<FETCH_PROL>(), kernel<FETCH_ZERO>(), kernel<FETCH_ZPROL>()})
                 if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
             int dev = 0, sms = 0, per_sm = 0;
             if (cudaGetDevice(&dev) != cudaSuccess) return 0;
@@ -1041,12 +1041,11 @@ cudaError_t launch_rows(const SweepArgs<T, TC> &a, cudaStream_t s)
     if (!slots) return cudaGetLastError() != cudaSuccess ? cudaErrorUnknown : cudaErrorInvalidConfiguration;
     int ty = a.rows > 0 ? a.rows + (a.rows & 1) : sweep_strip_rows(a.nx, a.ny, slots);
     dim3 grid((a.nx + SWEEP_STRIP_COLS - 1) / SWEEP_STRIP_COLS, (a.ny + ty - 1) / ty);
-    // the fetch form is fixed per launch (a restriction sweep never starts from
-    // zero or takes a correction)
-    auto k = a.zero_init && !RESTRICT ? SK::template kernel<FETCH_ZERO>()
-           : a.gc && !RESTRICT         ? SK::template kernel<FETCH_PROL>()
-                                       : SK::template kernel<FETCH_PLAIN>();
-    if (RESTRICT && (a.zero_init || a.gc)) return cudaErrorInvalidValue;
+    // the fetch form is fixed per launch
+    auto k = a.zero_init && a.gc ? SK::template kernel<FETCH_ZPROL>()
+           : a.zero_init         ? SK::template kernel<FETCH_ZERO>()
+           : a.gc                ? SK::template kernel<FETCH_PROL>()
+                                 : SK::template kernel<FETCH_PLAIN>();
     k<<<grid, SWEEP_NT, SK::smem, s>>>(a, ty);
     return cudaGetLastError();
 }

@@ -40,11 +40,32 @@ def test_binding_covers_the_header():
     assert sorted(biot.API_FUNCTIONS) == declared_functions()
 
 
-def test_struct_layout_matches_header():
-    """ctypes mirrors of the structs have the C sizes (x86-64 / aarch64 LP64)."""
+def test_struct_layout_matches_header(tmp_path):
+    """The ctypes mirrors of the header's structs have the sizes and field
+    offsets the C compiler gives them (compiled here from include/biot.h)."""
+    import subprocess
     from paper_2409_11382_gb300 import biot
-    assert C.sizeof(biot.biot_params) == 4 * 2 + 8 * 2 + 8 * 7 + 4 * 2 + 8 * 2 + 4 * 3 + 4  # + tail padding
-    assert C.sizeof(biot.biot_side) == 24
+    structs = {"biot_params": biot.biot_params, "biot_side": biot.biot_side, "biot_stats": biot.biot_stats,
+               "biot_request_info": biot.biot_request_info, "biot_server_stats": biot.biot_server_stats}
+    src = ['#include <stdio.h>', '#include <stddef.h>', '#include "biot.h"', "int main(void) {"]
+    for name, cls in structs.items():
+        src.append(f'printf("{name} size %zu\\n", sizeof({name}));')
+        for field, _ in cls._fields_:
+            cfield = "lambda" if field == "lambda_" else field
+            src.append(f'printf("{name} {field} %zu\\n", offsetof({name}, {cfield}));')
+    src.append("return 0; }")
+    c_file = tmp_path / "layout.c"
+    c_file.write_text("\n".join(src))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(c_file), "-o", str(exe)], check=True)
+    got = {}
+    for line in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.splitlines():
+        name, field, value = line.split()
+        got[(name, field)] = int(value)
+    for name, cls in structs.items():
+        assert got[(name, "size")] == C.sizeof(cls), name
+        for field, _ in cls._fields_:
+            assert got[(name, field)] == getattr(cls, field).offset, (name, field)
 
 
 def _params(**kw):

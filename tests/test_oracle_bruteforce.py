@@ -16,10 +16,11 @@ from oracle import oracle as O
 P, S, D, N = O.PERIODIC, O.SYMMETRY, O.DIRICHLET, O.NEUMANN
 
 
-def setup(n, sides_kind, alpha=1.0, r=0.5, c0=0.3, seed=0):
+def setup(n, sides_kind, alpha=1.0, r=0.5, c0=0.3, seed=0, **extra):
     p = dict(nx=n, ny=n, lx=1.0, ly=1.0, lam=1.0, mu=0.5, alpha=alpha, c0=c0, kappa=0.2,
              dt=0.01, r=r, levels=int(np.log2(n)) - 1, K=2, gamma=0.75, tol=1e-14,
              ne_max=2000, ne_fixed=0)
+    p.update(extra)
     rng = np.random.default_rng(seed)
     prof = np.zeros((2, 2 * n + 1))
     prof[0] = 0.2 * rng.normal(size=2 * n + 1)

@@ -85,10 +85,11 @@ def test_terzaghi_first_order():
     assert np.all((eS[:-1] / eS[1:] > 1.6) & (eS[:-1] / eS[1:] < 3.0))
 
 
-def manufactured_errors(n, alpha, r, ne=3, K=2, tf=1.0, alg1_ne=None):
+def manufactured_errors(n, alpha, r, ne=3, K=2, tf=1.0, alg1_ne=None, extra=None):
     p, sides = W.manufactured_params(n, alpha, r, ne_fixed=ne, K=K)
     if alg1_ne is not None:
         p = W.alg1(p, alg1_ne)
+    p = dict(p, **(extra or {}))
     lam, mu, kap = p["lam"], p["mu"], p["kappa"]
     o = O.Oracle(p, sides)
     x = (np.arange(n) + 0.5) / n
