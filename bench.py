@@ -555,6 +555,27 @@ def oracle_errors(cases, steps):
     return out
 
 
+def strip_oracle_errors(params, sides_fn, steps, eta, p):
+    """L-infinity and L2 relative errors of an x-independent solve (uniform top
+    load, mirror sides) against the FP64 oracle run on the narrowest strip of the
+    same problem whose hierarchy still coarsens (2^(levels-1) columns): every GPU
+    column against the oracle's first column."""
+    from oracle import oracle as O
+    from paper_2409_11382_gb300 import workloads as W
+    w = 1 << (params["levels"] - 1)
+    strip = dict(params, nx=w, lx=params["lx"] * w / params["nx"], precision=W.FP64)
+    o = O.Oracle(strip, sides_fn(w))
+    o.step(steps)
+    eo, po = o.read_u()[0][:, :, :1], o.read_p()[0][:, :1]
+    o.close()
+    out = {}
+    for name, g, r in (("eta", eta, eo), ("p", p, po)):
+        d = g - r
+        out[f"{name}_linf_rel"] = float(np.abs(d).max() / np.abs(r).max())
+        out[f"{name}_l2_rel"] = float(np.sqrt((d * d).sum() / (r * r * np.ones_like(g)).sum()))
+    return out
+
+
 def _percentile(v, q):
     return float(np.percentile(np.asarray(v, dtype=np.float64), q)) if len(v) else None
 
@@ -705,7 +726,9 @@ def run_served(args):
         st = srv.stats()
         checks = [srv.fetch(rid) for rid in ids[:2]]
         ismall = min(range(len(reqs)), key=lambda i: reqs[i][1]["nx"])
+        ilarge = max(range(len(reqs)), key=lambda i: reqs[i][1]["nx"])
         small_res = srv.fetch(ids[ismall])
+        large_res = srv.fetch(ids[ilarge])
     clock_info = clocks.stop() if clocks else None
     lat = [i["t_done"] - i["t_submit"] for i in infos]
 
@@ -734,6 +757,13 @@ def run_served(args):
             same = same and np.array_equal(eta, sol.read_u()[0]) and np.array_equal(pr, sol.read_p()[0])
     _, sp, ss, sT = reqs[ismall]
     accuracy = oracle_errors([((sp, ss), (small_res[0], small_res[1]))], int(round(sT / sp["dt"]))) if rank == 0 else None
+    if rank == 0:
+        _, lp, _, lT = reqs[ilarge]
+        accuracy = {"smallest": accuracy,
+                    "largest": dict(strip_oracle_errors(lp, lambda w: W.top_load_sides(w, W.uniform_load(w)),
+                                                        int(round(lT / lp["dt"])), large_res[0], large_res[1]),
+                                    how=f"{lp['nx']}^2 request after {int(round(lT / lp['dt']))} steps, every column "
+                                        "vs the FP64 oracle on a strip of the same x-independent problem")}
     value = world * cells_steps / makespan / 1e6
     line = {"metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world,
             "steps": args.requests, "accuracy": accuracy, "warmup": 1, "higher_is_better": True, "scaling": "weak",

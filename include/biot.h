@@ -373,6 +373,8 @@ typedef struct biot_server_stats {
     int    queued, peak_resident;
     size_t used_bytes, peak_bytes;
     long   ticks, graph_launches;  /* ticks: scheduler passes that launched or finished work */
+    long   graphs_reused;          /* step graphs taken over from a finished request of the same
+                                      shape (cudaGraphExecUpdate) instead of instantiated */
 } biot_server_stats;
 
 /* Device bytes an instance with these parameters holds (allocation plus the

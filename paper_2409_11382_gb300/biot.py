@@ -71,7 +71,8 @@ class biot_request_info(C.Structure):
 
 class biot_server_stats(C.Structure):
     _fields_ = [("queued", C.c_int), ("peak_resident", C.c_int), ("used_bytes", C.c_size_t),
-                ("peak_bytes", C.c_size_t), ("ticks", C.c_long), ("graph_launches", C.c_long)]
+                ("peak_bytes", C.c_size_t), ("ticks", C.c_long), ("graph_launches", C.c_long),
+                ("graphs_reused", C.c_long)]
 
 
 class biot_stats(C.Structure):

@@ -111,6 +111,58 @@ struct Level {
     int hist_valid = 0;
 };
 
+// Executable step graphs of finished server requests, kept for the next
+// request of the same shape: capturing a step is cheap, instantiating its graph
+// is not, and cudaGraphExecUpdate moves a captured graph's arguments into an
+// existing executable graph of the same topology.  Used by the server's
+// scheduler thread only.
+struct GraphKey {
+    int nx, ny, L, K, ne_fixed, precision, options, cycle, fmg, pgrad;
+    int bc[8];
+    bool operator==(const GraphKey &o) const { return std::memcmp(this, &o, sizeof(GraphKey)) == 0; }
+};
+struct GraphCache {
+    struct Entry {
+        GraphKey key;
+        int par;
+        cudaGraphExec_t exec;
+    };
+    static constexpr size_t CAP = 64;
+    std::deque<Entry> entries;
+    std::atomic<long> reused{0}, rejected{0};  // read by biot_server_stats_get
+    // an executable graph of this key and parity, updated to the captured graph g
+    cudaGraphExec_t take(const GraphKey &key, int par, cudaGraph_t g)
+    {
+        for (auto it = entries.begin(); it != entries.end(); ++it) {
+            if (it->par != par || !(it->key == key)) continue;
+            cudaGraphExec_t e = it->exec;
+            entries.erase(it);
+            cudaGraphExecUpdateResultInfo info;
+            if (cudaGraphExecUpdate(e, g, &info) == cudaSuccess) {
+                reused++;
+                return e;
+            }
+            cudaGetLastError();
+            cudaGraphExecDestroy(e);
+            rejected++;
+            return nullptr;
+        }
+        return nullptr;
+    }
+    void put(const GraphKey &key, int par, cudaGraphExec_t e)
+    {
+        entries.push_back({key, par, e});
+        while (entries.size() > CAP) {
+            cudaGraphExecDestroy(entries.front().exec);
+            entries.pop_front();
+        }
+    }
+    ~GraphCache()
+    {
+        for (Entry &e : entries) cudaGraphExecDestroy(e.exec);
+    }
+};
+
 }  // namespace
 
 struct biot_ctx {
@@ -194,6 +246,7 @@ struct biot_ctx {
     cudaMemPool_t pool = nullptr;
     bool host_lent = false;
     int device = -1;  // the CUDA device current at biot_create (owns every buffer)
+    GraphCache *gcache = nullptr;  // a server's cache of executable step graphs (see GraphCache)
 };
 
 namespace {
@@ -1078,6 +1131,27 @@ int advance(biot_ctx *h)
     return rc;
 }
 
+GraphKey graph_key(const biot_ctx *h)
+{
+    GraphKey k;
+    std::memset(&k, 0, sizeof(k));
+    k.nx = h->P.nx;
+    k.ny = h->P.ny;
+    k.L = h->L;
+    k.K = h->P.K;
+    k.ne_fixed = h->P.ne_fixed;
+    k.precision = h->P.precision;
+    k.options = h->P.options;
+    k.cycle = h->P.cycle;
+    k.fmg = h->P.fmg;
+    k.pgrad = h->P.pgrad;
+    for (int i = 0; i < 4; i++) {
+        k.bc[i] = h->bc_eta[i];
+        k.bc[4 + i] = h->bc_p[i];
+    }
+    return k;
+}
+
 // advance() through a captured CUDA graph (fixed number of V-cycles: the
 // launch sequence and every buffer parity repeat from step to step except the
 // flow ping-pong, hence one graph per parity).
@@ -1095,7 +1169,8 @@ int advance_graph(biot_ctx *h)
             return rc;
         }
         if (e != cudaSuccess) return fail(BIOT_ERR_CUDA, std::string("cudaStreamEndCapture: ") + cudaGetErrorString(e));
-        e = cudaGraphInstantiate(&h->graph[par], g, 0);
+        h->graph[par] = h->gcache ? h->gcache->take(graph_key(h), par, g) : nullptr;
+        e = h->graph[par] ? cudaSuccess : cudaGraphInstantiate(&h->graph[par], g, 0);
         cudaGraphDestroy(g);
         if (e != cudaSuccess) {
             h->graph[par] = nullptr;
@@ -1776,7 +1851,7 @@ int batch_plan(biot_batch_s *b)
     for (int t = 0; t < 3; t++) b->slots[t].clear();
     for (int key = 0; key <= maxkey; key++) {
         for (int tk = 0; tk < 3; tk++) {
-            for (int v = 0; v < 32; v++) {
+            for (int v = 0; v < 128; v++) {  // every combination of the SWEEP_V_* flags
                 std::vector<BatchSlot> grp;
                 for (const BatchSlot &s : bykey[key]) {
                     const biot_ctx *h = b->inst[s.inst];
@@ -1901,7 +1976,14 @@ int batch_capture(biot_batch_s *b, int par)
         nl += h->launches - l0[i];
         if (!rc && rec[i].size() != b->nops[i]) rc = fail(BIOT_ERR_CUDA, "batched schedule does not match the recorded sweeps");
     }
-    // every recorded sweep must be of the kind its planned launch instantiates
+    // every recorded sweep must be planned, and of the kind its planned launch instantiates
+    {
+        size_t planned = 0;
+        for (const BatchLaunch &L : b->launches) planned += (size_t)L.njobs;
+        size_t recorded = 0;
+        for (int i = 0; i < n; i++) recorded += rec[i].size();
+        if (!rc && planned != recorded) rc = fail(BIOT_ERR_CUDA, "batched schedule: a recorded sweep has no planned launch");
+    }
     for (size_t k = 0; k < b->launches.size() && !rc; k++) {
         const BatchLaunch &L = b->launches[k];
         for (int j = 0; j < L.njobs && !rc; j++) {
@@ -2231,6 +2313,7 @@ struct biot_server_s {
     cudaMemPool_t pool = nullptr;
     unsigned char *host_arena = nullptr;
     std::vector<int> free_slots;  // worker thread only
+    GraphCache gcache;            // worker thread only
     static constexpr size_t SLOT_BYTES = 256;
     static_assert(RES_WORDS * sizeof(unsigned long long) + sizeof(StopState) <= SLOT_BYTES, "arena slot");
     double now() const { return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count(); }
@@ -2254,6 +2337,13 @@ void server_finish(biot_server_s *S, Request &r, int status, const std::string &
         }
     } else {
         r.error = err;
+    }
+    if (status == BIOT_OK && r.h->use_graphs) {  // the step graphs serve the next request of this shape
+        for (int par = 0; par < 2; par++) {
+            if (!r.h->graph[par]) continue;
+            S->gcache.put(graph_key(r.h), par, r.h->graph[par]);
+            r.h->graph[par] = nullptr;
+        }
     }
     release(r.h);
     r.h = nullptr;
@@ -2304,6 +2394,7 @@ void server_loop(biot_server_s *S)
             }
             if (!rc) {
                 h->cold64 = r->cold64;
+                h->gcache = &S->gcache;
                 rc = ensure_initialized(h);
             }
             if (!rc) {
@@ -2568,6 +2659,7 @@ int biot_server_stats_get(biot_server S, biot_server_stats *o)
     o->peak_bytes = S->peak_used;
     o->ticks = S->ticks;
     o->graph_launches = S->graph_launches;
+    o->graphs_reused = S->gcache.reused.load();
     return BIOT_OK;
 }
 

@@ -52,6 +52,7 @@ def test_served_results_equal_solo_runs_and_overlap():
         results = [srv.fetch(rid) for rid in ids]
         st = srv.stats()
     assert st["peak_resident"] >= 2            # requests were resident together
+    assert st["graphs_reused"] >= 1             # a finished request's step graphs served a later one
     assert st["peak_bytes"] <= budget           # admission kept to the budget
     for info in infos:
         assert info["state"] == biot.REQ_DONE
