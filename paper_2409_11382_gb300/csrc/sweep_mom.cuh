@@ -293,17 +293,22 @@ __device__ __forceinline__ T half_pa_dot(T x, T y)
 // and the high parts m_10, m_01 themselves: a pull adds e/2 a_p . (m_hi(source)
 // - m_hi(target)), a difference of nearby values (exact), so that no
 // displacement-sized value is ever rounded into a population.
-template <typename T, typename TC, int KIND, bool LO, int W>
-__device__ __forceinline__ void collide_cell(const SweepArgs<T, TC> &a, const Rings<T, W, KIND, LO> &rg, int sm, int s,
-                                             int sp, int c)
+template <typename T>
+struct CollideOut {
+    T G[8];   // G_0 .. G_7
+    T mx, my; // high parts of the collision-input m_10, m_01
+};
+
+// The arithmetic of the collision from the cell's own values (moments m0..m4,
+// extra values e in the raw-ring order of RingLayout) and m_s of its eight
+// neighbours; shared by the ring and register forms of the strip sweep, so that
+// both round identically.
+template <typename T, typename TC, int KIND, bool LO, int NE>
+__device__ __forceinline__ CollideOut<T> collide_math(const SweepArgs<T, TC> &a, T m0, T m1, T m2, T m3, T m4,
+                                                     const T (&e)[NE], T dE, T dW, T dN, T dS, T dNE, T dNW, T dSE,
+                                                     T dSW)
 {
     using L = RingLayout<KIND, LO>;
-    const V4<T> q0 = rg.Q(s, 0, c);
-    T e[L::NE];
-    rg.get_extras(s, c, e);
-    T m0 = q0.x, m1 = q0.y, m2 = q0.z, m3 = rg.ms(s, c), m4 = q0.w;
-    const T dE = rg.ms(s, c + 1), dW = rg.ms(s, c - 1), dN = rg.ms(sp, c), dS = rg.ms(sm, c);
-    const T dNE = rg.ms(sp, c + 1), dNW = rg.ms(sp, c - 1), dSE = rg.ms(sm, c + 1), dSW = rg.ms(sm, c - 1);
     const T cf = a.k_fs;  // alpha^2 r/2 * dD/dm_s
     T Fx = cf * ((dE - dW) * T(1.0 / 3.0) + ((dNE + dSE) - (dNW + dSW)) * T(1.0 / 12.0));
     T Fy = cf * ((dN - dS) * T(1.0 / 3.0) + ((dNE + dNW) - (dSE + dSW)) * T(1.0 / 12.0));
@@ -361,36 +366,55 @@ __device__ __forceinline__ void collide_cell(const SweepArgs<T, TC> &a, const Ri
         G5 = hS3 + T(1.0 / 24.0) * Fm;
         G7 = hS3 - T(1.0 / 24.0) * Fm;
     }
-    rg.G(s, 0, c) = G0;
-    rg.G(s, 1, c) = G1;
-    rg.G(s, 2, c) = G2;
-    rg.G(s, 3, c) = G3;
-    rg.G(s, 4, c) = G4;
-    rg.G(s, 5, c) = G5;
-    rg.G(s, 6, c) = G6;
-    rg.G(s, 7, c) = G7;
-    rg.MX(s, c) = m0;
-    rg.MY(s, c) = m1;
+    CollideOut<T> o;
+    o.G[0] = G0;
+    o.G[1] = G1;
+    o.G[2] = G2;
+    o.G[3] = G3;
+    o.G[4] = G4;
+    o.G[5] = G5;
+    o.G[6] = G6;
+    o.G[7] = G7;
+    o.mx = m0;
+    o.my = m1;
+    return o;
+}
+
+template <typename T, typename TC, int KIND, bool LO, int W>
+__device__ __forceinline__ void collide_cell(const SweepArgs<T, TC> &a, const Rings<T, W, KIND, LO> &rg, int sm, int s,
+                                             int sp, int c)
+{
+    using L = RingLayout<KIND, LO>;
+    const V4<T> q0 = rg.Q(s, 0, c);
+    T e[L::NE];
+    rg.get_extras(s, c, e);
+    const T dE = rg.ms(s, c + 1), dW = rg.ms(s, c - 1), dN = rg.ms(sp, c), dS = rg.ms(sm, c);
+    const T dNE = rg.ms(sp, c + 1), dNW = rg.ms(sp, c - 1), dSE = rg.ms(sm, c + 1), dSW = rg.ms(sm, c - 1);
+    const CollideOut<T> o = collide_math<T, TC, KIND, LO, L::NE>(a, q0.x, q0.y, q0.z, rg.ms(s, c), q0.w, e, dE, dW, dN,
+                                                                 dS, dNE, dNW, dSE, dSW);
+#pragma unroll
+    for (int k = 0; k < 8; k++) rg.G(s, k, c) = o.G[k];
+    rg.MX(s, c) = o.mx;
+    rg.MY(s, c) = o.my;
 }
 
 // Post-collision population K of the source cell in slot s, column c, split
 // relative to the target's collision-input first moments (tx, ty high, tlx,
 // tly low parts): sig = G_K + e/2 a_p . ((m_hi - t_hi) - t_lo).
-template <typename T, bool LO, int W, int KIND, int K>
-__device__ __forceinline__ PVal<T> post_at(const Rings<T, W, KIND, LO> &rg, int s, int c, T tx, T ty, T tlx, T tly)
+template <typename T, bool LO, int K>
+__device__ __forceinline__ PVal<T> pval_from(T g, T smx, T smy, T tx, T ty, T tlx, T tly)
 {
     constexpr int p = pair_of(K);
     constexpr bool POS = sign_of(K) > 0;
     T dx = T(0), dy = T(0);
     if constexpr (pa_x(p) != 0.0) {
-        dx = rg.MX(s, c) - tx;
+        dx = smx - tx;
         if constexpr (LO) dx -= tlx;
     }
     if constexpr (pa_y(p) != 0.0) {
-        dy = rg.MY(s, c) - ty;
+        dy = smy - ty;
         if constexpr (LO) dy -= tly;
     }
-    const T g = rg.G(s, K, c);
     T h;
     if constexpr (p == 0) h = mul_rn(T(1.0 / 3.0), dx);
     else if constexpr (p == 1) h = mul_rn(T(1.0 / 3.0), dy);
@@ -405,6 +429,15 @@ __device__ __forceinline__ PVal<T> post_at(const Rings<T, W, KIND, LO> &rg, int 
     v.bx = T(sign_of(K) * 0.5 * pa_x(p));
     v.by = T(sign_of(K) * 0.5 * pa_y(p));
     return v;
+}
+
+template <typename T, bool LO, int W, int KIND, int K>
+__device__ __forceinline__ PVal<T> post_at(const Rings<T, W, KIND, LO> &rg, int s, int c, T tx, T ty, T tlx, T tly)
+{
+    constexpr int p = pair_of(K);
+    const T smx = pa_x(p) != 0.0 ? rg.MX(s, c) : T(0);
+    const T smy = pa_y(p) != 0.0 ? rg.MY(s, c) : T(0);
+    return pval_from<T, LO, K>(rg.G(s, K, c), smx, smy, tx, ty, tlx, tly);
 }
 
 // Population of direction K arriving at cell (x, y) (ring column c0); sl[0..2]
@@ -471,12 +504,21 @@ struct PairOut {
     T dbx, dby;    // beta difference minus a_p (A)
 };
 
+template <typename T, int P>
+__device__ __forceinline__ PairOut<T> pair_from(const PVal<T> &u, const PVal<T> &v);
+
 template <typename T, typename TC, int KIND, bool LO, int W, int P, bool WALL>
 __device__ __forceinline__ PairOut<T> pull_pair(const SweepArgs<T, TC> &a, const Rings<T, W, KIND, LO> &rg, int x, int y,
                                                 const int (&sl)[3], int c0, T tx, T ty, T tlx, T tly, bool perx, bool pery)
 {
     const PVal<T> u = pull<T, TC, KIND, LO, W, pair_first(P), WALL>(a, rg, x, y, sl, c0, tx, ty, tlx, tly, perx, pery);
     const PVal<T> v = pull<T, TC, KIND, LO, W, pair_second(P), WALL>(a, rg, x, y, sl, c0, tx, ty, tlx, tly, perx, pery);
+    return pair_from<T, P>(u, v);
+}
+
+template <typename T, int P>
+__device__ __forceinline__ PairOut<T> pair_from(const PVal<T> &u, const PVal<T> &v)
+{
     PairOut<T> o;
     o.Ss = (u.g + v.g) + (u.h + v.h);
     o.As = (u.g - v.g) + (u.h - v.h);
@@ -505,19 +547,16 @@ struct OwnCell {
     T tx, ty, tlx, tly;
 };
 
-template <typename T, int W, int KIND, bool LO>
-__device__ __forceinline__ OwnCell<T> own_cell(const Rings<T, W, KIND, LO> &rg, int s, int c)
+template <typename T, int KIND, bool LO, int NE>
+__device__ __forceinline__ OwnCell<T> own_from(T m0, T m1, T m2, T m3, T m4, const T (&e)[NE])
 {
     using L = RingLayout<KIND, LO>;
-    const V4<T> q0 = rg.Q(s, 0, c);
-    T e[L::NE];
-    rg.get_extras(s, c, e);
     OwnCell<T> o;
-    o.g[0] = q0.x;
-    o.g[1] = q0.y;
-    o.g[2] = q0.z;
-    o.g[3] = rg.ms(s, c);
-    o.g[4] = q0.w;
+    o.g[0] = m0;
+    o.g[1] = m1;
+    o.g[2] = m2;
+    o.g[3] = m3;
+    o.g[4] = m4;
 #pragma unroll
     for (int i = 0; i < 3; i++) o.g[5 + i] = T(0);
     if constexpr (kind_ghosts(KIND)) {
@@ -546,19 +585,24 @@ __device__ __forceinline__ OwnCell<T> own_cell(const Rings<T, W, KIND, LO> &rg, 
     return o;
 }
 
-// Residual d = m - m** of the cell (x, y) (small parts only, see the file
-// comment); own: the cell's own values.
-template <typename T, typename TC, int KIND, bool LO, int W, bool WALL>
-__device__ __forceinline__ void residual_cell(const SweepArgs<T, TC> &a, const Rings<T, W, KIND, LO> &rg, int x, int y,
-                                              const int (&sl)[3], int c0, bool perx, bool pery, const OwnCell<T> &own,
-                                              T (&d)[8])
+template <typename T, int W, int KIND, bool LO>
+__device__ __forceinline__ OwnCell<T> own_cell(const Rings<T, W, KIND, LO> &rg, int s, int c)
 {
-    const int s0 = sl[1];
+    using L = RingLayout<KIND, LO>;
+    const V4<T> q0 = rg.Q(s, 0, c);
+    T e[L::NE];
+    rg.get_extras(s, c, e);
+    return own_from<T, KIND, LO, L::NE>(q0.x, q0.y, q0.z, rg.ms(s, c), q0.w, e);
+}
+
+// The wall-free part of the residual d = m - m** from the four streamed pairs
+// (shared by the ring and register forms of the strip sweep).
+template <typename T, int KIND, bool LO>
+__device__ __forceinline__ void residual_core(const OwnCell<T> &own, const PairOut<T> &P0, const PairOut<T> &P1,
+                                              const PairOut<T> &P2, const PairOut<T> &P3, T (&d)[8])
+{
     const T(&gcur)[8] = own.g;
     const T tx = own.tx, ty = own.ty, tlx = own.tlx, tly = own.tly;
-#define BIOT_PAIR(P) pull_pair<T, TC, KIND, LO, W, P, WALL>(a, rg, x, y, sl, c0, tx, ty, tlx, tly, perx, pery)
-    const PairOut<T> P0 = BIOT_PAIR(0), P1 = BIOT_PAIR(1), P2 = BIOT_PAIR(2), P3 = BIOT_PAIR(3);
-#undef BIOT_PAIR
     const T mxf = tx + tlx, myf = ty + tly;  // full first moments: beta terms (walls) and the m_12, m_21 residuals
     // odd moments: m**_10 = (A0 + A2 - A3) = small + m_10(x) + dB-terms, etc.
     // (sum_p c_p a_p = (1,0), (0,1), (1/3,0), (0,1/3) for 10, 01, 12, 21)
@@ -577,6 +621,23 @@ __device__ __forceinline__ void residual_cell(const SweepArgs<T, TC> &a, const R
     d[3] = gcur[3] - ((P0.Ss + P1.Ss) + T(2) * (P2.Ss + P3.Ss));
     d[4] = gcur[4] - (P0.Ss - P1.Ss);
     d[7] = gcur[7] - (P2.Ss + P3.Ss);
+}
+
+// Residual d = m - m** of the cell (x, y) (small parts only, see the file
+// comment); own: the cell's own values.
+template <typename T, typename TC, int KIND, bool LO, int W, bool WALL>
+__device__ __forceinline__ void residual_cell(const SweepArgs<T, TC> &a, const Rings<T, W, KIND, LO> &rg, int x, int y,
+                                              const int (&sl)[3], int c0, bool perx, bool pery, const OwnCell<T> &own,
+                                              T (&d)[8])
+{
+    const int s0 = sl[1];
+    const T(&gcur)[8] = own.g;
+    const T tx = own.tx, ty = own.ty, tlx = own.tlx, tly = own.tly;
+#define BIOT_PAIR(P) pull_pair<T, TC, KIND, LO, W, P, WALL>(a, rg, x, y, sl, c0, tx, ty, tlx, tly, perx, pery)
+    const PairOut<T> P0 = BIOT_PAIR(0), P1 = BIOT_PAIR(1), P2 = BIOT_PAIR(2), P3 = BIOT_PAIR(3);
+#undef BIOT_PAIR
+    residual_core<T, KIND, LO>(own, P0, P1, P2, P3, d);
+    const T mxf = tx + tlx, myf = ty + tly;
     constexpr bool GH = kind_ghosts(KIND);
     if (WALL) {
         d[0] -= ((P0.dbx + P2.dbx) - P3.dbx) * mxf + ((P0.dby + P2.dby) - P3.dby) * myf;
@@ -813,6 +874,216 @@ __device__ __forceinline__ void sweep_strip(const SweepArgs<T, TC> &a, int bx, i
     }
 }
 
+// ---------------------------------------------------------------------------
+// Register form of the interior strip (fixed V-cycle counts: no ghost moments).
+// The values only the column's own thread uses stay in registers instead of
+// the shared rings: the raw values of rows y, y+1, y+2 (its moments, F~ or r,
+// low parts), and of the post-collision data the populations 01 and 0-1 --
+// which only the cell above and the cell below pull, both in this column --
+// with m_01 of rows y-1 and y+1.  The rings keep what neighbouring columns
+// read: m_s of three rows, and G_K of the other six directions with m_10,
+// m_01 of three rows.  Shared-memory traffic per cell drops from 34 loads and
+// 13 stores (six of them 128-bit) to 22 loads and 9 stores, all 32-bit.  The
+// arithmetic is that of the ring form (collide_math, pval_from, pair_from,
+// residual_core), so both forms round identically.
+// ---------------------------------------------------------------------------
+constexpr int REG_POST_PLANES = 8;  // G_0, G_2, G_4, G_5, G_6, G_7, m_10, m_01
+__host__ __device__ constexpr int reg_post_plane(int k) { return k == 0 ? 0 : k == 2 ? 1 : k - 2; }
+
+template <typename T>
+constexpr size_t reg_smem_bytes(int W)
+{
+    return (size_t)3 * W * (1 + REG_POST_PLANES) * sizeof(T);
+}
+
+template <typename T, typename TC, int NT, int KIND, bool LO, bool RESTRICT, int FM>
+__device__ __forceinline__ void sweep_strip_reg(const SweepArgs<T, TC> &a, int bx, int by, int TY, unsigned char *smem_raw,
+                                                double (&red)[3][NT / 32])
+{
+    static_assert(!kind_ghosts(KIND), "the register form serves fixed V-cycle counts");
+    using L = RingLayout<KIND, LO>;
+    constexpr int W = NT, RV = L::RV, XV = L::XV, NE = L::NE;
+    static_assert(L::EX == 0 && NE == RV - XV, "extra values follow the moments in the fetched vector");
+    T *rms = reinterpret_cast<T *>(smem_raw);  // [3][W]
+    T *rpost = rms + 3 * W;                     // [3][REG_POST_PLANES][W]
+    auto MSR = [&](int s, int c) -> T & { return rms[s * W + c]; };
+    auto PST = [&](int s, int j, int c) -> T & { return rpost[(s * REG_POST_PLANES + j) * W + c]; };
+
+    const int nx = a.nx;
+    const size_t NP = (size_t)nx * a.ny;
+    const int t = threadIdx.x;
+    const int x0 = bx * (W - 4), y0 = by * TY;
+    const int y1 = min(y0 + TY, a.ny);
+    const int x = x0 - 2 + t;
+    const bool collides = t >= 1 && t < W - 1;
+    const bool writes = t >= 2 && t < W - 2;
+
+    T pv[RV], A[RV], B[RV], C[RV];  // fetched row; raw values of rows y, y+1, y+2
+    auto fetch = [&](int yy) { fetch_cell<T, TC, KIND, LO, RV, FM, true>(a, x, yy, NP, false, false, pv); };
+    auto extras = [&](const T (&v)[RV], T (&e)[NE]) {
+#pragma unroll
+        for (int i = 0; i < NE; i++) e[i] = v[XV + i];
+    };
+    // collide the row whose raw values are R (ring slot s, neighbours' m_s in
+    // slots sm / sp, own m_s below / above msS / msN): post data of the
+    // neighbour-read directions to the ring, the rest returned
+    auto collide = [&](const T (&R)[RV], T msS, T msN, int sm, int s, int sp, T &g1, T &g3, T &my) {
+        T e[NE];
+        extras(R, e);
+        const CollideOut<T> o = collide_math<T, TC, KIND, LO, NE>(
+            a, R[0], R[1], R[2], R[3], R[4], e, MSR(s, t + 1), MSR(s, t - 1), msN, msS, MSR(sp, t + 1),
+            MSR(sp, t - 1), MSR(sm, t + 1), MSR(sm, t - 1));
+        PST(s, 0, t) = o.G[0];
+        PST(s, 1, t) = o.G[2];
+#pragma unroll
+        for (int k = 4; k < 8; k++) PST(s, k - 2, t) = o.G[k];
+        PST(s, 6, t) = o.mx;
+        PST(s, 7, t) = o.my;
+        g1 = o.G[1];
+        g3 = o.G[3];
+        my = o.my;
+    };
+
+    // ring slots: row r in slot (r - y0 + 2) % 3; rows y0-2 .. y0+2 first
+    T msm2;  // own m_s of row y0-2
+    fetch(y0 - 2);
+    msm2 = pv[3];
+    MSR(0, t) = pv[3];
+    fetch(y0 - 1);
+#pragma unroll
+    for (int i = 0; i < RV; i++) A[i] = pv[i];  // row y0-1
+    MSR(1, t) = pv[3];
+    fetch(y0);
+#pragma unroll
+    for (int i = 0; i < RV; i++) B[i] = pv[i];  // row y0
+    MSR(2, t) = pv[3];
+    __syncthreads();
+    T g1m = T(0), mym = T(0), g1c = T(0), myc = T(0), g3n, myn, g1n;
+    if (collides) collide(A, msm2, B[3], 0, 1, 2, g1m, g3n, mym);  // row y0-1
+    fetch(y0 + 1);
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < RV; i++) C[i] = pv[i];  // row y0+1
+    MSR(0, t) = pv[3];
+    fetch(y0 + 2);
+    __syncthreads();
+    if (collides) collide(B, A[3], C[3], 1, 2, 0, g1c, g3n, myc);  // row y0
+    __syncthreads();
+    // from here: A = row y, B = row y+1, pv = row y+2 (C is rebuilt from it)
+#pragma unroll
+    for (int i = 0; i < RV; i++) {
+        A[i] = B[i];
+        B[i] = C[i];
+    }
+
+    T rmax = T(0), gmax = T(0);
+    double rsum = 0.0;
+    T acc[8];
+#pragma unroll
+    for (int k = 0; k < 8; k++) acc[k] = T(0);
+    const T gam = a.k_gam;
+    int sa = 1, sb = 2, sc = 0;  // slots of rows y-1, y, y+1
+
+    for (int y = y0; y < y1; y++) {
+#pragma unroll
+        for (int i = 0; i < RV; i++) C[i] = pv[i];  // (A) row y+2
+        MSR(sa, t) = C[3];
+        fetch(y + 3);
+        __syncthreads();  // (C)
+        if (collides) collide(B, A[3], C[3], sb, sc, sa, g1n, g3n, myn);  // row y+1
+        __syncthreads();  // (E)
+        T d[8];
+#pragma unroll
+        for (int k = 0; k < 8; k++) d[k] = T(0);
+        if (writes) {
+            T e[NE];
+            extras(A, e);
+            const OwnCell<T> own = own_from<T, KIND, LO, NE>(A[0], A[1], A[2], A[3], A[4], e);
+            const T tx = own.tx, ty = own.ty, tlx = own.tlx, tly = own.tly;
+            // the eight pulls: (x - c) for direction c, rows y-1 (slot sa), y (sb), y+1 (sc)
+            const PVal<T> p0 = pval_from<T, LO, 0>(PST(sb, 0, t - 1), PST(sb, 6, t - 1), T(0), tx, ty, tlx, tly);
+            const PVal<T> p2 = pval_from<T, LO, 2>(PST(sb, 1, t + 1), PST(sb, 6, t + 1), T(0), tx, ty, tlx, tly);
+            const PVal<T> p1 = pval_from<T, LO, 1>(g1m, T(0), mym, tx, ty, tlx, tly);
+            const PVal<T> p3 = pval_from<T, LO, 3>(g3n, T(0), myn, tx, ty, tlx, tly);
+            const PVal<T> p4 = pval_from<T, LO, 4>(PST(sa, 2, t - 1), PST(sa, 6, t - 1), PST(sa, 7, t - 1), tx, ty, tlx, tly);
+            const PVal<T> p5 = pval_from<T, LO, 5>(PST(sa, 3, t + 1), PST(sa, 6, t + 1), PST(sa, 7, t + 1), tx, ty, tlx, tly);
+            const PVal<T> p6 = pval_from<T, LO, 6>(PST(sc, 4, t + 1), PST(sc, 6, t + 1), PST(sc, 7, t + 1), tx, ty, tlx, tly);
+            const PVal<T> p7 = pval_from<T, LO, 7>(PST(sc, 5, t - 1), PST(sc, 6, t - 1), PST(sc, 7, t - 1), tx, ty, tlx, tly);
+            residual_core<T, KIND, LO>(own, pair_from<T, 0>(p0, p2), pair_from<T, 1>(p1, p3), pair_from<T, 2>(p4, p6),
+                                       pair_from<T, 3>(p5, p7), d);
+            d[5] = d[6] = d[7] = T(0);  // elided ghost moments
+            if (!RESTRICT) {
+                store_smoothed<T, TC, KIND, LO>(a, (size_t)y * nx + x, NP, own, d, gam);
+                if (a.resmax) {
+                    rmax = fmax(rmax, pop_absmax(d));
+                    gmax = fmax(gmax, pop_absmax(own.g));
+                    rsum += (double)pop_sumsq(d);
+                }
+            }
+        }
+        if (RESTRICT) {
+            const bool odd = ((y - y0) & 1) != 0;
+#pragma unroll
+            for (int k = 0; k < 8; k++) acc[k] = odd ? acc[k] + d[k] : d[k];
+            if (odd) {
+                TC tot[8];
+#pragma unroll
+                for (int k = 0; k < 8; k++) {
+                    const TC mine = (TC)acc[k];
+                    tot[k] = mine + __shfl_down_sync(0xffffffffu, mine, 1);
+                }
+                if (writes && (x & 1) == 0) {
+                    const size_t NPc = NP >> 2;
+                    const size_t cidx = (size_t)(y >> 1) * (nx >> 1) + (x >> 1);
+#pragma unroll
+                    for (int k = 0; k < 5; k++) a.rc[k * NPc + cidx] = tot[k];
+                }
+            }
+        }
+        // rotate: rows y, y+1, y+2 become y-1, y, y+1
+#pragma unroll
+        for (int i = 0; i < RV; i++) {
+            A[i] = B[i];
+            B[i] = C[i];
+        }
+        g1m = g1c;
+        mym = myc;
+        g1c = g1n;
+        myc = myn;
+        const int s_old = sa;
+        sa = sb;
+        sb = sc;
+        sc = s_old;
+    }
+
+    if (!RESTRICT && a.resmax) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            rmax = fmax(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
+            gmax = fmax(gmax, __shfl_xor_sync(0xffffffffu, gmax, o));
+            rsum += __shfl_xor_sync(0xffffffffu, rsum, o);
+        }
+        const int warp = t >> 5, lane = t & 31;
+        if (lane == 0) {
+            red[0][warp] = (double)rmax;
+            red[1][warp] = (double)gmax;
+            red[2][warp] = rsum;
+        }
+        __syncthreads();
+        if (t == 0) {
+            double r0 = 0.0, g0 = 0.0, q0 = 0.0;
+            for (int w = 0; w < NT / 32; w++) {
+                r0 = fmax(r0, red[0][w]);
+                g0 = fmax(g0, red[1][w]);
+                q0 += red[2][w];
+            }
+            atomicMax(&a.resmax[0], (unsigned long long)__double_as_longlong(r0));
+            atomicMax(&a.resmax[1], (unsigned long long)__double_as_longlong(g0));
+            atomicAdd(reinterpret_cast<double *>(&a.resmax[2]), q0);
+        }
+    }
+}
+
 // Whether strip (bx, by) of TY rows lies inside the grid with its whole window
 // (the INT form of sweep_strip applies).
 template <int W>
@@ -826,14 +1097,19 @@ template <typename T, typename TC, int NT, int CPT, int KIND, bool LO, bool REST
 __device__ __forceinline__ void sweep_strip_any(const SweepArgs<T, TC> &a, int bx, int by, int TY, unsigned char *smem_raw,
                                                 double (&red)[3][NT / 32])
 {
-    if (sweep_strip_interior<NT * CPT>(a.nx, a.ny, bx, by, TY))
-        sweep_strip<T, TC, NT, CPT, KIND, LO, RESTRICT, FM, true>(a, bx, by, TY, smem_raw, red);
-    else
+    static_assert(reg_smem_bytes<T>(NT) <= rows_smem_bytes<T, KIND, LO, NT * CPT>(),
+                  "the register form's rings fit in the ring form's shared memory");
+    if (sweep_strip_interior<NT * CPT>(a.nx, a.ny, bx, by, TY)) {
+        if constexpr (CPT == 1 && !kind_ghosts(KIND))
+            sweep_strip_reg<T, TC, NT, KIND, LO, RESTRICT, FM>(a, bx, by, TY, smem_raw, red);
+        else
+            sweep_strip<T, TC, NT, CPT, KIND, LO, RESTRICT, FM, true>(a, bx, by, TY, smem_raw, red);
+    } else
         sweep_strip<T, TC, NT, CPT, KIND, LO, RESTRICT, FM, false>(a, bx, by, TY, smem_raw, red);
 }
 
 template <typename T, typename TC, int NT, int CPT, int KIND, bool LO, bool RESTRICT, int FM>
-__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 768 / (NT * CPT) : 1) k_sweep_mom(const SweepArgs<T, TC> a, int TY)
+__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 896 / (NT * CPT) : 1) k_sweep_mom(const SweepArgs<T, TC> a, int TY)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double red[3][NT / 32];
