@@ -99,6 +99,11 @@ def step_model(params, n, fp64, dev=False):
     (3 planes, once per solve).
     Returns (cell-sweeps per step, bytes per step)."""
     L, K, ne = params["levels"], params["K"], params["ne_fixed"]
+    K_level = list(params.get("K_level", ())) + [0] * 16
+
+    def sweeps(l):  # per-level smoothing sweeps (level l from the coarsest)
+        k = K_level[L - 1 - l]
+        return k if k > 0 else K
     esz = 8 if fp64 else 4
     c64 = coarsest_fp64(params)
     cell_sweeps = 0.0
@@ -111,11 +116,12 @@ def step_model(params, n, fp64, dev=False):
         fine = l == L - 1
         nlo = 2 if (fine and not fp64) else 0
         xin = 2 if fine else 5  # F~ or r
-        prol = 5 * ec / 4.0 / (2 * K) if l > 0 else 0.0  # correction from level l - 1
+        Kl = sweeps(l)
+        prol = 5 * ec / 4.0 / (2 * Kl) if l > 0 else 0.0  # correction from level l - 1
         nst = 3 if (fine and dev) else 0  # moments in the 2-byte store
         smooth = ((5 - nst + nlo) * 2 + xin) * e + nst * 2 * 2 + prol
-        cell_sweeps += ne * 2 * K * c
-        nbytes += ne * 2 * K * c * smooth
+        cell_sweeps += ne * 2 * Kl * c
+        nbytes += ne * 2 * Kl * c * smooth
         if fine and dev:
             nbytes += c * 3 * e  # the FP32 copy of the last sweep of the solve
         if l > 0:

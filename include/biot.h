@@ -112,6 +112,8 @@ extern "C" {
 #define BIOT_TOP    2  /* y = ly, outward normal (0,1)  */
 #define BIOT_LEFT   3  /* x = 0,  outward normal (-1,0) */
 
+#define BIOT_MAX_LEVELS 16
+
 /* Parameters of one instance (all dimensional, §2.1).  Lattice quantities
  * follow the scaling of §2.2 with L = h, T = dt, H = 1 (eps = h). */
 typedef struct biot_params {
@@ -146,6 +148,9 @@ typedef struct biot_params {
                           solution below it and given one cycle */
     int    pgrad;      /* 0: eq. pressure:gradient (flux moment of f); 1: the central
                           difference of eq. pressure:gradient:alternative (§3.4) */
+    int    K_level[BIOT_MAX_LEVELS];  /* smoothing sweeps before and after the coarse correction on
+                          the level j steps below the finest (j = 0: the finest level); 0 takes
+                          K.  biot_autotune_sweeps chooses them */
 } biot_params;
 #define BIOT_CYCLE_V 0
 #define BIOT_CYCLE_W 1
@@ -300,6 +305,22 @@ BIOT_API int biot_load(biot_handle h, const void *buf, size_t size);
  * the first max_levels levels: the rows chosen (0 = not tuned) and the mean
  * time of one sweep (ms). */
 BIOT_API int biot_autotune(biot_handle h, int *rows_out, double *ms_out, int max_levels);
+
+/* Autotune the smoothing sweeps per multigrid level (biot_params.K_level).
+ * On a scratch instance of the same problem (allocated for the call, then
+ * freed), V-cycles run from the zero iterate of the solve at t = 0; for a
+ * candidate set of per-level counts the tuner measures the time of a V-cycle
+ * (CUDA events) and the residual contraction per V-cycle rho (the stopping-test
+ * norm of consecutive V-cycles), and it minimises the time to reduce the
+ * residual by a factor e, time / -ln(rho), by coordinate descent over the
+ * levels with counts from 1 to 8.  The counts found are written to
+ * K_out[0 .. L-1] (level j below the finest at K_out[j]) and, with apply != 0,
+ * set for this instance (its captured graphs are dropped).  Changing the counts
+ * changes the iteration, not its fixed point: with a fixed number of V-cycles
+ * per step the results change within the solver's convergence; the FP64 oracle
+ * takes the same counts.  Needs fixed V-cycles or tolerance mode alike;
+ * batches take the counts through biot_params.K_level at creation. */
+BIOT_API int biot_autotune_sweeps(biot_handle h, int apply, int *K_out, double *rho_out, double *ms_per_cycle_out);
 
 /* ---- batched execution ----------------------------------------------------------
  * Many independent instances (different grids, materials, boundary data) advanced

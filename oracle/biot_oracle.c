@@ -72,6 +72,8 @@ typedef struct {
     int cycle;              /* 0: V-cycle (Alg. 4); 1: W-cycle; 2: F-cycle (reading R20) */
     int fmg;                /* 1: the first cycle of every elastic solve is a full-multigrid cycle (reading R21) */
     int pgrad;              /* 0: eq. pressure:gradient; 1: eq. pressure:gradient:alternative (reading R22) */
+    int K_level[ORC_MAX_LEVELS]; /* smoothing sweeps of the level j below the finest (j = 0: finest);
+                                    <= 0: K (reading R23) */
 } orc_params;
 
 typedef struct {
@@ -403,6 +405,14 @@ static double absmax_nan_inf(double v) { return (v == v) ? fabs(v) : INFINITY; }
 
 enum { CYC_V = 0, CYC_W = 1, CYC_F = 2 };
 
+/* Pre- and post-smoothing sweeps of level index l (0 = coarsest): K of Alg. 4,
+ * or the per-level count (reading R23). */
+static int sweeps_of(const Orc *o, int l)
+{
+    int k = o->P.K_level[o->L - 1 - l];
+    return k > 0 ? k : o->P.K;
+}
+
 /* ELASTIC_MULTIGRID (Alg. 4) on level index l (0 = coarsest); the iterate
  * Lv->g is updated in place; Ft is NULL on coarse levels (zero explicit force).
  * kind selects how the coarse-grid correction problem is solved (reading R20):
@@ -414,8 +424,9 @@ static void multigrid(Orc *o, int l, const double *Ft, int kind)
     const int fine = (l == o->L - 1);
     const int n = Lv->nx * Lv->ny;
     const double gam = o->P.gamma;
+    const int K = sweeps_of(o, l);
     /* pre-smoothing, eq. MG:smoother */
-    for (int k = 0; k < o->P.K; k++) {
+    for (int k = 0; k < K; k++) {
         step_of_iterate(o, Lv, fine, Lv->g, Ft, Lv->gout);
         ORC_PAR_FOR
         for (int c = 0; c < 8 * n; c++) Lv->g[c] = (1.0 - gam) * Lv->g[c] + gam * Lv->gout[c];
@@ -454,9 +465,9 @@ static void multigrid(Orc *o, int l, const double *Ft, int kind)
     /* post-smoothing; on the finest level the last sweep also yields the
      * residual max|g - ELASTIC_STEP(g, F)| of the iterate it starts from
      * (reading R16: the stopping test of the adaptive variant, §3.4) */
-    for (int k = 0; k < o->P.K; k++) {
+    for (int k = 0; k < K; k++) {
         step_of_iterate(o, Lv, fine, Lv->g, Ft, Lv->gout);
-        if (fine && k == o->P.K - 1) {
+        if (fine && k == K - 1) {
             double res = 0.0, gn = 0.0, sq = 0.0;
             for (int c = 0; c < 8 * n; c++) {
                 double a = absmax_nan_inf(Lv->g[c] - Lv->gout[c]);
@@ -731,6 +742,7 @@ static int validate(const orc_params *p, const orc_side s[4])
     if (!(p->c0 > 0 && p->kappa > 0 && p->dt > 0 && p->lambda + p->mu > 0 && p->mu > 0)) return -1;
     if (!(p->gamma > 0 && p->gamma <= 1) || p->r < 0 || p->r > 1) return -1;
     if (p->cycle < 0 || p->cycle > 2 || (p->fmg != 0 && p->fmg != 1) || (p->pgrad != 0 && p->pgrad != 1)) return -1;
+    for (int j = 0; j < ORC_MAX_LEVELS; j++) if (p->K_level[j] > 64) return -1;
     for (int pair = 0; pair < 2; pair++) {
         int a = pair, b = pair + 2;
         if ((s[a].eta_type == ORC_PERIODIC) != (s[b].eta_type == ORC_PERIODIC)) return -1;

@@ -34,7 +34,8 @@ class _Params(C.Structure):
                 ("c0", C.c_double), ("kappa", C.c_double), ("dt", C.c_double),
                 ("r", C.c_double), ("levels", C.c_int), ("K", C.c_int),
                 ("gamma", C.c_double), ("tol", C.c_double), ("ne_max", C.c_int),
-                ("ne_fixed", C.c_int), ("cycle", C.c_int), ("fmg", C.c_int), ("pgrad", C.c_int)]
+                ("ne_fixed", C.c_int), ("cycle", C.c_int), ("fmg", C.c_int), ("pgrad", C.c_int),
+                ("K_level", C.c_int * 16)]
 
 
 class _Side(C.Structure):
@@ -148,6 +149,10 @@ class Oracle:
         self._lib = lib
         p = _Params()
         for name, _ in _Params._fields_:
+            if name == "K_level":  # per-level sweeps (level j below the finest); 0 = K
+                ks = list(params.get("K_level", ())) + [0] * 16
+                p.K_level = (C.c_int * 16)(*ks[:16])
+                continue
             # cycle, fmg, pgrad default to the paper's V-cycle and eq. pressure:gradient
             setattr(p, name, params[name] if name in params or name not in ("cycle", "fmg", "pgrad") else 0)
         self.nx, self.ny = params["nx"], params["ny"]

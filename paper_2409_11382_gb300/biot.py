@@ -37,6 +37,7 @@ API_FUNCTIONS = (
     "biot_estimate_bytes", "biot_server_create", "biot_server_submit", "biot_server_poll",
     "biot_server_wait", "biot_server_fetch", "biot_server_release", "biot_server_stats_get",
     "biot_server_destroy", "biot_autotune", "biot_checkpoint_size", "biot_save", "biot_load",
+    "biot_autotune_sweeps",
 )
 REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_FAILED = 0, 1, 2, 3
 NOALLOC_MAX_CELLS = 262144  # BIOT_NOALLOC_MAX_CELLS of include/biot.h
@@ -55,7 +56,7 @@ class biot_params(C.Structure):
                 ("r_coupling", C.c_double), ("mg_levels", C.c_int), ("K", C.c_int),
                 ("gamma", C.c_double), ("tol", C.c_double), ("ne_max", C.c_int),
                 ("ne_fixed", C.c_int), ("precision", C.c_int), ("options", C.c_int),
-                ("cycle", C.c_int), ("fmg", C.c_int), ("pgrad", C.c_int)]
+                ("cycle", C.c_int), ("fmg", C.c_int), ("pgrad", C.c_int), ("K_level", C.c_int * 16)]
 
 
 class biot_side(C.Structure):
@@ -132,6 +133,7 @@ def load_library(path: str = LIB_PATH):
     lib.biot_batch_read_async.argtypes = [H, PP, PP, PP, P]
     lib.biot_batch_read_wait.argtypes = [H]
     lib.biot_autotune.argtypes = [H, C.POINTER(C.c_int), P, C.c_int]
+    lib.biot_autotune_sweeps.argtypes = [H, C.c_int, C.POINTER(C.c_int), P, P]
     lib.biot_checkpoint_size.argtypes = [H, C.POINTER(C.c_size_t)]
     lib.biot_save.argtypes = [H, C.c_void_p, C.c_size_t]
     lib.biot_load.argtypes = [H, C.c_void_p, C.c_size_t]
@@ -178,6 +180,8 @@ def _fill_params(p: "biot_params", params: dict) -> "biot_params":
     p.cycle = int(params.get("cycle", CYCLE_V))
     p.fmg = int(params.get("fmg", 0))
     p.pgrad = int(params.get("pgrad", 0))
+    ks = [int(k) for k in params.get("K_level", ())] + [0] * 16
+    p.K_level = (C.c_int * 16)(*ks[:16])
     return p
 
 
@@ -352,6 +356,15 @@ class Solver:
                 if rows[2 * l + m]:
                     out[f"L{l}_{name}"] = (rows[2 * l + m], round(ms[2 * l + m], 5))
         return out
+
+    def autotune_sweeps(self, apply: bool = True) -> dict:
+        """biot_autotune_sweeps: smoothing sweeps per level (finest first), the
+        residual contraction per V-cycle and the time of a V-cycle they give."""
+        k = (C.c_int * 16)()
+        rho, ms = C.c_double(), C.c_double()
+        self._check(self._lib.biot_autotune_sweeps(self._h, int(apply), k, C.byref(rho), C.byref(ms)),
+                    "biot_autotune_sweeps")
+        return {"K_level": [int(v) for v in k if v > 0], "rho": rho.value, "ms_per_cycle": ms.value}
 
     def stats(self) -> dict:
         s = biot_stats()

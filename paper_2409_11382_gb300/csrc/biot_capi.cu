@@ -97,6 +97,14 @@ bool coarsest_fp64(const biot_params *p)
     return (p->options & BIOT_OPT_COARSEST_STORAGE) == 0;
 }
 
+// Smoothing sweeps of level index l (0 = coarsest) of an L-level hierarchy:
+// the per-level count for the level L-1-l below the finest, or K.
+int sweeps_of(const biot_params *p, int l)
+{
+    const int k = p->K_level[p->mg_levels - 1 - l];
+    return k > 0 ? k : p->K;
+}
+
 struct Level {
     int nx = 0, ny = 0;
     size_t np = 0;
@@ -119,6 +127,7 @@ struct Level {
 struct GraphKey {
     int nx, ny, L, K, ne_fixed, precision, options, cycle, fmg, pgrad;
     int bc[8];
+    int K_level[BIOT_MAX_LEVELS];
     bool operator==(const GraphKey &o) const { return std::memcmp(this, &o, sizeof(GraphKey)) == 0; }
 };
 struct GraphCache {
@@ -297,6 +306,8 @@ int check_params(const biot_params *p, const biot_side *s)
     if (!(p->c0 > 0) || !(p->kappa > 0) || !(p->dt > 0)) return fail(BIOT_ERR_INVALID_ARG, "c0, kappa, dt must be positive");
     if (!(p->r_coupling >= 0 && p->r_coupling <= 1)) return fail(BIOT_ERR_INVALID_ARG, "r_coupling must lie in [0, 1]");
     if (p->K < 1) return fail(BIOT_ERR_INVALID_ARG, "K must be >= 1");
+    for (int j = 0; j < BIOT_MAX_LEVELS; j++)
+        if (p->K_level[j] > 64) return fail(BIOT_ERR_INVALID_ARG, "K_level entries must not exceed 64");
     if (!(p->gamma > 0 && p->gamma <= 1)) return fail(BIOT_ERR_INVALID_ARG, "gamma must lie in (0, 1]");
     if (p->ne_fixed <= 0 && (p->ne_max < 1 || !(p->tol > 0))) return fail(BIOT_ERR_INVALID_ARG, "tolerance mode needs tol > 0 and ne_max >= 1");
     if (p->precision != BIOT_FP64 && p->precision != BIOT_FP32 && p->precision != BIOT_FP32_COARSE64 &&
@@ -529,7 +540,7 @@ int sweep(biot_ctx *h, int l, int mode, bool zero_init, bool prolong, bool want_
 // followed by a V-cycle (F).
 int vcycle(biot_ctx *h, int l, bool zero_start, bool prolong_first = false, int kind = BIOT_CYCLE_V)
 {
-    const int K = h->P.K;
+    const int K = sweeps_of(&h->P, l);
     const bool fine = (l == h->L - 1);
     int rc;
     // the coarsest level's 2K sweeps, when it is a small FP64 level below the
@@ -1149,6 +1160,7 @@ GraphKey graph_key(const biot_ctx *h)
         k.bc[i] = h->bc_eta[i];
         k.bc[4 + i] = h->bc_p[i];
     }
+    for (int j = 0; j < BIOT_MAX_LEVELS; j++) k.K_level[j] = h->P.K_level[j];
     return k;
 }
 
@@ -1711,13 +1723,16 @@ struct PlanOp {
 // coarsest-level index over the batch.
 void plan_vcycle(const biot_ctx *h, int l, int K, int Dmax, std::vector<PlanOp> &out)
 {
+    // K: the largest per-level sweep count of the batch (the key spacing); this
+    // level runs its own count Kl <= K of the sweeps of each leg
+    const int Kl = sweeps_of(&h->P, l);
     const int bottom = Dmax * (K + 1);  // first key of the coarsest sweeps
-    for (int k = 0; k < K; k++) out.push_back({l, SWEEP_SMOOTH, l == 0 ? bottom + k : (Dmax - l) * (K + 1) + k});
+    for (int k = 0; k < Kl; k++) out.push_back({l, SWEEP_SMOOTH, l == 0 ? bottom + k : (Dmax - l) * (K + 1) + k});
     if (l > 0) {
         out.push_back({l, SWEEP_RESTRICT, (Dmax - l) * (K + 1) + K});
         plan_vcycle(h, l - 1, K, Dmax, out);
     }
-    for (int k = 0; k < K; k++)
+    for (int k = 0; k < Kl; k++)
         out.push_back({l, SWEEP_SMOOTH, l == 0 ? bottom + K + k : bottom + 2 * K + (l - 1) * K + k});
 }
 
@@ -2077,8 +2092,8 @@ int biot_batch_create(int count, const biot_params *params, const biot_side *sid
     if (count < 1 || !params || !sides) return fail(BIOT_ERR_INVALID_ARG, "need count >= 1 and parameter / side arrays");
     for (int i = 0; i < count; i++) {
         if (params[i].ne_fixed <= 0) return fail(BIOT_ERR_INVALID_ARG, "batched instances need a fixed number of V-cycles (ne_fixed > 0)");
-        if (params[i].K != params[0].K || params[i].ne_fixed != params[0].ne_fixed)
-            return fail(BIOT_ERR_INVALID_ARG, "batched instances need equal K and ne_fixed");
+        if (params[i].ne_fixed != params[0].ne_fixed)
+            return fail(BIOT_ERR_INVALID_ARG, "batched instances need equal ne_fixed");
         if (params[i].cycle != BIOT_CYCLE_V || params[i].fmg)
             return fail(BIOT_ERR_INVALID_ARG, "batched instances run V-cycles (cycle = BIOT_CYCLE_V, fmg = 0)");
     }
@@ -2090,7 +2105,10 @@ int biot_batch_create(int count, const biot_params *params, const biot_side *sid
         delete b;
         return fail(BIOT_ERR_CUDA, "cudaStreamCreate failed");
     }
-    b->K = params[0].K;
+    b->K = 1;  // the largest sweep count of any level of any instance (phase-key spacing)
+    for (int i = 0; i < count; i++)
+        for (int l = 0; l < params[i].mg_levels && l < BIOT_MAX_LEVELS; l++)
+            b->K = std::max(b->K, sweeps_of(&params[i], l));
     b->ne = params[0].ne_fixed;
     for (int i = 0; i < count; i++) {
         biot_handle h = nullptr;
@@ -2684,6 +2702,139 @@ int biot_server_destroy(biot_server S)
 // ============================================================================
 // Autotuning of the sweep launch shape.
 // ============================================================================
+// Per-level smoothing counts (see biot.h).  One scratch instance with the
+// caller's boundary data and sources; each candidate set of counts is run from
+// the initial state for a few V-cycles, timed, and its residual contraction per
+// V-cycle measured.
+namespace {
+
+struct SweepTrial {
+    double rho = 1e30, ms = 0.0, cost = 1e300;
+};
+
+int sweep_trial(biot_ctx *c, cudaEvent_t e0, cudaEvent_t e1, SweepTrial &out)
+{
+    int rc;
+    c->initialized = false;
+    if ((rc = ensure_initialized(c))) return rc;
+    c->ft_fresh = false;
+    c->se_stale = true;
+    if ((rc = c->fp32 ? force_typed<float>(c) : force_typed<double>(c))) return rc;
+    c->lv[c->L - 1].hist_valid = 0;
+    c->cold_solve = false;  // time the cycles as a time step runs them
+    c->measure_cycle = true;
+    constexpr int M = 5;
+    double res[M];
+    float ms_sum = 0.f;
+    for (int m = 0; m < M; m++) {
+        CUDA_TRY(cudaMemsetAsync(c->resmax, 0, RES_WORDS * sizeof(unsigned long long), c->stream));
+        CUDA_TRY(cudaEventRecord(e0, c->stream));
+        if ((rc = vcycle(c, c->L - 1, false, false, c->P.cycle))) return rc;
+        CUDA_TRY(cudaEventRecord(e1, c->stream));
+        CUDA_TRY(cudaMemcpyAsync(c->resmax_host, c->resmax, RES_WORDS * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                                 c->stream));
+        CUDA_TRY(cudaStreamSynchronize(c->stream));
+        float ms = 0.f;
+        CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+        if (m > 0) ms_sum += ms;  // the first cycle includes one-off set-up
+        std::memcpy(&res[m], &c->resmax_host[0], sizeof(double));
+    }
+    out.ms = ms_sum / (M - 1);
+    // contraction from the second cycle on (the first leaves the start's transients)
+    const double r1 = res[1], r4 = res[M - 1];
+    if (!(r1 > 0.0) || !std::isfinite(r4)) {
+        out.rho = 1e30;
+        out.cost = 1e300;
+        return BIOT_OK;
+    }
+    out.rho = std::pow(r4 / r1, 1.0 / (M - 2));
+    out.cost = out.rho < 1.0 ? out.ms / -std::log(std::max(out.rho, 1e-30)) : 1e300;
+    return BIOT_OK;
+}
+
+}  // namespace
+
+extern "C" int biot_autotune_sweeps(biot_handle h, int apply, int *K_out, double *rho_out, double *ms_per_cycle_out)
+{
+    if (!h) return fail(BIOT_ERR_INVALID_ARG, "null handle");
+    if (h->rec) return fail(BIOT_ERR_INVALID_ARG, "an instance of a batch: set K_level at creation");
+    int rc;
+    CUDA_TRY(cudaStreamSynchronize(h->stream));
+    biot_side sides[4];
+    for (int i = 0; i < 4; i++) sides[i] = biot_side{h->bc_eta[i], h->bc_p[i], nullptr, nullptr};
+    biot_params p = h->P;
+    p.options |= BIOT_OPT_COLD_FP32;  // the scratch copy never needs an FP64 copy of its own
+    biot_handle c = nullptr;
+    if ((rc = biot_create(&p, sides, &c))) return rc;
+    // the caller's boundary data and sources: the residual of a zero iterate is theirs
+    const size_t np = (size_t)h->P.nx * h->P.ny;
+    for (int side = 0; side < 4 && !rc; side++) {
+        const size_t m = 2 * (size_t)side_cells(h, side) + 1;
+        if (h->eta_prof[side] && !(rc = dev_alloc(c, (void **)&c->eta_prof[side], 2 * m * sizeof(double))))
+            if (cudaMemcpyAsync(c->eta_prof[side], h->eta_prof[side], 2 * m * sizeof(double), cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess)
+                rc = fail(BIOT_ERR_CUDA, "boundary data copy failed");
+        if (!rc && h->p_prof[side] && !(rc = dev_alloc(c, (void **)&c->p_prof[side], m * sizeof(double))))
+            if (cudaMemcpyAsync(c->p_prof[side], h->p_prof[side], m * sizeof(double), cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess)
+                rc = fail(BIOT_ERR_CUDA, "boundary data copy failed");
+    }
+    if (!rc && h->has_src && !(rc = dev_alloc(c, (void **)&c->src, np * sizeof(double)))) {
+        if (cudaMemcpyAsync(c->src, h->src, np * sizeof(double), cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess)
+            rc = fail(BIOT_ERR_CUDA, "source copy failed");
+        c->has_src = true;
+    }
+    if (!rc && h->has_fbody && !(rc = dev_alloc(c, (void **)&c->fbody, 2 * np * sizeof(double)))) {
+        if (cudaMemcpyAsync(c->fbody, h->fbody, 2 * np * sizeof(double), cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess)
+            rc = fail(BIOT_ERR_CUDA, "body force copy failed");
+        c->has_fbody = true;
+    }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (!rc && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)) {
+        cudaGetLastError();
+        rc = fail(BIOT_ERR_CUDA, "cudaEventCreate failed");
+    }
+    const int L = h->L;
+    std::vector<int> best(L);
+    for (int j = 0; j < L; j++) best[j] = sweeps_of(&h->P, L - 1 - j);
+    SweepTrial bt;
+    auto run = [&](const std::vector<int> &K, SweepTrial &t) {
+        for (int j = 0; j < BIOT_MAX_LEVELS; j++) c->P.K_level[j] = j < L ? K[j] : 0;
+        return sweep_trial(c, e0, e1, t);
+    };
+    if (!rc) rc = run(best, bt);
+    static const int cand[] = {1, 2, 3, 4, 6, 8};
+    for (int pass = 0; pass < 2 && !rc; pass++) {
+        bool changed = false;
+        for (int j = 0; j < L && !rc; j++) {
+            for (int k : cand) {
+                if (k == best[j]) continue;
+                std::vector<int> K = best;
+                K[j] = k;
+                SweepTrial t;
+                if ((rc = run(K, t))) break;
+                if (t.cost < 0.97 * bt.cost) {  // a clear gain, not timing noise
+                    bt = t;
+                    best = K;
+                    changed = true;
+                }
+            }
+        }
+        if (!changed) break;
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    release(c);
+    if (rc) return rc;
+    if (K_out)
+        for (int j = 0; j < L; j++) K_out[j] = best[j];
+    if (rho_out) *rho_out = bt.rho;
+    if (ms_per_cycle_out) *ms_per_cycle_out = bt.ms;
+    if (apply) {
+        for (int j = 0; j < BIOT_MAX_LEVELS; j++) h->P.K_level[j] = j < L ? best[j] : 0;
+        drop_graphs(h);
+    }
+    return BIOT_OK;
+}
+
 extern "C" int biot_autotune(biot_handle h, int *rows_out, double *ms_out, int max_levels)
 {
     if (!h) return fail(BIOT_ERR_INVALID_ARG, "null handle");

@@ -268,6 +268,13 @@ __device__ __forceinline__ void store_cell(const Rings<T, W, KIND, LO> &rg, int 
 // code, and an x-independent problem must give identical columns.
 __device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
 __device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+// a * b + c with the rounding fixed by the source, not by the compiler's
+// contraction choices: one fused multiply-add in FP32, a rounded product and a
+// rounded sum in FP64 (the FP64 kernels fuse nothing).  The collision, pull,
+// residual and relaxation arithmetic is shared by inlined copies in different
+// kernels and loop forms; written with these, every copy rounds alike.
+__device__ __forceinline__ float mad_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double mad_rn(double a, double b, double c) { return __dadd_rn(__dmul_rn(a, b), c); }
 
 // a_p . (x, y) / 2 for the odd coefficient vectors a_p of Tab. moments:inverse,
 // zero terms omitted.
@@ -277,10 +284,10 @@ __device__ __forceinline__ T half_pa_dot(T x, T y)
     static_assert(pa_x(0) == 2.0 / 3.0 && pa_y(0) == 0.0 && pa_x(1) == 0.0 && pa_y(1) == 2.0 / 3.0 &&
                       pa_x(2) == 1.0 / 6.0 && pa_y(2) == 1.0 / 6.0 && pa_x(3) == -1.0 / 6.0 && pa_y(3) == 1.0 / 6.0,
                   "coefficients a_p");
-    if constexpr (P == 0) return T(1.0 / 3.0) * x;
-    if constexpr (P == 1) return T(1.0 / 3.0) * y;
-    if constexpr (P == 2) return T(1.0 / 12.0) * (x + y);
-    return T(1.0 / 12.0) * (y - x);
+    if constexpr (P == 0) return mul_rn(T(1.0 / 3.0), x);
+    if constexpr (P == 1) return mul_rn(T(1.0 / 3.0), y);
+    if constexpr (P == 2) return mul_rn(T(1.0 / 12.0), x + y);
+    return mul_rn(T(1.0 / 12.0), y - x);
 }
 
 // Collision of the cell in raw slot s, column c (Alg. 2, first six lines, in
@@ -310,8 +317,8 @@ __device__ __forceinline__ CollideOut<T> collide_math(const SweepArgs<T, TC> &a,
 {
     using L = RingLayout<KIND, LO>;
     const T cf = a.k_fs;  // alpha^2 r/2 * dD/dm_s
-    T Fx = cf * ((dE - dW) * T(1.0 / 3.0) + ((dNE + dSE) - (dNW + dSW)) * T(1.0 / 12.0));
-    T Fy = cf * ((dN - dS) * T(1.0 / 3.0) + ((dNE + dNW) - (dSE + dSW)) * T(1.0 / 12.0));
+    T Fx = mul_rn(cf, mad_rn(dE - dW, T(1.0 / 3.0), mul_rn((dNE + dSE) - (dNW + dSW), T(1.0 / 12.0))));
+    T Fy = mul_rn(cf, mad_rn(dN - dS, T(1.0 / 3.0), mul_rn((dNE + dNW) - (dSE + dSW), T(1.0 / 12.0))));
     T lx = T(0), ly = T(0);  // low parts of the collision-input first moments (LO)
     if constexpr (kind_fine(KIND)) {
         Fx += e[L::EX];  // F~
@@ -333,9 +340,9 @@ __device__ __forceinline__ CollideOut<T> collide_math(const SweepArgs<T, TC> &a,
         m4 -= e[L::EX + 4];
     }
     // halves of the even combinations S*_p, one multiply and one fused multiply-add each
-    const T hd = a.k_hd * m4, h22 = a.k_h22 * m3;
-    const T hS0 = a.k_hs * m3 + hd, hS1 = a.k_hs * m3 - hd;
-    const T hS2 = a.k_hd * m2 + h22, hS3 = h22 - a.k_hd * m2;
+    const T hd = mul_rn(a.k_hd, m4), h22 = mul_rn(a.k_h22, m3);
+    const T hS0 = mad_rn(a.k_hs, m3, hd), hS1 = mad_rn(a.k_hs, m3, -hd);
+    const T hS2 = mad_rn(a.k_hd, m2, h22), hS3 = mad_rn(-a.k_hd, m2, h22);
     // G_K = S*_p/2 + e (a_p . m_lo + b_p . F)/2, b_p = (5/6, 0), (0, 5/6), (1/12, 1/12), (-1/12, 1/12)
     static_assert(pb_x(0) == 5.0 / 6.0 && pb_y(0) == 0.0 && pb_x(1) == 0.0 && pb_y(1) == 5.0 / 6.0 &&
                       pb_x(2) == 1.0 / 12.0 && pb_y(2) == 1.0 / 12.0 && pb_x(3) == -1.0 / 12.0 && pb_y(3) == 1.0 / 12.0,
@@ -346,8 +353,10 @@ __device__ __forceinline__ CollideOut<T> collide_math(const SweepArgs<T, TC> &a,
     const T Fp = Fx + Fy, Fm = Fy - Fx;
     T G0, G1, G2, G3, G4, G5, G6, G7;
     if constexpr (LO) {  // odd parts without the high moments first (small), then one add each
-        const T A0 = T(5.0 / 12.0) * Fx + half_pa_dot<T, 0>(lx, ly), A1 = T(5.0 / 12.0) * Fy + half_pa_dot<T, 1>(lx, ly);
-        const T A2 = T(1.0 / 24.0) * Fp + half_pa_dot<T, 2>(lx, ly), A3 = T(1.0 / 24.0) * Fm + half_pa_dot<T, 3>(lx, ly);
+        const T A0 = mad_rn(T(5.0 / 12.0), Fx, half_pa_dot<T, 0>(lx, ly));
+        const T A1 = mad_rn(T(5.0 / 12.0), Fy, half_pa_dot<T, 1>(lx, ly));
+        const T A2 = mad_rn(T(1.0 / 24.0), Fp, half_pa_dot<T, 2>(lx, ly));
+        const T A3 = mad_rn(T(1.0 / 24.0), Fm, half_pa_dot<T, 3>(lx, ly));
         G0 = hS0 + A0;
         G2 = hS0 - A0;
         G1 = hS1 + A1;
@@ -357,14 +366,14 @@ __device__ __forceinline__ CollideOut<T> collide_math(const SweepArgs<T, TC> &a,
         G5 = hS3 + A3;
         G7 = hS3 - A3;
     } else {  // one fused multiply-add each
-        G0 = hS0 + T(5.0 / 12.0) * Fx;
-        G2 = hS0 - T(5.0 / 12.0) * Fx;
-        G1 = hS1 + T(5.0 / 12.0) * Fy;
-        G3 = hS1 - T(5.0 / 12.0) * Fy;
-        G4 = hS2 + T(1.0 / 24.0) * Fp;
-        G6 = hS2 - T(1.0 / 24.0) * Fp;
-        G5 = hS3 + T(1.0 / 24.0) * Fm;
-        G7 = hS3 - T(1.0 / 24.0) * Fm;
+        G0 = mad_rn(T(5.0 / 12.0), Fx, hS0);
+        G2 = mad_rn(T(-5.0 / 12.0), Fx, hS0);
+        G1 = mad_rn(T(5.0 / 12.0), Fy, hS1);
+        G3 = mad_rn(T(-5.0 / 12.0), Fy, hS1);
+        G4 = mad_rn(T(1.0 / 24.0), Fp, hS2);
+        G6 = mad_rn(T(-1.0 / 24.0), Fp, hS2);
+        G5 = mad_rn(T(1.0 / 24.0), Fm, hS3);
+        G7 = mad_rn(T(-1.0 / 24.0), Fm, hS3);
     }
     CollideOut<T> o;
     o.G[0] = G0;
@@ -615,8 +624,8 @@ __device__ __forceinline__ void residual_core(const OwnCell<T> &own, const PairO
     }
     d[0] = r0 - ((P0.As + P2.As) - P3.As);
     d[1] = r1 - ((P1.As + P2.As) + P3.As);
-    d[5] = (gcur[5] - mxf * T(1.0 / 3.0)) - (P2.As - P3.As);
-    d[6] = (gcur[6] - myf * T(1.0 / 3.0)) - (P2.As + P3.As);
+    d[5] = (gcur[5] - mul_rn(mxf, T(1.0 / 3.0))) - (P2.As - P3.As);
+    d[6] = (gcur[6] - mul_rn(myf, T(1.0 / 3.0))) - (P2.As + P3.As);
     d[2] = gcur[2] - (P2.Ss - P3.Ss);
     d[3] = gcur[3] - ((P0.Ss + P1.Ss) + T(2) * (P2.Ss + P3.Ss));
     d[4] = gcur[4] - (P0.Ss - P1.Ss);
@@ -672,7 +681,7 @@ __device__ __forceinline__ void store_smoothed(const SweepArgs<T, TC> &a, size_t
     T *go = a.gout + idx;
 #pragma unroll
     for (int k = 2; k < (kind_ghosts(KIND) ? 8 : 5); k++) {
-        const T v = gcur[k] - gam * d[k];
+        const T v = mad_rn(-gam, d[k], gcur[k]);
         if (DEV && k <= 4) {
             dev_store<DEV>(a.gd_out, (k - 2) * NP + idx, float(v * T(a.dsc)));
             if (a.dev_full) go[k * NP] = v;
@@ -684,13 +693,13 @@ __device__ __forceinline__ void store_smoothed(const SweepArgs<T, TC> &a, size_t
 #pragma unroll
         for (int k = 0; k < 2; k++) {
             T hi, lw;
-            two_sum(gcur[k], own.lo[k] - gam * d[k], hi, lw);
+            two_sum(gcur[k], mad_rn(-gam, d[k], own.lo[k]), hi, lw);
             go[k * NP] = hi;
             a.glo_out[k * NP + idx] = lw;
         }
     } else {
 #pragma unroll
-        for (int k = 0; k < 2; k++) go[k * NP] = gcur[k] - gam * d[k];
+        for (int k = 0; k < 2; k++) go[k * NP] = mad_rn(-gam, d[k], gcur[k]);
     }
 }
 

@@ -109,3 +109,33 @@ def test_central_gradient_keeps_second_order():
     ep = np.array([e[0] for e in errs])
     ee = np.array([e[1] for e in errs])
     assert np.all(ep[:-1] / ep[1:] > 3.3) and np.all(ee[:-1] / ee[1:] > 3.3), (ep, ee)
+
+
+@pytest.mark.parametrize("K_level", [[1, 3], [4, 1, 2], [2, 6, 1]])
+def test_per_level_sweep_counts_keep_the_fixed_point(K_level):
+    """Reading R23: the smoothing counts per level (K_level[j] on the level j
+    below the finest, Alg. 4's K elsewhere) change the iteration, not its fixed
+    point."""
+    n, kind = 16, "mixed"
+    o, _ = setup(n, kind)
+    g_direct, _ = dense_solution(o, n)
+    o.close()
+    o, _ = setup(n, kind, K_level=K_level)
+    res, g = cycles_to_converge(o, n)
+    o.close()
+    assert res[-1] < 1e-14
+    assert np.abs(g - g_direct).max() < 1e-10 * max(np.abs(g_direct).max(), 1.0)
+
+
+def test_per_level_sweep_counts_change_the_contraction():
+    """More sweeps on the finest level contract the residual faster per cycle;
+    K_level = [K] * L is Alg. 4 with K itself (bitwise)."""
+    n, kind = 16, "roller"
+    out = {}
+    for name, extra in (("K2", {}), ("same", {"K_level": [2, 2, 2]}), ("fine6", {"K_level": [6]})):
+        o, _ = setup(n, kind, **extra)
+        o.set_g(np.zeros((n, n, 8)))
+        out[name] = [o.vcycle(reset_history=(k == 0)) for k in range(6)]
+        o.close()
+    assert out["K2"] == out["same"]
+    assert out["fine6"][-1] < out["K2"][-1]
