@@ -17,6 +17,7 @@
 #include <chrono>
 #include <condition_variable>
 #include <deque>
+#include <functional>
 #include <map>
 #include <memory>
 #include <mutex>
@@ -1795,6 +1796,7 @@ struct BatchLaunch {
     int tkind, variant;
     size_t job_off, item_off;  // offsets into slots[tkind] and into the work items
     int njobs, nitems;
+    int group;                 // the depth group whose branch of the step graph launches it
 };
 
 // A job of the schedule: which instance's which recorded sweep fills it.
@@ -1822,6 +1824,14 @@ struct biot_batch_s {
     SweepItem *flow_items_dev[2] = {};
     long launches_per_step = 0, kernel_launches = 0, nstep = 0;
     std::vector<void *> allocs;
+    // instances of equal depth (multigrid levels) form a group; the groups' phase
+    // launches are independent chains, captured as parallel branches of the step
+    // graph on streams of their own
+    int ngroups = 1;
+    std::vector<int> group_of;
+    std::vector<cudaStream_t> branch;
+    cudaEvent_t ev_fork = nullptr;
+    std::vector<cudaEvent_t> ev_join;
 };
 
 namespace {
@@ -1846,25 +1856,38 @@ int batch_plan(biot_batch_s *b)
 {
     const int n = (int)b->inst.size();
     std::vector<std::vector<PlanOp>> ops(n);
-    int maxkey = 0;
-    const int up = b->Dmax * (b->K + 1) + 2 * b->K + b->Dmax * b->K;
+    // depth groups: instances with the same number of levels
+    std::vector<int> depths;
+    for (biot_ctx *h : b->inst)
+        if (std::find(depths.begin(), depths.end(), h->L) == depths.end()) depths.push_back(h->L);
+    std::sort(depths.begin(), depths.end(), std::greater<int>());  // deepest (usually largest) first
+    b->ngroups = (int)depths.size();
+    b->group_of.assign(n, 0);
+    for (int i = 0; i < n; i++)
+        b->group_of[i] = (int)(std::find(depths.begin(), depths.end(), b->inst[i]->L) - depths.begin());
     b->nops.assign(n, 0);
+    std::vector<int> maxkey(b->ngroups, 0);
     for (int i = 0; i < n; i++) {
+        const int Dg = b->inst[i]->L - 1;  // the group's depth: its own coarsest level aligns its V-cycles
+        const int up = Dg * (b->K + 1) + 2 * b->K + Dg * b->K;
         std::vector<PlanOp> cyc;
-        plan_vcycle(b->inst[i], b->inst[i]->L - 1, b->K, b->Dmax, cyc);
+        plan_vcycle(b->inst[i], b->inst[i]->L - 1, b->K, Dg, cyc);
         for (int c = 0; c < b->ne; c++)
             for (const PlanOp &o : cyc) ops[i].push_back({o.level, o.mode, c * up + o.key});
         b->nops[i] = ops[i].size();
-        for (const PlanOp &o : ops[i]) maxkey = o.key > maxkey ? o.key : maxkey;
+        int &mk = maxkey[b->group_of[i]];
+        for (const PlanOp &o : ops[i]) mk = o.key > mk ? o.key : mk;
     }
-    // bucket the ops by key, then by (tkind, variant)
-    std::vector<std::vector<BatchSlot>> bykey(maxkey + 1);
-    for (int i = 0; i < n; i++)
-        for (size_t j = 0; j < ops[i].size(); j++) bykey[ops[i][j].key].push_back({i, (int)j});
     b->launches.clear();
     b->items.clear();
     for (int t = 0; t < 3; t++) b->slots[t].clear();
-    for (int key = 0; key <= maxkey; key++) {
+    for (int g = 0; g < b->ngroups; g++) {
+    // bucket the group's ops by key, then by (tkind, variant)
+    std::vector<std::vector<BatchSlot>> bykey(maxkey[g] + 1);
+    for (int i = 0; i < n; i++)
+        if (b->group_of[i] == g)
+            for (size_t j = 0; j < ops[i].size(); j++) bykey[ops[i][j].key].push_back({i, (int)j});
+    for (int key = 0; key <= maxkey[g]; key++) {
         for (int tk = 0; tk < 3; tk++) {
             for (int v = 0; v < 128; v++) {  // every combination of the SWEEP_V_* flags
                 std::vector<BatchSlot> grp;
@@ -1878,7 +1901,7 @@ int batch_plan(biot_batch_s *b)
                 const bool tile = (v & SWEEP_V_TILE) != 0;
                 const int slots = tile ? 1 : tkind_slots(tk, v & ~SWEEP_V_TILE);
                 if (!slots) return fail(BIOT_ERR_CUDA, "occupancy query of the batched sweep kernel failed");
-                BatchLaunch L{tk, v, b->slots[tk].size(), b->items.size(), (int)grp.size(), 0};
+                BatchLaunch L{tk, v, b->slots[tk].size(), b->items.size(), (int)grp.size(), 0, g};
                 std::vector<int> tys;
                 if (!tile) {
                     std::vector<std::pair<int, int>> dims;
@@ -1909,6 +1932,17 @@ int batch_plan(biot_batch_s *b)
             }
         }
     }
+    }
+    // the branch streams and the fork / join events of the step graph
+    while ((int)b->branch.size() < b->ngroups) {
+        cudaStream_t st;
+        CUDA_TRY(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+        b->branch.push_back(st);
+        cudaEvent_t ev;
+        CUDA_TRY(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        b->ev_join.push_back(ev);
+    }
+    if (!b->ev_fork) CUDA_TRY(cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming));
     // flow steps: one job per instance
     for (int t = 0; t < 2; t++) {
         b->flow_inst[t].clear();
@@ -1939,7 +1973,8 @@ int batch_plan(biot_batch_s *b)
 // each with its parameter block: the recorded arguments of its sweeps and the
 // geometry of their work items (job-major, row by row, as batch_plan lays them out).
 template <typename T, typename TC>
-cudaError_t batch_launch_typed(biot_batch_s *b, const BatchLaunch &L, std::vector<std::vector<SweepJob>> &rec)
+cudaError_t batch_launch_typed(biot_batch_s *b, const BatchLaunch &L, std::vector<std::vector<SweepJob>> &rec,
+                               cudaStream_t stream)
 {
     std::unique_ptr<BatchParams<T, TC>> P(new (std::nothrow) BatchParams<T, TC>());
     if (!P) return cudaErrorMemoryAllocation;
@@ -1962,7 +1997,7 @@ cudaError_t batch_launch_typed(biot_batch_s *b, const BatchLaunch &L, std::vecto
             }
         }
         P->start[nj] = count;
-        cudaError_t e = launch_sweep_batch<T, TC>(L.variant, *P, b->stream);
+        cudaError_t e = launch_sweep_batch<T, TC>(L.variant, *P, stream);
         if (e != cudaSuccess) return e;
     }
     return it == it_end ? cudaSuccess : cudaErrorInvalidValue;
@@ -2021,13 +2056,28 @@ int batch_capture(biot_batch_s *b, int par)
         if (e != cudaSuccess) rc = fail(BIOT_ERR_CUDA, std::string("batched flow launch: ") + cudaGetErrorString(e));
         nl++;
     }
+    // the groups' phase launches as parallel branches (one group: on the main stream)
+    const bool fork = b->ngroups > 1;
+    if (!rc && fork) {
+        cudaError_t e = cudaEventRecord(b->ev_fork, b->stream);
+        for (int g = 0; g < b->ngroups && e == cudaSuccess; g++) e = cudaStreamWaitEvent(b->branch[g], b->ev_fork, 0);
+        if (e != cudaSuccess) rc = fail(BIOT_ERR_CUDA, std::string("batched graph fork: ") + cudaGetErrorString(e));
+    }
     for (size_t k = 0; k < b->launches.size() && !rc; k++) {
         const BatchLaunch &L = b->launches[k];
-        cudaError_t e = L.tkind == 0 ? batch_launch_typed<double, double>(b, L, rec)
-                      : L.tkind == 1 ? batch_launch_typed<float, double>(b, L, rec)
-                                     : batch_launch_typed<float, float>(b, L, rec);
+        const cudaStream_t st = fork ? b->branch[L.group] : b->stream;
+        cudaError_t e = L.tkind == 0 ? batch_launch_typed<double, double>(b, L, rec, st)
+                      : L.tkind == 1 ? batch_launch_typed<float, double>(b, L, rec, st)
+                                     : batch_launch_typed<float, float>(b, L, rec, st);
         if (e != cudaSuccess) rc = fail(BIOT_ERR_CUDA, std::string("batched sweep launch: ") + cudaGetErrorString(e));
         nl++;
+    }
+    if (fork) {  // join every branch, also after an error, so that the capture can end
+        for (int g = 0; g < b->ngroups; g++) {
+            cudaError_t e = cudaEventRecord(b->ev_join[g], b->branch[g]);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, b->ev_join[g], 0);
+            if (!rc && e != cudaSuccess) rc = fail(BIOT_ERR_CUDA, std::string("batched graph join: ") + cudaGetErrorString(e));
+        }
     }
     for (int i = 0; i < n && !rc; i++) {
         biot_ctx *h = b->inst[i];
@@ -2073,6 +2123,12 @@ void batch_release(biot_batch_s *b)
 {
     if (!b) return;
     if (b->stream) cudaStreamSynchronize(b->stream);
+    for (cudaStream_t st : b->branch) {
+        cudaStreamSynchronize(st);
+        cudaStreamDestroy(st);
+    }
+    for (cudaEvent_t ev : b->ev_join) cudaEventDestroy(ev);
+    if (b->ev_fork) cudaEventDestroy(b->ev_fork);
     for (int i = 0; i < 2; i++)
         if (b->graph[i]) cudaGraphExecDestroy(b->graph[i]);
     for (void *p : b->allocs) cudaFree(p);
