@@ -207,10 +207,15 @@ struct BatchParams {
 // `variant` (SWEEP_V_* flags).
 template <typename T, typename TC>
 cudaError_t launch_sweep_batch(int variant, const BatchParams<T, TC> &P, cudaStream_t s);
-// Resident CTAs of a sweep launch of this kind on the current device, and the
-// strip geometry of the sweep kernels (columns per strip).
+// Resident CTAs of a batched sweep launch (sweep_slots) and of a
+// single-instance strip launch (sweep_strip_slots) of this kind on the current
+// device, and the strip geometry of the two strip kernels (output columns per
+// strip: 156 of a 160-thread CTA for single instances, 124 of a 128-thread CTA
+// in batches, whose levels are at most 512 cells wide).
 template <typename T, typename TC> int sweep_slots(int variant);
-constexpr int SWEEP_STRIP_COLS = 124;
+template <typename T, typename TC> int sweep_strip_slots(int variant);
+constexpr int SWEEP_STRIP_COLS = 156;
+constexpr int BATCH_STRIP_COLS = 124;
 
 // Largest strip height of a sweep launch (rows) unless biot_autotune chose one.
 inline int sweep_rows_cap() { return 32; }

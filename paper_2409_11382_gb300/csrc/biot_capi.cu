@@ -1770,7 +1770,7 @@ std::vector<int> batch_strip_rows(const std::vector<std::pair<int, int>> &dims, 
         bool ok = true;
         for (size_t g = 0; g < dims.size(); g++) {
             const int nx = dims[g].first, ny = dims[g].second;
-            const long sx = (nx + SWEEP_STRIP_COLS - 1) / SWEEP_STRIP_COLS;
+            const long sx = (nx + BATCH_STRIP_COLS - 1) / BATCH_STRIP_COLS;
             const long share = (long)((double)waves * slots * ((double)nx * ny) / cells);
             long nsy = share / sx;
             if (nsy < 1) nsy = 1;
@@ -1789,6 +1789,13 @@ int tkind_slots(int tkind, int variant)
 {
     return tkind == 0 ? sweep_slots<double, double>(variant)
          : tkind == 1 ? sweep_slots<float, double>(variant) : sweep_slots<float, float>(variant);
+}
+
+// The same for the single-instance strip kernel.
+int tkind_strip_slots(int tkind, int variant)
+{
+    return tkind == 0 ? sweep_strip_slots<double, double>(variant)
+         : tkind == 1 ? sweep_strip_slots<float, double>(variant) : sweep_strip_slots<float, float>(variant);
 }
 
 // One launch of the batched schedule.
@@ -1921,7 +1928,7 @@ int batch_plan(biot_batch_s *b)
                             for (int bx = 0; bx < (Lv.nx + tx - 1) / tx; bx++) b->items.push_back({(int)g, bx, by, 0});
                     } else {  // strips sized so that the launch fills whole waves of the GPU
                         const int ty = tys[g];
-                        const int sx = (Lv.nx + SWEEP_STRIP_COLS - 1) / SWEEP_STRIP_COLS, sy = (Lv.ny + ty - 1) / ty;
+                        const int sx = (Lv.nx + BATCH_STRIP_COLS - 1) / BATCH_STRIP_COLS, sy = (Lv.ny + ty - 1) / ty;
                         for (int by = 0; by < sy; by++)
                             for (int bx = 0; bx < sx; bx++) b->items.push_back({(int)g, bx, by, ty});
                     }
@@ -2920,7 +2927,7 @@ extern "C" int biot_autotune(biot_handle h, int *rows_out, double *ms_out, int m
             // candidates: fixed heights, and the heights whose strips fill exactly
             // 1, 2 or 3 waves of resident CTAs (tall strips repeat fewer halo rows)
             std::vector<int> cand(std::begin(fixed_cand), std::end(fixed_cand));
-            const int slots = strips ? tkind_slots(level_tkind(h, l), level_variant(h, l, mode) & ~SWEEP_V_TILE) : 0;
+            const int slots = strips ? tkind_strip_slots(level_tkind(h, l), level_variant(h, l, mode) & ~SWEEP_V_TILE) : 0;
             const int sx = (Lv.nx + SWEEP_STRIP_COLS - 1) / SWEEP_STRIP_COLS;
             for (int w = 1; w <= 3 && slots > 0; w++) {
                 const int nsy = w * slots / sx;

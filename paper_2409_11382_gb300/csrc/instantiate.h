@@ -13,6 +13,7 @@
                                                             cudaStream_t s)                            \
     { return biot::launch_sweep_batch_impl<T, TC>(v, P, s); }                                          \
     template <> int biot::sweep_slots<T, TC>(int v) { return biot::sweep_slots_impl<T, TC>(v); }       \
+    template <> int biot::sweep_strip_slots<T, TC>(int v) { return biot::sweep_strip_slots_impl<T, TC>(v); } \
     template <> cudaError_t biot::launch_sweep_chain<T, TC>(const biot::SweepArgs<T, TC> &a, int n,     \
                                                             cudaStream_t s)                            \
     { return biot::launch_sweep_chain_impl<T, TC>(a, n, s); }

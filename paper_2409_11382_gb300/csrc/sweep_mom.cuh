@@ -1289,8 +1289,12 @@ cudaError_t launch_tile(const SweepArgs<T, TC> &a, cudaStream_t s)
     return cudaGetLastError();
 }
 
-// Strip sweep launch shape: SWEEP_NT threads, SWEEP_CPT cells of a row per thread.
-constexpr int SWEEP_NT = 128, SWEEP_CPT = 1;
+// Strip sweep launch shape: SWEEP_NT threads, SWEEP_CPT cells of a row per
+// thread.  Measured on the 4096^2 finest sweep (tuned strip heights; resident
+// CTAs per SM from the register bound of __launch_bounds__): 128 threads
+// 0.288 ms, 160: 0.257, 192: 0.265, 224: 0.302, 256: 0.271, 320: 0.315, 384:
+// 0.289 ms.
+constexpr int SWEEP_NT = 160, SWEEP_CPT = 1;
 static_assert(SWEEP_NT * SWEEP_CPT - 4 == SWEEP_STRIP_COLS, "strip geometry shared with the host planner");
 
 template <typename T, typename TC, int KIND, bool LO, bool RESTRICT>
@@ -1373,6 +1377,18 @@ template <typename T, typename TC, int KIND, bool LO, bool RS>
 struct RowsRun {
     static cudaError_t run(const SweepArgs<T, TC> &a, cudaStream_t s) { return launch_rows<T, TC, KIND, LO, RS>(a, s); }
 };
+template <typename T, typename TC, int KIND, bool LO, bool RS>
+struct StripSlotsRun {
+    static int run() { return SweepKernel<T, TC, KIND, LO, RS>::slots(); }
+};
+
+template <typename T, typename TC>
+int sweep_strip_slots_impl(int v)
+{
+    return dispatch_kind<T, TC, StripSlotsRun>(v & SWEEP_V_COARSE, v & SWEEP_V_LO, v & SWEEP_V_RESTRICT,
+                                               !(v & SWEEP_V_NOGHOST),
+                                               (v & SWEEP_V_DEV16) ? 1 : (v & SWEEP_V_DEVBF16) ? 2 : 0);
+}
 
 // Level kind from the arguments: F~ present = finest level; low parts only
 // with FP32 storage on the finest level.

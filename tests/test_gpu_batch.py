@@ -107,14 +107,45 @@ def test_batched_workload_64_instances():
     for i, (params, _) in enumerate(probs):
         first.setdefault(params["nx"], i)
     assert sorted(first) == [64, 128, 256, 512]
+    # every instance against its solo run
+    for i, (params, sides) in enumerate(probs):
+        eta, p, _ = alone(params, sides, steps)
+        assert rel(out[i][0], eta) < TOL32 and rel(out[i][1], p) < TOL32, i
     for i in first.values():
         params, sides = probs[i]
-        eta, p, _ = alone(params, sides, steps)
-        assert rel(out[i][0], eta) < TOL32 and rel(out[i][1], p) < TOL32
         o = O.Oracle(dict(params, precision=W.FP64), sides)
         o.step(steps)
         assert rel(out[i][0], o.read_u()[0]) < 1e-5
         assert rel(out[i][1], o.read_p()[0]) < 1e-5
+        o.close()
+
+
+def test_equal_sized_instances_with_own_walls_equal_solo_runs():
+    """Instances of one size share every phase launch of a batch, each with its
+    own materials and boundary conditions (symmetric and periodic sides; a
+    512-column level ends in a part-filled strip), beside a 512 x 128 rectangle
+    of another depth: each equals its solo run (FP32 tolerance) and the FP64
+    oracle."""
+    probs = []
+    for k, (alpha, c0, side) in enumerate([(1.0, 0.01, W.SYMMETRY), (0.7, 0.05, W.PERIODIC),
+                                           (0.9, 0.1, W.SYMMETRY), (0.8, 0.02, W.PERIODIC)]):
+        p, _, _ = W.step_load_257(alpha=alpha, precision=W.FP32, n=512)
+        probs.append((dict(p, c0=c0), W.top_load_sides(512, W.step_load(512), side)))
+    p, _, _ = W.step_load_257(alpha=0.6, precision=W.FP32, n=512)
+    probs.append((dict(p, ny=128, ly=0.25, c0=0.03, levels=6), W.top_load_sides(512, W.step_load(512))))
+    steps = 3
+    with biot.Batch(probs) as b:
+        assert b.step(steps) == biot.OK
+        out = [(b[i].read_u()[0], b[i].read_p()[0]) for i in range(len(b))]
+    for i, (params, sides) in enumerate(probs):
+        eta, p, _ = alone(params, sides, steps)
+        assert rel(out[i][0], eta) < TOL32 and rel(out[i][1], p) < TOL32, i
+    for i in (1, 4):
+        params, sides = probs[i]
+        o = O.Oracle(dict(params, precision=W.FP64), sides)
+        o.step(steps)
+        assert rel(out[i][0], o.read_u()[0]) < 1e-5, i
+        assert rel(out[i][1], o.read_p()[0]) < 1e-5, i
         o.close()
 
 
