@@ -269,12 +269,14 @@ __device__ __forceinline__ void store_cell(const Rings<T, W, KIND, LO> &rg, int 
 __device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
 __device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
 // a * b + c with the rounding fixed by the source, not by the compiler's
-// contraction choices: one fused multiply-add in FP32, a rounded product and a
-// rounded sum in FP64 (the FP64 kernels fuse nothing).  The collision, pull,
-// residual and relaxation arithmetic is shared by inlined copies in different
-// kernels and loop forms; written with these, every copy rounds alike.
+// contraction choices: one fused multiply-add in either precision (the FP64
+// kernels fuse nothing else).  The collision, pull, residual and relaxation
+// arithmetic is shared by inlined copies in different kernels and loop forms;
+// written with these, every copy rounds alike.  In FP64 the fused form also
+// halves the FP64 instructions of these terms, and FP64 issue is what bounds
+// the FP64 sweeps on this GPU.
 __device__ __forceinline__ float mad_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
-__device__ __forceinline__ double mad_rn(double a, double b, double c) { return __dadd_rn(__dmul_rn(a, b), c); }
+__device__ __forceinline__ double mad_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
 
 // a_p . (x, y) / 2 for the odd coefficient vectors a_p of Tab. moments:inverse,
 // zero terms omitted.
