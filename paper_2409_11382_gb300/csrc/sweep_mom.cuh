@@ -896,7 +896,10 @@ __device__ __forceinline__ void sweep_strip(const SweepArgs<T, TC> &a, int bx, i
 // m_01 of three rows.  Shared-memory traffic per cell drops from 34 loads and
 // 13 stores (six of them 128-bit) to 22 loads and 9 stores, all 32-bit.  The
 // arithmetic is that of the ring form (collide_math, pval_from, pair_from,
-// residual_core), so both forms round identically.
+// residual_core), so both forms round identically.  A row's global loads are
+// issued two rows before its values are used, so that a whole row of work
+// (two barriers, a collision and a residual) and more lies between a load and
+// its first use.
 // ---------------------------------------------------------------------------
 constexpr int REG_POST_PLANES = 8;  // G_0, G_2, G_4, G_5, G_6, G_7, m_10, m_01
 __host__ __device__ constexpr int reg_post_plane(int k) { return k == 0 ? 0 : k == 2 ? 1 : k - 2; }
@@ -929,8 +932,11 @@ __device__ __forceinline__ void sweep_strip_reg(const SweepArgs<T, TC> &a, int b
     const bool collides = t >= 1 && t < W - 1;
     const bool writes = t >= 2 && t < W - 2;
 
-    T pv[RV], A[RV], B[RV], C[RV];  // fetched row; raw values of rows y, y+1, y+2
+    // fetched rows (pv the next, pv2 the one after: global loads are issued two
+    // rows ahead of their use); raw values of rows y, y+1, y+2
+    T pv[RV], pv2[RV], A[RV], B[RV], C[RV];
     auto fetch = [&](int yy) { fetch_cell<T, TC, KIND, LO, RV, FM, true>(a, x, yy, NP, false, false, pv); };
+    auto fetch2 = [&](int yy) { fetch_cell<T, TC, KIND, LO, RV, FM, true>(a, x, yy, NP, false, false, pv2); };
     auto extras = [&](const T (&v)[RV], T (&e)[NE]) {
 #pragma unroll
         for (int i = 0; i < NE; i++) e[i] = v[XV + i];
@@ -977,6 +983,7 @@ __device__ __forceinline__ void sweep_strip_reg(const SweepArgs<T, TC> &a, int b
     for (int i = 0; i < RV; i++) C[i] = pv[i];  // row y0+1
     MSR(0, t) = pv[3];
     fetch(y0 + 2);
+    fetch2(y0 + 3);  // y0 + 3 <= y1 + 1: inside the window
     __syncthreads();
     if (collides) collide(B, A[3], C[3], 1, 2, 0, g1c, g3n, myc);  // row y0
     __syncthreads();
@@ -999,7 +1006,9 @@ __device__ __forceinline__ void sweep_strip_reg(const SweepArgs<T, TC> &a, int b
 #pragma unroll
         for (int i = 0; i < RV; i++) C[i] = pv[i];  // (A) row y+2
         MSR(sa, t) = C[3];
-        fetch(y + 3);
+#pragma unroll
+        for (int i = 0; i < RV; i++) pv[i] = pv2[i];  // row y+3
+        if (y + 3 <= y1) fetch2(y + 4);  // row y+4 is the C of iteration y+2 (the last uses row y1+1)
         __syncthreads();  // (C)
         if (collides) collide(B, A[3], C[3], sb, sc, sa, g1n, g3n, myn);  // row y+1
         __syncthreads();  // (E)
