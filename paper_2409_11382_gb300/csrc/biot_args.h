@@ -132,6 +132,7 @@ struct FlowFusedArgs {
     double dt, a_over_h, r, kD, c0, c0h2;
     T k_om, k_src, k_m3w, k_mah;  // omega, 1 - omega/2, -3 omega, -alpha h
     T k_a1r, k_ar;                // (alpha/h)(1 - r), (alpha/h) r
+    T k_c2;                       // (alpha/h) r kD, evaluated in FP64 on the host and rounded
 };
 
 // Physical fields of the current state.

@@ -935,6 +935,7 @@ int flow_typed(biot_ctx *h)
     a.k_mah = T(-(h->P.alpha * h->h));
     a.k_a1r = T(a.a_over_h * (1.0 - a.r));
     a.k_ar = T(a.a_over_h * a.r);
+    a.k_c2 = T(a.a_over_h * a.r * a.kD);
     if (h->frec) {  // batched step: the batch launches it with the others
         FlowRec r{};
         r.fp64 = sizeof(T) == 8;

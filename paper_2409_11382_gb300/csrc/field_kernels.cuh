@@ -297,8 +297,12 @@ __device__ __forceinline__ void flow_tile(const FlowFusedArgs<T> &a, int bx, int
     grad(qs0, g0x, g0y);
     grad(qA, gAx, gAy);
     grad(qms, gmx, gmy);
-    // grad s'_exp = grad s0 - (alpha/h) [(1-r) grad A - r kD grad m_s]
-    const T c1 = T(a.a_over_h * (1.0 - a.r)), c2 = T(a.a_over_h * a.r * a.kD);
+    // grad s'_exp = grad s0 - (alpha/h) [(1-r) grad A - r kD grad m_s]; the two
+    // coefficients come from the host (FP64 products rounded to T), so the
+    // kernel's FP64 work is the divergence history alone (GB300 issues FP64 at
+    // 1/64 of the FP32 rate, and per-thread FP64 coefficients made this kernel
+    // FP64-bound)
+    const T c1 = a.k_a1r, c2 = a.k_c2;
     const T gx_ = (g0x - c1 * gAx) + c2 * gmx;
     const T gy_ = (g0y - c1 * gAy) + c2 * gmy;
     T fx = a.k_mah * (a.k_m3w * jx + T(0.5) * gx_);
