@@ -545,7 +545,7 @@ __device__ __forceinline__ void store_history(const SweepArgs<T, TC> &a, const R
                                               int s0, int c0, T tx, T ty, T tlx, T tly)
 {
     const PVal<T> o = post_at<T, LO, W, KIND, K>(rg, s0, c0, tx, ty, tlx, tly);
-    a.H[side][3 * pos + hslot(side, K)] = (o.g + o.h) + (o.bx * (tx + tlx) + o.by * (ty + tly));
+    a.H[side][3 * pos + hslot(side, K)] = (o.g + o.h) + (mul_rn(o.bx, tx + tlx) + mul_rn(o.by, ty + tly));
 }
 
 // The streamed cell's own values, from its raw ring slot: the iterate's moments
@@ -651,14 +651,17 @@ __device__ __forceinline__ void residual_cell(const SweepArgs<T, TC> &a, const R
     const T mxf = tx + tlx, myf = ty + tly;
     constexpr bool GH = kind_ghosts(KIND);
     if (WALL) {
-        d[0] -= ((P0.dbx + P2.dbx) - P3.dbx) * mxf + ((P0.dby + P2.dby) - P3.dby) * myf;
-        d[1] -= ((P1.dbx + P2.dbx) + P3.dbx) * mxf + ((P1.dby + P2.dby) + P3.dby) * myf;
-        d[5] -= (P2.dbx - P3.dbx) * mxf + (P2.dby - P3.dby) * myf;
-        d[6] -= (P2.dbx + P3.dbx) * mxf + (P2.dby + P3.dby) * myf;
-        d[2] -= (P2.bsx - P3.bsx) * mxf + (P2.bsy - P3.bsy) * myf;
-        d[3] -= ((P0.bsx + P1.bsx) + T(2) * (P2.bsx + P3.bsx)) * mxf + ((P0.bsy + P1.bsy) + T(2) * (P2.bsy + P3.bsy)) * myf;
-        d[4] -= (P0.bsx - P1.bsx) * mxf + (P0.bsy - P1.bsy) * myf;
-        d[7] -= (P2.bsx + P3.bsx) * mxf + (P2.bsy + P3.bsy) * myf;
+        // beta terms of the wall pulls; products rounded on their own (mul_rn), so
+        // that no contraction choice of the compiler makes kernel forms differ
+        d[0] -= mul_rn((P0.dbx + P2.dbx) - P3.dbx, mxf) + mul_rn((P0.dby + P2.dby) - P3.dby, myf);
+        d[1] -= mul_rn((P1.dbx + P2.dbx) + P3.dbx, mxf) + mul_rn((P1.dby + P2.dby) + P3.dby, myf);
+        d[5] -= mul_rn(P2.dbx - P3.dbx, mxf) + mul_rn(P2.dby - P3.dby, myf);
+        d[6] -= mul_rn(P2.dbx + P3.dbx, mxf) + mul_rn(P2.dby + P3.dby, myf);
+        d[2] -= mul_rn(P2.bsx - P3.bsx, mxf) + mul_rn(P2.bsy - P3.bsy, myf);
+        d[3] -= mul_rn((P0.bsx + P1.bsx) + T(2) * (P2.bsx + P3.bsx), mxf) +
+                mul_rn((P0.bsy + P1.bsy) + T(2) * (P2.bsy + P3.bsy), myf);
+        d[4] -= mul_rn(P0.bsx - P1.bsx, mxf) + mul_rn(P0.bsy - P1.bsy, myf);
+        d[7] -= mul_rn(P2.bsx + P3.bsx, mxf) + mul_rn(P2.bsy + P3.bsy, myf);
         // history of the fullway bounce-back: this call's outgoing populations
 #define BIOT_HIST(SIDE, POS, K) store_history<T, TC, LO, W, KIND, K>(a, rg, SIDE, POS, s0, c0, tx, ty, tlx, tly)
         if (y == 0 && a.bc[SIDE_BOTTOM] == BC_DIRICHLET) { BIOT_HIST(SIDE_BOTTOM, x, 3); BIOT_HIST(SIDE_BOTTOM, x, 6); BIOT_HIST(SIDE_BOTTOM, x, 7); }
