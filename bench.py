@@ -133,7 +133,7 @@ def step_model(params, n, fp64, dev=False):
     return cell_sweeps, nbytes
 
 
-OPT_COARSEST_STORAGE, OPT_COLD_FP64, OPT_COLD_FP32 = 1, 2, 4  # biot_params.options flags of include/biot.h
+OPT_COARSEST_STORAGE, OPT_COLD_FP64, OPT_COLD_FP32, OPT_SEGMENTS = 1, 2, 4, 32  # biot_params.options flags of include/biot.h
 
 
 def coarsest_fp64(params):
@@ -388,6 +388,8 @@ def run_ours(args):
         params = dict(params, options=int(params.get("options", 0)) | OPT_COARSEST_STORAGE)
     if args.cold != "auto":
         params = dict(params, options=int(params.get("options", 0)) | (OPT_COLD_FP64 if args.cold == "fp64" else OPT_COLD_FP32))
+    if args.segments:
+        params = dict(params, options=int(params.get("options", 0)) | OPT_SEGMENTS)
     nx, ny = params["nx"], params["ny"]
     cells = nx * ny
     stream = torch.cuda.current_stream()
@@ -515,6 +517,7 @@ def run_ours(args):
                    "precision": precision_label(params, fp64),
                    "l2": f"state ({st['device_bytes'] / 1e9:.1f} GB) larger than L2; no flush needed",
                    "parallelism": f"replicas{world}",
+                   "coarse_sweeps": "cluster segments" if args.segments else "separate graph-launched kernels",
                    "autotuned_strip_rows": tuned},
         "roofline": roofline,
         "cpu_baseline": cpu_base,
@@ -601,6 +604,8 @@ def run_batched(args):
     probs = W.batched_instances(count=args.instances, seed=2409 + 7919 * rank)
     if args.precision in DEV_PRECISIONS:
         probs = [(dict(p, precision=DEV_PRECISIONS[args.precision]), s) for p, s in probs]
+    if args.segments:
+        probs = [(dict(p, options=int(p.get("options", 0)) | OPT_SEGMENTS), s) for p, s in probs]
     cells = sum(p["nx"] * p["ny"] for p, _ in probs)
     b = biot.Batch(probs)
     b.step(args.warmup)
@@ -679,7 +684,9 @@ def run_batched(args):
             "config": {"workload": "batched_64_instances_64-512_fp32", "instances": len(probs),
                        "cells_total": cells, "ne_fixed": 3, "K": 4,
                        "l2": "state of all instances larger than L2; no flush needed",
-                       "parallelism": f"replicas{world}"},
+                       "parallelism": f"replicas{world}",
+                       "coarse_sweeps": "cluster segments" if args.segments else "separate graph-launched kernels",
+                       "launches_per_step": st["launches_per_step"]},
             "e2e": {"value": cells * e2e_steps / e2e / 1e6, "unit": "MLUPS",
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h // e2e_steps,
                     "finite": e2e_finite},
@@ -805,6 +812,8 @@ def main():
                     help="single, FP32 path: precision of the coarsest multigrid level")
     ap.add_argument("--cold", choices=["auto", "fp64", "fp32"], default="auto",
                     help="single, FP32 path: the solve at t = 0 on an FP64 copy (auto: from 2048^2 cells)")
+    ap.add_argument("--segments", action="store_true",
+                    help="the sweeps of the small coarse levels as cluster segments (BIOT_OPT_SEGMENTS)")
     ap.add_argument("--requests", type=int, default=200, help="served: number of requests")
     ap.add_argument("--mean-service", type=float, default=0.05, help="served: assumed mean service time (s)")
     ap.add_argument("--budget-gb", type=float, default=16.0, help="served: device-memory budget")

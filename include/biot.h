@@ -81,7 +81,7 @@ extern "C" {
  * 0 selects the defaults described at BIOT_FP32.  They change rounding only:
  * the scheme, its iteration counts and its fixed point are the same.
  * BIOT_OPT_COLD_FP64 / _COLD_FP32 and BIOT_OPT_COARSE_LO_ALL / _OFF exclude
- * each other; the options are ignored by BIOT_FP64. */
+ * each other; BIOT_FP64 ignores all but BIOT_OPT_SEGMENTS. */
 #define BIOT_OPT_COARSEST_STORAGE 1   /* the coarsest level in FP32 like the other coarse
                                          levels (faster on small instances) */
 #define BIOT_OPT_COLD_FP64        2   /* the solve at t = 0 on an FP64 copy on every grid */
@@ -89,6 +89,14 @@ extern "C" {
 #define BIOT_OPT_COARSE_LO_ALL    8   /* double-float first moments on the FP32 coarse levels
                                          in every solve (default: in an FP32 solve at t = 0) */
 #define BIOT_OPT_COARSE_LO_OFF   16   /* ... in no solve */
+#define BIOT_OPT_SEGMENTS        32   /* a launch choice, honoured in every precision: the
+                                         sweeps of the small coarse levels of a V-cycle (at most 16
+                                         tiles each) as one thread-block-cluster launch per run of
+                                         sweeps of one storage type (one cluster per instance in a
+                                         batch) instead of one graph-launched kernel per sweep.
+                                         Results are bitwise the same; on GB300 it is measured
+                                         slower (graph launches cost about what the cluster
+                                         barriers cost), so it is off by default */
 
 /* ---- boundary condition types (§3.6) --------------------------------------- */
 #define BIOT_PERIODIC  0  /* wrap-around streaming; must be set on both opposite sides

@@ -22,6 +22,7 @@ FP64, FP32, FP32_COARSE64, FP32_DEV16, FP32_DEVBF16 = 0, 1, 2, 3, 4
 CYCLE_V, CYCLE_W, CYCLE_F = 0, 1, 2
 # biot_params.options (include/biot.h)
 OPT_COARSEST_STORAGE, OPT_COLD_FP64, OPT_COLD_FP32, OPT_COARSE_LO_ALL, OPT_COARSE_LO_OFF = 1, 2, 4, 8, 16
+OPT_SEGMENTS = 32
 PERIODIC, SYMMETRY, DIRICHLET, NEUMANN = 0, 1, 2, 3
 BOTTOM, RIGHT, TOP, LEFT = 0, 1, 2, 3
 

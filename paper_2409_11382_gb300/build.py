@@ -30,6 +30,7 @@ UNITS = {
     "kernels_fp64.cu": ["--fmad=false"],
     "kernels_fp32.cu": [],
     "kernels_fp32c.cu": [],
+    "kernels_seg32.cu": [],
 }
 
 

@@ -76,7 +76,7 @@ struct SweepItem {
 
 // Storage kind of a sweep launch (bit flags).
 enum { SWEEP_V_COARSE = 1, SWEEP_V_LO = 2, SWEEP_V_RESTRICT = 4, SWEEP_V_NOGHOST = 8, SWEEP_V_TILE = 16,
-       SWEEP_V_DEV16 = 32, SWEEP_V_DEVBF16 = 64 };
+       SWEEP_V_DEV16 = 32, SWEEP_V_DEVBF16 = 64, SWEEP_V_SEGMENT = 128 };
 // Tile sweeps: levels of at most SWEEP_TILE_CELLS cells (single instance); tile
 // shape per storage type.  The fused flow step works on FLOW_TILE_X x FLOW_TILE_Y tiles.
 constexpr long SWEEP_TILE_CELLS = 256L * 256L;
@@ -208,6 +208,64 @@ struct BatchParams {
 // `variant` (SWEEP_V_* flags).
 template <typename T, typename TC>
 cudaError_t launch_sweep_batch(int variant, const BatchParams<T, TC> &P, cudaStream_t s);
+// Segment of a V-cycle: consecutive sweeps of small coarse levels of one
+// storage family (T = float: levels of tkind float/float and float/double;
+// T = double: double/double) run by one thread-block cluster in one launch, a
+// cluster barrier between the sweeps.  A program is the sweeps of one
+// instance's segment; one launch runs one program per cluster (one cluster per
+// instance of a batch).  Each level of a program has one record: its sweep
+// arguments with the parts that change from sweep to sweep (iterate buffers,
+// prolongation source, restriction target, flags) taken from the sweep's job
+// word.  Everything is a kernel parameter, so a launch captured in a graph
+// needs no device table.
+struct SegLevel {
+    union {
+        SweepArgs<double, double> dd;
+        SweepArgs<float, double> fd;
+        SweepArgs<float, float> ff;
+    } a;                  // base arguments; g, gout, gc, rc, zero_init, hist_valid, mode set per sweep
+    const void *buf[2];   // the level's two iterate buffers
+    const void *cbuf[2];  // the next coarser level's two iterate buffers (prolongation source)
+    void *crc;            // the next coarser level's residual right-hand side (restriction target)
+    int tkind;            // 0: double/double, 1: float/double, 2: float/float
+    int pad;
+};
+// Job word of one sweep: bits 0-3 the level record (relative to the program's
+// first), bit 4 restriction, bit 5 the parity of the input buffer, bit 6 zero
+// iterate, bit 7 prolongation (add the coarser level's buffer cbuf[bit 8]), bit 9
+// history valid.
+enum { SEGJ_LEVEL = 15, SEGJ_RESTRICT = 16, SEGJ_CUR = 32, SEGJ_ZERO = 64, SEGJ_PROL = 128, SEGJ_CCUR = 256,
+       SEGJ_HIST = 512 };
+// The arguments of job word w from its level record: the host builds the
+// words with this function's inverse and checks that it reproduces every sweep.
+template <typename T, typename TC>
+__host__ __device__ inline void seg_patch(SweepArgs<T, TC> &a, const SegLevel &L, unsigned w)
+{
+    const int cur = (w & SEGJ_CUR) ? 1 : 0;
+    const bool rs = (w & SEGJ_RESTRICT) != 0;
+    a.g = static_cast<const T *>(L.buf[cur]);
+    a.gout = rs ? nullptr : const_cast<T *>(static_cast<const T *>(L.buf[1 - cur]));
+    a.gc = (w & SEGJ_PROL) ? static_cast<const TC *>(L.cbuf[(w & SEGJ_CCUR) ? 1 : 0]) : nullptr;
+    a.rc = rs ? static_cast<TC *>(L.crc) : nullptr;
+    a.zero_init = (w & SEGJ_ZERO) ? 1 : 0;
+    a.hist_valid = (w & SEGJ_HIST) ? 1 : 0;
+    a.mode = rs ? SWEEP_RESTRICT : SWEEP_SMOOTH;
+}
+constexpr int SEG_MAX_PROGS = 32, SEG_MAX_LEVELS = 60, SEG_MAX_JOBS = 1200;
+constexpr int SEG_CLUSTER = 8;    // CTAs per cluster (the portable maximum)
+constexpr int SEG_MAX_TILES = 2 * SEG_CLUSTER;  // tiles of a level in a segment: at most 2 per CTA
+struct SegParams {
+    int nprog;
+    int ghosts;                   // 1: the ghost moments are loaded and stored (tolerance mode)
+    int lev0[SEG_MAX_PROGS + 1];  // program p: level records lev0[p] .. lev0[p+1]-1
+    int job0[SEG_MAX_PROGS + 1];  // program p: jobs job0[p] .. job0[p+1]-1
+    SegLevel lev[SEG_MAX_LEVELS];
+    unsigned job[SEG_MAX_JOBS];
+};
+// One launch of P.nprog clusters of cs CTAs (1 <= cs <= SEG_CLUSTER); T selects
+// the storage family of every job.
+template <typename T>
+cudaError_t launch_sweep_segment(const SegParams &P, int cs, cudaStream_t s);
 // Resident CTAs of a batched sweep launch (sweep_slots) and of a
 // single-instance strip launch (sweep_strip_slots) of this kind on the current
 // device, and the strip geometry of the two strip kernels (output columns per

@@ -40,6 +40,15 @@ struct SweepJob {
     SweepArgs<double, double> dd;
     SweepArgs<float, double> fd;
     SweepArgs<float, float> ff;
+    int seg = -1;  // SWEEP_V_SEGMENT: index of its program among the instance's recorded ones
+};
+// The program of one segment of a V-cycle (sweep_segment.cuh): the records of
+// its levels and one job word per sweep.
+struct SegProg {
+    int fam = 1;  // storage family: 0 double (tkind 0), 1 float (tkinds 1 and 2)
+    int cs = 1;   // CTAs per cluster: the most tiles of any of its levels, at most SEG_CLUSTER
+    std::vector<SegLevel> lev;
+    std::vector<unsigned> job;
 };
 // A flow step prepared for a batched launch.
 struct FlowRec {
@@ -249,6 +258,8 @@ struct biot_ctx {
     // record mode (batched execution): sweeps are appended here instead of launched
     std::vector<biot::SweepJob> *rec = nullptr;
     std::vector<biot::FlowRec> *frec = nullptr;  // record mode: flow steps appended here
+    std::vector<biot::SegProg> *segrec = nullptr;  // record mode: programs of the recorded segments
+    bool in_seg = false;  // recording the sweeps of a segment (seg_vcycle)
     // Allocation source of a server's instance: the server's stream-ordered
     // pool, so that freeing the instance synchronises only its own stream
     // (cudaFree would wait for every resident instance); its two pinned host
@@ -317,7 +328,7 @@ int check_params(const biot_params *p, const biot_side *s)
     if ((p->precision == BIOT_FP32_DEV16 || p->precision == BIOT_FP32_DEVBF16) && p->ne_fixed <= 0)
         return fail(BIOT_ERR_INVALID_ARG, "the 16-bit deviation store needs a fixed number of V-cycles (ne_fixed > 0)");
     constexpr int known = BIOT_OPT_COARSEST_STORAGE | BIOT_OPT_COLD_FP64 | BIOT_OPT_COLD_FP32 |
-                          BIOT_OPT_COARSE_LO_ALL | BIOT_OPT_COARSE_LO_OFF;
+                          BIOT_OPT_COARSE_LO_ALL | BIOT_OPT_COARSE_LO_OFF | BIOT_OPT_SEGMENTS;
     if (p->options & ~known) return fail(BIOT_ERR_INVALID_ARG, "unknown option flag");
     if (p->cycle < BIOT_CYCLE_V || p->cycle > BIOT_CYCLE_F) return fail(BIOT_ERR_INVALID_ARG, "unknown cycle");
     if (p->fmg != 0 && p->fmg != 1) return fail(BIOT_ERR_INVALID_ARG, "fmg must be 0 or 1");
@@ -533,6 +544,203 @@ int sweep(biot_ctx *h, int l, int mode, bool zero_init, bool prolong, bool want_
     return sweep_typed<float, float>(h, l, mode, zero_init, prolong, want_res, chain);
 }
 
+// ---------------------------------------------------------------------------
+// Segments (BIOT_OPT_SEGMENTS).  The sweeps of the small coarse levels of a
+// V-cycle -- every level from the segment's start level down to the coarsest,
+// each of at most SEG_MAX_TILES tiles -- are recorded instead of launched, split
+// into runs of one storage family, and each run becomes one cluster launch of
+// k_sweep_segment (one cluster per instance).  Per-cell code and arguments are
+// those of the separate tile launches, so results are bitwise the same.  A
+// sweep inside a cluster costs what a graph-launched tile sweep costs (the
+// cluster barrier takes the place of the launch gap), and a 64^2 level's 16
+// tiles fall two to a CTA: measured slower than separate launches on GB300,
+// hence not the default.
+// ---------------------------------------------------------------------------
+int seg_tiles_of(const biot_ctx *h, int l)
+{
+    int tx, ty;
+    sweep_tile_shape(h->lv[l].fp64, &tx, &ty);
+    return ((h->lv[l].nx + tx - 1) / tx) * ((h->lv[l].ny + ty - 1) / ty);
+}
+
+// The level where a V-cycle's segment starts (-1: none): the finest coarse
+// level such that it and every coarser level have at most SEG_MAX_TILES tiles
+// and no double-float first moments (which the tile form of a segment does not
+// take).  cold: for the solve at t = 0.  Only with BIOT_OPT_SEGMENTS.
+int seg_start(const biot_ctx *h, bool cold)
+{
+    if (!(h->P.options & BIOT_OPT_SEGMENTS)) return -1;
+    int s = -1;
+    for (int l = 0; l < h->L - 1; l++) {
+        if (level_lo(h, l, cold) || seg_tiles_of(h, l) > SEG_MAX_TILES) break;
+        s = l;
+    }
+    return s;
+}
+
+template <typename X>
+bool seg_eq(const X &a, const X &b) { return std::memcmp(&a, &b, sizeof(X)) == 0; }
+
+// Field by field (padding aside): are two sweeps' arguments the same?  The
+// strip height `rows` is not compared: tile sweeps do not read it.
+template <typename T, typename TC>
+bool seg_same_args(const SweepArgs<T, TC> &a, const SweepArgs<T, TC> &b)
+{
+    bool ok = a.nx == b.nx && a.ny == b.ny && a.g == b.g && a.gout == b.gout && a.glo == b.glo &&
+              a.glo_out == b.glo_out && a.r == b.r && a.Ft == b.Ft && a.gc == b.gc && a.rc == b.rc &&
+              a.hist_valid == b.hist_valid && a.zero_init == b.zero_init && a.mode == b.mode &&
+              seg_eq(a.gamma, b.gamma) && seg_eq(a.om_s, b.om_s) && seg_eq(a.om_d, b.om_d) && seg_eq(a.lm, b.lm) &&
+              seg_eq(a.coef_fstar, b.coef_fstar) && seg_eq(a.c0h, b.c0h) && a.resmax == b.resmax &&
+              a.ghosts == b.ghosts && seg_eq(a.k_fs, b.k_fs) && seg_eq(a.k_hs, b.k_hs) && seg_eq(a.k_hd, b.k_hd) &&
+              seg_eq(a.k_h22, b.k_h22) && seg_eq(a.k_gam, b.k_gam) && a.dev == b.dev && a.gd == b.gd &&
+              a.gd_out == b.gd_out && seg_eq(a.dsc, b.dsc) && seg_eq(a.dinv, b.dinv) && a.dev_full == b.dev_full;
+    for (int i = 0; i < 4; i++) ok = ok && a.H[i] == b.H[i] && a.prof[i] == b.prof[i] && a.bc[i] == b.bc[i];
+    return ok;
+}
+
+// Job word of one recorded sweep of level l (level record rel of the program),
+// checked to reproduce the sweep's arguments through seg_patch.
+template <typename T, typename TC>
+int seg_word(const biot_ctx *h, const SweepArgs<T, TC> &a, int l, const SegLevel &L, int rel, unsigned *out)
+{
+    const Level &Lv = h->lv[l];
+    unsigned w = (unsigned)rel;
+    if (a.mode == SWEEP_RESTRICT) w |= SEGJ_RESTRICT;
+    if (a.g == Lv.g[1]) w |= SEGJ_CUR;
+    if (a.zero_init) w |= SEGJ_ZERO;
+    if (a.gc) {
+        w |= SEGJ_PROL;
+        if (l > 0 && (const void *)a.gc == h->lv[l - 1].g[1]) w |= SEGJ_CCUR;
+    }
+    if (a.hist_valid) w |= SEGJ_HIST;
+    SweepArgs<T, TC> b;
+    std::memcpy(&b, &L.a, sizeof(b));
+    seg_patch<T, TC>(b, L, w);
+    if (a.resmax || a.glo || a.Ft || a.dev || !seg_same_args(a, b))
+        return fail(BIOT_ERR_CUDA, "segment program: a sweep is not reproduced by its job word");
+    *out = w;
+    return BIOT_OK;
+}
+
+// The program of recorded sweeps rec[i0 .. i1) (one storage family).
+int seg_build(const biot_ctx *h, const std::vector<SweepJob> &rec, size_t i0, size_t i1, SegProg &prog)
+{
+    prog.fam = rec[i0].tkind == 0 ? 0 : 1;
+    prog.cs = 1;
+    prog.lev.clear();
+    prog.job.clear();
+    std::vector<int> lvl;  // level of each record
+    for (size_t k = i0; k < i1; k++) {
+        const SweepJob &j = rec[k];
+        const int l = j.level;
+        int rel = (int)(std::find(lvl.begin(), lvl.end(), l) - lvl.begin());
+        if (rel == (int)lvl.size()) {
+            if (rel > SEGJ_LEVEL) return fail(BIOT_ERR_CUDA, "segment program: too many levels");
+            SegLevel L;
+            std::memset(&L, 0, sizeof(L));
+            L.tkind = j.tkind;
+            if (j.tkind == 0) L.a.dd = j.dd;
+            else if (j.tkind == 1) L.a.fd = j.fd;
+            else L.a.ff = j.ff;
+            L.buf[0] = h->lv[l].g[0];
+            L.buf[1] = h->lv[l].g[1];
+            if (l > 0) {
+                L.cbuf[0] = h->lv[l - 1].g[0];
+                L.cbuf[1] = h->lv[l - 1].g[1];
+                L.crc = h->lv[l - 1].r;
+            }
+            prog.lev.push_back(L);
+            lvl.push_back(l);
+        }
+        const SegLevel &L = prog.lev[rel];
+        if (L.tkind != j.tkind) return fail(BIOT_ERR_CUDA, "segment program: a level changed its storage kind");
+        unsigned w = 0;
+        int rc = j.tkind == 0 ? seg_word<double, double>(h, j.dd, l, L, rel, &w)
+               : j.tkind == 1 ? seg_word<float, double>(h, j.fd, l, L, rel, &w)
+                              : seg_word<float, float>(h, j.ff, l, L, rel, &w);
+        if (rc) return rc;
+        prog.job.push_back(w);
+        prog.cs = std::max(prog.cs, std::min(SEG_CLUSTER, seg_tiles_of(h, l)));
+    }
+    if (prog.lev.size() > (size_t)SEG_MAX_LEVELS || prog.job.size() > (size_t)SEG_MAX_JOBS)
+        return fail(BIOT_ERR_CUDA, "segment program: too many levels or sweeps for one launch");
+    return BIOT_OK;
+}
+
+// Append program g to the launch parameters P (false: P is full).
+bool seg_pack(SegParams &P, const SegProg &g)
+{
+    if (P.nprog >= SEG_MAX_PROGS || P.lev0[P.nprog] + (int)g.lev.size() > SEG_MAX_LEVELS ||
+        P.job0[P.nprog] + (int)g.job.size() > SEG_MAX_JOBS)
+        return false;
+    const int p = P.nprog;
+    std::copy(g.lev.begin(), g.lev.end(), P.lev + P.lev0[p]);
+    std::copy(g.job.begin(), g.job.end(), P.job + P.job0[p]);
+    P.lev0[p + 1] = P.lev0[p] + (int)g.lev.size();
+    P.job0[p + 1] = P.job0[p] + (int)g.job.size();
+    P.nprog = p + 1;
+    return true;
+}
+
+cudaError_t seg_launch(int fam, const SegParams &P, int cs, cudaStream_t s)
+{
+    return fam == 0 ? launch_sweep_segment<double>(P, cs, s) : launch_sweep_segment<float>(P, cs, s);
+}
+
+int vcycle(biot_ctx *h, int l, bool zero_start, bool prolong_first, int kind);
+
+// The V-cycle from level l down (a coarse-grid correction, zero start) as
+// segments.  Single instance: one launch per run of one storage family, except
+// that a run of the coarsest level's smoothing sweeps alone, FP64 and at most
+// SWEEP_CHAIN_MAX^2 cells, keeps the chained launch.  Batch (record mode): one
+// recorded job per run, whose program goes to segrec.
+int seg_vcycle(biot_ctx *h, int l)
+{
+    std::vector<SweepJob> rec;
+    std::vector<SweepJob> *outer = h->rec;
+    h->rec = &rec;
+    h->in_seg = true;
+    int rc = vcycle(h, l, true, false, BIOT_CYCLE_V);
+    h->rec = outer;
+    h->in_seg = false;
+    if (rc) return rc;
+    std::unique_ptr<SegParams> P;
+    for (size_t i = 0; i < rec.size();) {
+        const int fam = rec[i].tkind == 0 ? 0 : 1;
+        size_t j = i;
+        while (j < rec.size() && (rec[j].tkind == 0 ? 0 : 1) == fam) j++;
+        SegProg prog;
+        if ((rc = seg_build(h, rec, i, j, prog))) return rc;
+        if (outer) {
+            if (!h->segrec) return fail(BIOT_ERR_CUDA, "segment recorded without a program list");
+            SweepJob m{};
+            m.tkind = fam == 0 ? 0 : 2;
+            m.variant = SWEEP_V_SEGMENT | (h->P.ne_fixed > 0 ? SWEEP_V_NOGHOST : 0);
+            m.level = rec[i].level;
+            m.seg = (int)h->segrec->size();
+            h->segrec->push_back(std::move(prog));
+            outer->push_back(m);
+        } else {
+            bool chain = fam == 0 && h->lv[0].nx <= SWEEP_CHAIN_MAX && h->lv[0].ny <= SWEEP_CHAIN_MAX && j - i > 1;
+            for (size_t k = i; k < j && chain; k++) chain = rec[k].level == 0 && rec[k].dd.mode == SWEEP_SMOOTH;
+            if (chain) {
+                CUDA_TRY((launch_sweep_chain<double, double>(rec[i].dd, (int)(j - i), h->stream)));
+            } else {
+                if (!P) P.reset(new (std::nothrow) SegParams());
+                if (!P) return fail(BIOT_ERR_OOM, "segment launch parameters");
+                P->nprog = 0;
+                P->ghosts = h->P.ne_fixed > 0 ? 0 : 1;
+                P->lev0[0] = P->job0[0] = 0;
+                if (!seg_pack(*P, prog)) return fail(BIOT_ERR_CUDA, "segment program too large for one launch");
+                CUDA_TRY(seg_launch(fam, *P, prog.cs, h->stream));
+            }
+            h->launches++;
+        }
+        i = j;
+    }
+    return BIOT_OK;
+}
+
 // ELASTIC_MULTIGRID (Alg. 4) on level l.  zero_start: the iterate is zero
 // (coarse-grid correction of a finer level); prolong_first: the first sweep
 // adds the prolongated iterate of level l - 1 to it (the finer levels of a
@@ -541,6 +749,11 @@ int sweep(biot_ctx *h, int l, int mode, bool zero_init, bool prolong, bool want_
 // followed by a V-cycle (F).
 int vcycle(biot_ctx *h, int l, bool zero_start, bool prolong_first = false, int kind = BIOT_CYCLE_V)
 {
+    // a coarse-grid correction from the segment's start level down: as segments
+    // (a single instance keeps the chained coarsest level when that is all)
+    if (kind == BIOT_CYCLE_V && zero_start && !prolong_first && !h->in_seg && l == seg_start(h, h->cold_solve) &&
+        (h->rec || l > 0))
+        return seg_vcycle(h, l);
     const int K = sweeps_of(&h->P, l);
     const bool fine = (l == h->L - 1);
     int rc;
@@ -1711,9 +1924,11 @@ namespace {
 constexpr long BATCH_TILE_MAX_CELLS = 128L * 128L;
 long batch_tile_max_cells() { return BATCH_TILE_MAX_CELLS; }
 
-// One sweep of the static schedule of an instance.
+// One sweep of the static schedule of an instance, or one segment (fam >= 0:
+// a run of sweeps of one storage family, launched as one program).
 struct PlanOp {
     int level, mode, key;
+    int fam = -1;
 };
 
 // Mirror of vcycle(): the sweeps of one V-cycle from level l down, with their
@@ -1738,6 +1953,34 @@ void plan_vcycle(const biot_ctx *h, int l, int K, int Dmax, std::vector<PlanOp> 
         out.push_back({l, SWEEP_SMOOTH, l == 0 ? bottom + K + k : bottom + 2 * K + (l - 1) * K + k});
 }
 
+// The ops of the segments of one V-cycle's plan collapsed as seg_vcycle
+// records them: the ops of the levels at or below the segment's start level are
+// contiguous (the coarse-grid correction), and each run of one storage family
+// among them becomes one op at the key of its first sweep.
+void plan_segments(const biot_ctx *h, std::vector<PlanOp> &ops)
+{
+    const int s = seg_start(h, false);
+    if (s < 0) return;
+    std::vector<PlanOp> out;
+    for (size_t i = 0; i < ops.size();) {
+        if (ops[i].level > s) {
+            out.push_back(ops[i++]);
+            continue;
+        }
+        const int fam = h->lv[ops[i].level].fp64 ? 0 : 1;
+        PlanOp m = ops[i];
+        m.fam = fam;
+        size_t j = i;
+        while (j < ops.size() && ops[j].level <= s && (h->lv[ops[j].level].fp64 ? 0 : 1) == fam) j++;
+        out.push_back(m);
+        i = j;
+    }
+    ops.swap(out);
+}
+
+int op_tkind(const biot_ctx *h, const PlanOp &o);
+int op_variant(const biot_ctx *h, const PlanOp &o);
+
 int level_tkind(const biot_ctx *h, int l)
 {
     const bool t64 = h->lv[l].fp64;
@@ -1754,6 +1997,17 @@ int level_variant(const biot_ctx *h, int l, int mode)
     return (fine ? 0 : SWEEP_V_COARSE) | (level_lo(h, l, false) ? SWEEP_V_LO : 0) |
            (mode == SWEEP_RESTRICT ? SWEEP_V_RESTRICT : 0) | (h->P.ne_fixed > 0 ? SWEEP_V_NOGHOST : 0) |
            (tile ? SWEEP_V_TILE : 0) | (fine && h->dev == 1 ? SWEEP_V_DEV16 : 0) | (fine && h->dev == 2 ? SWEEP_V_DEVBF16 : 0);
+}
+
+int op_tkind(const biot_ctx *h, const PlanOp &o)
+{
+    return o.fam >= 0 ? (o.fam == 0 ? 0 : 2) : level_tkind(h, o.level);
+}
+
+int op_variant(const biot_ctx *h, const PlanOp &o)
+{
+    if (o.fam >= 0) return SWEEP_V_SEGMENT | (h->P.ne_fixed > 0 ? SWEEP_V_NOGHOST : 0);
+    return level_variant(h, o.level, o.mode);
 }
 
 // Strip heights of one batched launch (levels of nx x ny cells): the fewest whole
@@ -1880,8 +2134,9 @@ int batch_plan(biot_batch_s *b)
         const int up = Dg * (b->K + 1) + 2 * b->K + Dg * b->K;
         std::vector<PlanOp> cyc;
         plan_vcycle(b->inst[i], b->inst[i]->L - 1, b->K, Dg, cyc);
+        plan_segments(b->inst[i], cyc);
         for (int c = 0; c < b->ne; c++)
-            for (const PlanOp &o : cyc) ops[i].push_back({o.level, o.mode, c * up + o.key});
+            for (const PlanOp &o : cyc) ops[i].push_back({o.level, o.mode, c * up + o.key, o.fam});
         b->nops[i] = ops[i].size();
         int &mk = maxkey[b->group_of[i]];
         for (const PlanOp &o : ops[i]) mk = o.key > mk ? o.key : mk;
@@ -1897,15 +2152,21 @@ int batch_plan(biot_batch_s *b)
             for (size_t j = 0; j < ops[i].size(); j++) bykey[ops[i][j].key].push_back({i, (int)j});
     for (int key = 0; key <= maxkey[g]; key++) {
         for (int tk = 0; tk < 3; tk++) {
-            for (int v = 0; v < 128; v++) {  // every combination of the SWEEP_V_* flags
+            for (int v = 0; v < 256; v++) {  // every combination of the SWEEP_V_* flags
                 std::vector<BatchSlot> grp;
                 for (const BatchSlot &s : bykey[key]) {
                     const biot_ctx *h = b->inst[s.inst];
                     const PlanOp &o = ops[s.inst][s.op];
-                    if (level_tkind(h, o.level) != tk || level_variant(h, o.level, o.mode) != v) continue;
+                    if (op_tkind(h, o) != tk || op_variant(h, o) != v) continue;
                     grp.push_back(s);
                 }
                 if (grp.empty()) continue;
+                if (v & SWEEP_V_SEGMENT) {  // segments: one program per job, no work items
+                    BatchLaunch L{tk, v, b->slots[tk].size(), b->items.size(), (int)grp.size(), 0, g};
+                    for (const BatchSlot &sl : grp) b->slots[tk].push_back(sl);
+                    b->launches.push_back(L);
+                    continue;
+                }
                 const bool tile = (v & SWEEP_V_TILE) != 0;
                 const int slots = tile ? 1 : tkind_slots(tk, v & ~SWEEP_V_TILE);
                 if (!slots) return fail(BIOT_ERR_CUDA, "occupancy query of the batched sweep kernel failed");
@@ -2011,11 +2272,52 @@ cudaError_t batch_launch_typed(biot_batch_s *b, const BatchLaunch &L, std::vecto
     return it == it_end ? cudaSuccess : cudaErrorInvalidValue;
 }
 
+// A planned launch of segments: the programs of its jobs packed into as few
+// launches as the parameter block allows (*nl: how many).
+cudaError_t batch_launch_segments(biot_batch_s *b, const BatchLaunch &L, std::vector<std::vector<SweepJob>> &rec,
+                                  std::vector<std::vector<SegProg>> &segrec, cudaStream_t stream, long *nl)
+{
+    std::unique_ptr<SegParams> P(new (std::nothrow) SegParams());
+    if (!P) return cudaErrorMemoryAllocation;
+    const int fam = L.tkind == 0 ? 0 : 1;
+    int cs = 1;
+    auto reset = [&]() {
+        P->nprog = 0;
+        P->ghosts = (L.variant & SWEEP_V_NOGHOST) ? 0 : 1;
+        P->lev0[0] = P->job0[0] = 0;
+        cs = 1;
+    };
+    reset();
+    for (int k = 0; k < L.njobs; k++) {
+        const BatchSlot &sl = b->slots[L.tkind][L.job_off + k];
+        const int gi = rec[sl.inst][sl.op].seg;
+        if (gi < 0 || gi >= (int)segrec[sl.inst].size()) return cudaErrorInvalidValue;
+        const SegProg &g = segrec[sl.inst][gi];
+        if (g.fam != fam) return cudaErrorInvalidValue;
+        if (!seg_pack(*P, g)) {
+            if (P->nprog == 0) return cudaErrorInvalidValue;
+            cudaError_t e = seg_launch(fam, *P, cs, stream);
+            if (e != cudaSuccess) return e;
+            (*nl)++;
+            reset();
+            if (!seg_pack(*P, g)) return cudaErrorInvalidValue;
+        }
+        cs = std::max(cs, g.cs);
+    }
+    if (P->nprog > 0) {
+        cudaError_t e = seg_launch(fam, *P, cs, stream);
+        if (e != cudaSuccess) return e;
+        (*nl)++;
+    }
+    return cudaSuccess;
+}
+
 // Capture one time step of every instance (parity par of the flow buffers).
 int batch_capture(biot_batch_s *b, int par)
 {
     const int n = (int)b->inst.size();
     std::vector<std::vector<SweepJob>> rec(n);
+    std::vector<std::vector<SegProg>> segrec(n);
     std::vector<FlowRec> frec;
     std::vector<long> l0(n), c0(n);
     CUDA_TRY(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
@@ -2027,9 +2329,11 @@ int batch_capture(biot_batch_s *b, int par)
         c0[i] = h->total_cycles;
         h->rec = &rec[i];
         h->frec = &frec;
+        h->segrec = &segrec[i];
         rc = advance(h);  // flow steps and sweeps are recorded, launched below for all instances
         h->rec = nullptr;
         h->frec = nullptr;
+        h->segrec = nullptr;
         if (!rc && frec.size() != (size_t)i + 1) rc = fail(BIOT_ERR_CUDA, "batched schedule: flow step not recorded");
         nl += h->launches - l0[i];
         if (!rc && rec[i].size() != b->nops[i]) rc = fail(BIOT_ERR_CUDA, "batched schedule does not match the recorded sweeps");
@@ -2074,6 +2378,11 @@ int batch_capture(biot_batch_s *b, int par)
     for (size_t k = 0; k < b->launches.size() && !rc; k++) {
         const BatchLaunch &L = b->launches[k];
         const cudaStream_t st = fork ? b->branch[L.group] : b->stream;
+        if (L.variant & SWEEP_V_SEGMENT) {
+            cudaError_t e = batch_launch_segments(b, L, rec, segrec, st, &nl);
+            if (e != cudaSuccess) rc = fail(BIOT_ERR_CUDA, std::string("batched segment launch: ") + cudaGetErrorString(e));
+            continue;
+        }
         cudaError_t e = L.tkind == 0 ? batch_launch_typed<double, double>(b, L, rec, st)
                       : L.tkind == 1 ? batch_launch_typed<float, double>(b, L, rec, st)
                                      : batch_launch_typed<float, float>(b, L, rec, st);

@@ -5,6 +5,7 @@
 #include "sweep_batch.cuh"
 #include "sweep_chain.cuh"
 #include "sweep_mom.cuh"
+#include "sweep_segment.cuh"
 
 #define BIOT_SWEEP_MOM(T, TC)                                                                          \
     template <> cudaError_t biot::launch_sweep_mom<T, TC>(const biot::SweepArgs<T, TC> &a, cudaStream_t s) \
@@ -17,6 +18,9 @@
     template <> cudaError_t biot::launch_sweep_chain<T, TC>(const biot::SweepArgs<T, TC> &a, int n,     \
                                                             cudaStream_t s)                            \
     { return biot::launch_sweep_chain_impl<T, TC>(a, n, s); }
+#define BIOT_SEGMENT(T)                                                                                \
+    template <> cudaError_t biot::launch_sweep_segment<T>(const biot::SegParams &P, int cs, cudaStream_t s) \
+    { return biot::launch_sweep_segment_impl<T>(P, cs, s); }
 #define BIOT_FIELDS(T)                                                                                 \
     template <> cudaError_t biot::launch_sexp<T>(const biot::SexpArgs<T> &a, cudaStream_t s)             \
     { return biot::launch_sexp_impl<T>(a, s); }                                                        \

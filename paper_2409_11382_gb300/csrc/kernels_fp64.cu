@@ -4,6 +4,7 @@
 #include "instantiate.h"
 
 BIOT_SWEEP_MOM(double, double)
+BIOT_SEGMENT(double)
 BIOT_FIELDS(double)
 
 // Stopping test of one V-cycle (tolerance mode, inside a CUDA graph):
