@@ -117,12 +117,23 @@ def test_step_load_257_stable_variant_fp32_vs_oracle(alpha):
     assert rel(*r["p"]) < TOL32
 
 
-def test_step_load_257_stable_variant_fp64_full_run():
-    params, sides, steps = W.step_load_257(alpha=1.0)
+@pytest.mark.parametrize("alpha", [0.5, 1.0])
+def test_step_load_257_stable_variant_full_run_fp64_and_fp32(alpha):
+    """All 200 steps of the 257x257 step load with c0 = 0.1 (the stable variant):
+    one oracle run, against which the FP64 path holds 1e-12 and the FP32 path
+    1e-5 in eta, p and sigma."""
+    params, sides, steps = W.step_load_257(alpha=alpha)
     params = dict(params, c0=0.1)
-    r = run_both(params, sides, steps)
-    assert rel(*r["eta"]) < TOL64
-    assert rel(*r["p"]) < TOL64
+    o = O.Oracle(params, sides)
+    assert o.step(steps) == 0
+    ref = dict(eta=o.read_u()[0], p=o.read_p()[0], sigma=o.read_stress())
+    o.close()
+    for precision, tol in ((W.FP64, TOL64), (W.FP32, TOL32)):
+        with biot.Solver(dict(params, precision=precision), sides) as g:
+            assert g.step(steps) == biot.OK
+            got = dict(eta=g.read_u()[0], p=g.read_p()[0], sigma=g.read_stress())
+        for k in ref:
+            assert rel(got[k], ref[k]) < tol, (precision, k, rel(got[k], ref[k]))
 
 
 # ---------------------------------------------------------------------------
