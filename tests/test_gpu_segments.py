@@ -96,3 +96,30 @@ def test_batch_segments_bitwise_equal_to_separate_sweeps():
         assert np.array_equal(seg[i][0], sep[i][0]), i
         assert np.array_equal(seg[i][1], sep[i][1]), i
     assert st_seg["launches_per_step"] < st_sep["launches_per_step"]
+
+
+def test_served_segments_equal_solo_runs():
+    """A server whose requests take segments: the reused executable step graphs
+    (cudaGraphExecUpdate) carry the cluster launches, and every result equals
+    the request solved alone with separate launches, bitwise."""
+    import time
+    reqs = W.served_requests(count=6, seed=3, sizes=(64, 128), steps=8, T=0.008)
+    reqs = [(a, dict(p, options=p.get("options", 0) | biot.OPT_SEGMENTS), s, T) for a, p, s, T in reqs]
+    budget = sum(biot.estimate_bytes(p, s) for _, p, s, _ in reqs[:3])
+    with biot.Server(budget, max_resident=3) as srv:
+        ids = []
+        t0 = time.perf_counter()
+        for arrival, p, s, T in reqs:
+            while time.perf_counter() - t0 < arrival * 0.2:
+                time.sleep(0.0005)
+            ids.append(srv.submit(p, s, T))
+        for rid in ids:
+            assert srv.wait(rid, timeout=300) == biot.OK
+        results = [srv.fetch(rid) for rid in ids]
+        st = srv.stats()
+    assert st["graphs_reused"] >= 1
+    for (_, p, s, T), (eta, pr, t) in zip(reqs, results):
+        plain = dict(p, options=p["options"] & ~biot.OPT_SEGMENTS)
+        with biot.Solver(plain, s) as g:
+            g.solve_to(T)
+            assert np.array_equal(eta, g.read_u()[0]) and np.array_equal(pr, g.read_p()[0])
