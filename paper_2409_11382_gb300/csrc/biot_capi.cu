@@ -1922,6 +1922,9 @@ namespace {
 // In a batch, levels of at most this many cells run as tiles: a 128^2 level's
 // rows would fill only 128 of the 248 columns of two strips.
 constexpr long BATCH_TILE_MAX_CELLS = 128L * 128L;
+// Whether the depth groups' branches of the step graph run at descending stream
+// priorities, deepest first.
+constexpr bool BATCH_BRANCH_PRIORITIES = true;
 long batch_tile_max_cells() { return BATCH_TILE_MAX_CELLS; }
 
 // One sweep of the static schedule of an instance, or one segment (fam >= 0:
@@ -2203,9 +2206,16 @@ int batch_plan(biot_batch_s *b)
     }
     }
     // the branch streams and the fork / join events of the step graph
+    // the deepest group (usually the largest instances: the step's critical
+    // path) gets the highest stream priority, the next ones lower ones; the
+    // captured kernel nodes keep their stream's priority
+    int prio_least = 0, prio_greatest = 0;
+    CUDA_TRY(cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest));
     while ((int)b->branch.size() < b->ngroups) {
         cudaStream_t st;
-        CUDA_TRY(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+        const int g = (int)b->branch.size();
+        const int prio = BATCH_BRANCH_PRIORITIES ? std::min(prio_greatest + g, prio_least) : prio_least;
+        CUDA_TRY(cudaStreamCreateWithPriority(&st, cudaStreamNonBlocking, prio));
         b->branch.push_back(st);
         cudaEvent_t ev;
         CUDA_TRY(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
@@ -2405,7 +2415,7 @@ int batch_capture(biot_batch_s *b, int par)
     cudaError_t e = cudaStreamEndCapture(b->stream, &g);
     if (!rc && e != cudaSuccess) rc = fail(BIOT_ERR_CUDA, std::string("cudaStreamEndCapture: ") + cudaGetErrorString(e));
     if (!rc) {
-        e = cudaGraphInstantiate(&b->graph[par], g, 0);
+        e = cudaGraphInstantiate(&b->graph[par], g, BATCH_BRANCH_PRIORITIES ? cudaGraphInstantiateFlagUseNodePriority : 0);
         if (e != cudaSuccess) {
             b->graph[par] = nullptr;
             rc = fail(BIOT_ERR_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
