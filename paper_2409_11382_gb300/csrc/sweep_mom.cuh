@@ -1196,6 +1196,13 @@ __device__ __forceinline__ void tile_body(const SweepArgs<T, TC> &a, int bx, int
     T rmax = T(0), gmax = T(0);
     double rsum = 0.0;
     const bool writes = live && c >= 2 && c < W - 2 && rrow >= 2 && rrow < R - 2 && x < nx && y < ny;
+    // A warp with a wall cell among its written cells takes the wall form for
+    // all of them: it then runs one form instead of both one after the other
+    // (the slowest warp sets a tile's time at its barriers).  For a cell away
+    // from the walls the wall form adds zero terms (exactly zero coefficients):
+    // the values are the same, up to the sign of an exact zero.
+    const bool wall_cell = writes && ((!perx && (x == 0 || x == nx - 1)) || (!pery && (y == 0 || y == ny - 1)));
+    const bool wall = __any_sync(0xffffffffu, wall_cell);
     T d[8];
 #pragma unroll
     for (int k = 0; k < 8; k++) d[k] = T(0);
@@ -1203,14 +1210,6 @@ __device__ __forceinline__ void tile_body(const SweepArgs<T, TC> &a, int bx, int
         const int sl[3] = {rrow - 1, rrow, rrow + 1};
         const OwnCell<T> own = own_cell<T, W, KIND, LO>(rg, rrow, c);
         const T(&gcur)[8] = own.g;
-        // FP64 tiles that touch a wall take the wall form for every cell: a warp
-        // then runs one form instead of both one after the other, and FP64
-        // instructions are slow to issue on GB300.  For a cell away from the
-        // walls the wall form adds zero terms (exactly zero coefficients): the
-        // values are the same, up to the sign of an exact zero.
-        const bool tile_wall = (!perx && (x0 == 0 || x0 + TX >= nx)) || (!pery && (y0 == 0 || y0 + TY >= ny));
-        const bool wall = sizeof(T) == 8 ? tile_wall
-                                         : (!perx && (x == 0 || x == nx - 1)) || (!pery && (y == 0 || y == ny - 1));
         if (wall) residual_cell<T, TC, KIND, LO, W, true>(a, rg, x, y, sl, c, perx, pery, own, d);
         else residual_cell<T, TC, KIND, LO, W, false>(a, rg, x, y, sl, c, perx, pery, own, d);
         if (!RESTRICT) {
