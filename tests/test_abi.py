@@ -141,3 +141,21 @@ def test_server_needs_a_device(lib):
     with pytest.raises(biot.BiotError) as e:
         biot.Server(1 << 30, 4)
     assert e.value.code in (biot.ERR_NO_DEVICE, biot.ERR_CUDA)
+
+
+def test_binding_constants_match_the_header():
+    """Every numeric #define BIOT_<NAME> of the header that the binding mirrors
+    as <NAME> has the same value; the option flags are all mirrored."""
+    from paper_2409_11382_gb300 import biot
+    text = open(HEADER).read()
+    defines = dict(re.findall(r"^#define\s+BIOT_(\w+)\s+\(?(-?\d+)\)?", text, flags=re.M))
+    assert "OPT_SEGMENTS" in defines and "FP32" in defines
+    checked = 0
+    for name, value in defines.items():
+        if hasattr(biot, name):
+            assert getattr(biot, name) == int(value), name
+            checked += 1
+    for name in defines:
+        if name.startswith("OPT_"):
+            assert hasattr(biot, name), name
+    assert checked >= 20
