@@ -23,6 +23,14 @@ _SRC = os.path.join(_HERE, "biot_oracle.c")
 _LIB = os.path.join(_HERE, "_build", "libbiot_oracle.so")
 _lock = threading.Lock()
 _lib = None
+# Build flavours of the same source: "standard" (the oracle), and
+# "reassociated", which lets the compiler reorder FP64 sums (no other change).
+# The second one exists for one test only: how far the order of FP64 roundings
+# alone moves the oracle's results at a given grid size.
+_FLAVOURS = {"standard": ("libbiot_oracle.so", []),
+             "reassociated": ("libbiot_oracle_reassoc.so",
+                              ["-fassociative-math", "-fno-signed-zeros", "-fno-trapping-math"])}
+_libs = {}
 
 PERIODIC, SYMMETRY, DIRICHLET, NEUMANN = 0, 1, 2, 3
 BOTTOM, RIGHT, TOP, LEFT = 0, 1, 2, 3
@@ -50,54 +58,64 @@ class _Stats(C.Structure):
                 ("om_d", C.c_double), ("kap_lattice", C.c_double), ("last_res_l2", C.c_double)]
 
 
-def build(force: bool = False) -> str:
+def build(force: bool = False, flavour: str = "standard") -> str:
     """Compile the oracle into a shared library next to it (gcc, FP64, no FMA contraction)."""
+    name, extra = _FLAVOURS[flavour]
+    lib_path = os.path.join(_HERE, "_build", name)
     with _lock:
-        if (not force and os.path.exists(_LIB)
-                and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
-            return _LIB
-        os.makedirs(os.path.dirname(_LIB), exist_ok=True)
-        tmp = _LIB + f".{os.getpid()}.tmp"
-        cmd = ["gcc", "-std=c99", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
-               "-shared", "-o", tmp, _SRC, "-lm"]
+        if (not force and os.path.exists(lib_path)
+                and os.path.getmtime(lib_path) >= os.path.getmtime(_SRC)):
+            return lib_path
+        os.makedirs(os.path.dirname(lib_path), exist_ok=True)
+        tmp = lib_path + f".{os.getpid()}.tmp"
+        cmd = ["gcc", "-std=c99", "-O2", "-ffp-contract=off", "-fno-fast-math"] + extra + [
+            "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
         # OpenMP for the per-cell loops (orc_set_threads); without it the
         # pragmas are ignored and the oracle runs on one thread
         if subprocess.run(cmd[:-1] + ["-fopenmp", "-lm"], capture_output=True).returncode != 0:
             subprocess.run(cmd, check=True)
-        os.replace(tmp, _LIB)
-        return _LIB
+        os.replace(tmp, lib_path)
+        return lib_path
 
 
-def _load():
+def _load(flavour: str = "standard"):
     global _lib
+    if flavour != "standard":
+        if flavour not in _libs:
+            _libs[flavour] = _declare(C.CDLL(build(flavour=flavour)))
+        return _libs[flavour]
     if _lib is None:
-        lib = C.CDLL(build())
-        P = C.POINTER(C.c_double)
-        lib.orc_create.restype = C.c_void_p
-        lib.orc_create.argtypes = [C.POINTER(_Params), C.POINTER(_Side)]
-        lib.orc_destroy.argtypes = [C.c_void_p]
-        for name in ("orc_step",):
-            getattr(lib, name).argtypes = [C.c_void_p, C.c_int]
-        lib.orc_solve_to.argtypes = [C.c_void_p, C.c_double]
-        lib.orc_set_sources.argtypes = [C.c_void_p, P, P]
-        lib.orc_read_u.argtypes = [C.c_void_p, P, P]
-        lib.orc_read_p.argtypes = [C.c_void_p, P, P]
-        lib.orc_read_stress.argtypes = [C.c_void_p, P]
-        lib.orc_stats_get.argtypes = [C.c_void_p, C.POINTER(_Stats)]
-        lib.orc_collide_cell.argtypes = [C.c_double, C.c_double, P, P, P]
-        lib.orc_inverse_table.argtypes = [P]
-        lib.orc_prepare_elastic.argtypes = [C.c_void_p]
-        lib.orc_fixed_point_map.argtypes = [C.c_void_p, P, P]
-        lib.orc_vcycle.argtypes = [C.c_void_p, C.c_int]
-        lib.orc_vcycle.restype = C.c_double
-        lib.orc_plain_pseudo_step.argtypes = [C.c_void_p]
-        for name in ("orc_get_g", "orc_set_g", "orc_get_f", "orc_set_f"):
-            getattr(lib, name).argtypes = [C.c_void_p, P]
-        lib.orc_set_threads.argtypes = [C.c_int]
-        lib.orc_get_threads.restype = C.c_int
-        lib.orc_openmp.restype = C.c_int
-        _lib = lib
+        _lib = _declare(C.CDLL(build()))
     return _lib
+
+
+def _declare(lib):
+    """Argument and result types of the oracle's C functions."""
+    P = C.POINTER(C.c_double)
+    lib.orc_create.restype = C.c_void_p
+    lib.orc_create.argtypes = [C.POINTER(_Params), C.POINTER(_Side)]
+    lib.orc_destroy.argtypes = [C.c_void_p]
+    for name in ("orc_step",):
+        getattr(lib, name).argtypes = [C.c_void_p, C.c_int]
+    lib.orc_solve_to.argtypes = [C.c_void_p, C.c_double]
+    lib.orc_set_sources.argtypes = [C.c_void_p, P, P]
+    lib.orc_read_u.argtypes = [C.c_void_p, P, P]
+    lib.orc_read_p.argtypes = [C.c_void_p, P, P]
+    lib.orc_read_stress.argtypes = [C.c_void_p, P]
+    lib.orc_stats_get.argtypes = [C.c_void_p, C.POINTER(_Stats)]
+    lib.orc_collide_cell.argtypes = [C.c_double, C.c_double, P, P, P]
+    lib.orc_inverse_table.argtypes = [P]
+    lib.orc_prepare_elastic.argtypes = [C.c_void_p]
+    lib.orc_fixed_point_map.argtypes = [C.c_void_p, P, P]
+    lib.orc_vcycle.argtypes = [C.c_void_p, C.c_int]
+    lib.orc_vcycle.restype = C.c_double
+    lib.orc_plain_pseudo_step.argtypes = [C.c_void_p]
+    for name in ("orc_get_g", "orc_set_g", "orc_get_f", "orc_set_f"):
+        getattr(lib, name).argtypes = [C.c_void_p, P]
+    lib.orc_set_threads.argtypes = [C.c_int]
+    lib.orc_get_threads.restype = C.c_int
+    lib.orc_openmp.restype = C.c_int
+    return lib
 
 
 def _ptr(a: np.ndarray):
@@ -144,8 +162,8 @@ class Oracle:
     ``p_type`` and optional ``eta_profile`` (2 x (2n+1)) / ``p_profile`` (2n+1).
     """
 
-    def __init__(self, params: dict, sides):
-        lib = _load()
+    def __init__(self, params: dict, sides, flavour: str = "standard"):
+        lib = _load(flavour)
         self._lib = lib
         p = _Params()
         for name, _ in _Params._fields_:
