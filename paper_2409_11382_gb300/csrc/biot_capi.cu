@@ -260,6 +260,7 @@ struct biot_ctx {
     std::vector<biot::FlowRec> *frec = nullptr;  // record mode: flow steps appended here
     std::vector<biot::SegProg> *segrec = nullptr;  // record mode: programs of the recorded segments
     bool in_seg = false;  // recording the sweeps of a segment (seg_vcycle)
+    bool batched = false; // an instance of a batch (its steps are recorded and merged)
     // Allocation source of a server's instance: the server's stream-ordered
     // pool, so that freeing the instance synchronises only its own stream
     // (cudaFree would wait for every resident instance); its two pinned host
@@ -566,10 +567,13 @@ int seg_tiles_of(const biot_ctx *h, int l)
 // The level where a V-cycle's segment starts (-1: none): the finest coarse
 // level such that it and every coarser level have at most SEG_MAX_TILES tiles
 // and no double-float first moments (which the tile form of a segment does not
-// take).  cold: for the solve at t = 0.  Only with BIOT_OPT_SEGMENTS.
+// take).  cold: for the solve at t = 0.  With BIOT_OPT_SEGMENTS; without it,
+// only an instance of a batch has one, and only its FP64 coarsest level: the
+// 2K sweeps that a single instance runs as one chained launch.
 int seg_start(const biot_ctx *h, bool cold)
 {
-    if (!(h->P.options & BIOT_OPT_SEGMENTS)) return -1;
+    if (!(h->P.options & BIOT_OPT_SEGMENTS))
+        return (h->batched && h->L > 1 && h->lv[0].fp64 && seg_tiles_of(h, 0) <= SEG_MAX_TILES) ? 0 : -1;
     int s = -1;
     for (int l = 0; l < h->L - 1; l++) {
         if (level_lo(h, l, cold) || seg_tiles_of(h, l) > SEG_MAX_TILES) break;
@@ -1925,6 +1929,9 @@ constexpr long BATCH_TILE_MAX_CELLS = 128L * 128L;
 // Whether the depth groups' branches of the step graph run at descending stream
 // priorities, deepest first.
 constexpr bool BATCH_BRANCH_PRIORITIES = true;
+// Whether a batch runs the 2K sweeps of each instance's FP64 coarsest level as
+// one segment launch (one cluster per instance) rather than 2K phase launches.
+constexpr bool BATCH_COARSEST_SEGMENT = true;
 long batch_tile_max_cells() { return BATCH_TILE_MAX_CELLS; }
 
 // One sweep of the static schedule of an instance, or one segment (fam >= 0:
@@ -2502,6 +2509,7 @@ int biot_batch_create(int count, const biot_params *params, const biot_side *sid
             return fail(rc, msg);
         }
         b->inst.push_back(h);
+        h->batched = BATCH_COARSEST_SEGMENT;
         if (cudaStreamSynchronize(h->stream) != cudaSuccess) {
             batch_release(b);
             return fail(BIOT_ERR_CUDA, "instance set-up failed");
